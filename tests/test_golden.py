@@ -1,0 +1,27 @@
+"""Hand-derived examples (tests/golden/hand_examples.json) against the oracle."""
+import json
+import os
+
+import numpy as np
+
+import oracle
+
+G = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_examples.json")))
+
+
+def a(x):
+    return np.asarray(x, dtype=np.float64)
+
+
+def test_golden_oracle():
+    g = G["gemm"]
+    assert np.array_equal(oracle.gemm(a(g["A"]), a(g["B"]), a(g["C"]), g["alpha"], g["beta"]), a(g["out"]))
+    g = G["chain"]
+    E, F = oracle.gemm_chain(a(g["A"]), a(g["B"]), a(g["C"]), a(g["D"]), g["alpha"], g["beta"])
+    assert np.array_equal(E, a(g["E"])) and np.array_equal(F, a(g["F"]))
+    assert np.array_equal(oracle.covariance(a(G["covariance"]["X"])), a(G["covariance"]["out"]))
+    assert np.array_equal(oracle.correlation(a(G["correlation"]["X"])), a(G["correlation"]["out"]))
+    g = G["syrk"]
+    assert np.array_equal(oracle.syrk(a(g["A"]), a(g["C"]), g["alpha"], g["beta"], g["fill"]), a(g["out"]))
+    g = G["syr2k"]
+    assert np.array_equal(oracle.syr2k(a(g["A"]), a(g["B"]), a(g["C"]), g["alpha"], g["beta"], g["fill"]), a(g["out"]))
