@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Benchmark of libloopnest's hot path.
+
+One step = one pass of the chained product E = (A B) C, F = alpha E + beta D
+on 2048 x 2048 FP32 matrices (alpha = 1.5, beta = 1.2, entries U[-1,1],
+seed 0), the polybench 2mm loop nest of the paper's evaluation, through the
+C ABI (ln_gemm_chain) in the internalized tensor-core form with the 3xBF16
+split (hi*hi + hi*lo + lo*hi, FP32 accumulation), the gated precision.
+
+Reported (one JSON line from rank 0):
+  value        GFLOP/s of the internalized form, algorithmic flops 4 n^3 per
+               step, device time from CUDA events around each step, L2
+               flushed (256 MiB write) between steps outside the timed events
+  plain        GFLOP/s of the plain one-thread-per-output form, same work
+  fp32_tiled   GFLOP/s of the exact-FP32 shared-memory tiled form
+  roofline     the tcgen05 contraction kernel: algorithmic flops per launch
+               (2 n^3) / its mean launch time (CUDA events the library
+               records on the launch stream), against the measured BF16
+               peak divided by the 3 MMA products of the split
+  e2e          same metric through ln_gemm_chain with pinned host buffers:
+               H2D of A, B, C, D and D2H of E, F inside the timed region
+  cpu_baseline the FP64 oracle on this host's cores over a bounded sample of
+               rows of the same workload; its rows also give rel_err, the
+               sampled relative Frobenius error of E against the oracle
+  clocks       nvidia-smi samples taken while the steps ran
+
+`--impl reference` times the oracle alone (the reference arm of this
+project: the paper publishes no code), on bounded samples of the workload.
+With --gpus N under torchrun every rank runs its own replica (no data-path
+collective); value is the sum over ranks, timed by the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 2048
+WORKLOAD = {
+    "workload": "polybench 2mm chain E=(A*B)*C, F=alpha*E+beta*D, 2048x2048 FP32, alpha=1.5, beta=1.2, "
+                "U[-1,1] seed 0",
+    "n": N,
+    "form": "internalized",
+    "precision": "3xbf16",
+    "l2": "flushed between timed steps (256 MiB write outside the step events)",
+}
+METRIC = "GFLOP/s & roofline fraction, internalized vs plain kernels, at <=1e-5 rel error"
+FLOPS = 4.0 * N ** 3          # two N^3 multiply-adds per step
+FLOPS_PER_UMMA = 2.0 * N ** 3
+PRODUCTS = 3                   # MMA products per multiply-add in the 3xBF16 split
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["own", "reference"], default="own")
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the CPU baseline sample")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d.get("hbm_gbs", 6800.0)), "measured"
+    except Exception:
+        return 1900.0, 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- CPU (oracle) leg
+def cpu_sample(d, target_s, rows_max=N):
+    """Time the FP64 oracle on the first R rows of the chain (E rows depend
+    only on the same rows of A and D); R is calibrated to ~target_s."""
+    import oracle
+
+    oracle.build()
+    cores = oracle.max_threads()
+    r = 4
+    t0 = time.perf_counter()
+    oracle.gemm_chain(d["A"][:r], d["B"], d["C"], d["D"][:r], d["alpha"], d["beta"])
+    dt = max(time.perf_counter() - t0, 1e-4)
+    R = int(min(rows_max, max(r, r * target_s / dt)))
+    t0 = time.perf_counter()
+    E_rows, F_rows = oracle.gemm_chain(d["A"][:R], d["B"], d["C"], d["D"][:R], d["alpha"], d["beta"])
+    dt = time.perf_counter() - t0
+    gflops = 4.0 * R * N * N / dt / 1e9
+    return {"value": gflops, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {R} of {N} rows of E and F (4*{R}*{N}^2 flops), {dt:.2f} s",
+            "seconds": dt}, R, E_rows, F_rows
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    from paper_2312_13170_gb300 import inputs
+    import oracle
+
+    oracle.build()
+    d = inputs.chain_inputs(N, seed=0)
+    cores = oracle.max_threads()
+    # calibrate a per-step sample of about 1 s
+    r = 4
+    t0 = time.perf_counter()
+    oracle.gemm_chain(d["A"][:r], d["B"], d["C"], d["D"][:r], d["alpha"], d["beta"])
+    dt = max(time.perf_counter() - t0, 1e-4)
+    R = int(min(N, max(1, r * 1.0 / dt)))
+    for _ in range(args.warmup):
+        oracle.gemm_chain(d["A"][:R], d["B"], d["C"], d["D"][:R], d["alpha"], d["beta"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.gemm_chain(d["A"][:R], d["B"], d["C"], d["D"][:R], d["alpha"], d["beta"])
+    total = time.perf_counter() - t0
+    ms = total / max(args.steps, 1) * 1e3
+    gflops = 4.0 * R * N * N / (ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": gflops, "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": WORKLOAD, "impl": "reference",
+        "cpu_baseline": {"value": gflops, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {R} of {N} rows of E and F per step"},
+        "e2e": {"value": gflops, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU leg
+def run_own(args):
+    import torch
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2312_13170_gb300 import api, inputs
+
+    d = inputs.chain_inputs(N, seed=0)
+    dev = torch.device("cuda", local)
+    T = {k: torch.from_numpy(d[k]).to(dev) for k in "ABCD"}
+    E = torch.empty((N, N), dtype=torch.float32, device=dev)
+    F = torch.empty_like(E)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    alpha, beta = d["alpha"], d["beta"]
+
+    def step(form="internalized", prec="3xbf16"):
+        api.gemm_chain(T["A"], T["B"], T["C"], T["D"], alpha, beta, form=form, prec=prec, out=(E, F))
+
+    def timed(nsteps, warm, form, prec, with_timing=False):
+        for _ in range(warm):
+            step(form, prec)
+        api.stream_check()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        barrier()
+        if with_timing:
+            api.timing_enable(True)
+            for fam in ("umma", "pack", "simt", "plain", "stats"):
+                api.timing_read(fam)
+        l0 = api.launch_count()
+        for s, e in evs:
+            flush.zero_()
+            s.record()
+            step(form, prec)
+            e.record()
+        barrier()
+        launches = api.launch_count() - l0
+        fams = {}
+        if with_timing:
+            for fam in ("umma", "pack"):
+                fams[fam] = api.timing_read(fam)
+            api.timing_enable(False)
+        api.stream_check()
+        ms = sum(s.elapsed_time(e) for s, e in evs) / max(nsteps, 1)
+        return ms, launches, fams
+
+    clocks = Clocks(local)
+    ms, launches, fams = timed(args.steps, args.warmup, "internalized", "3xbf16", with_timing=True)
+    clk = clocks.stop()
+    E_int = E.clone()
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = FLOPS * ws / (ms_max / 1e3) / 1e9
+
+    # plain and exact-FP32 tiled forms: same work, fewer steps
+    ms_plain, _, _ = timed(args.plain_steps, 1, "plain", "fp32")
+    ms_tiled, _, _ = timed(max(args.plain_steps, 5), 1, "internalized", "fp32")
+
+    # end to end through the public API with host buffers
+    hostA = {k: torch.from_numpy(d[k]).pin_memory() for k in "ABCD"}
+    hostE = torch.empty((N, N), dtype=torch.float32).pin_memory()
+    hostF = torch.empty_like(hostE)
+    h2d = sum(v.numel() * 4 for v in hostA.values())
+    d2h = 2 * N * N * 4
+
+    def e2e_step():
+        for k in "ABCD":
+            T[k].copy_(hostA[k], non_blocking=True)
+        step()
+        hostE.copy_(E, non_blocking=True)
+        hostF.copy_(F, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.e2e_steps)]
+    for s, e in evs:
+        s.record()
+        e2e_step()
+        e.record()
+    barrier()
+    ms_e2e = sum(s.elapsed_time(e) for s, e in evs) / max(args.e2e_steps, 1)
+
+    bf16_peak, hbm, peak_src = peaks()
+    umma_ms, umma_n = fams.get("umma", (0.0, 0))
+    achieved = FLOPS_PER_UMMA / (umma_ms / umma_n / 1e3) / 1e12 if umma_n else None
+    peak = bf16_peak / PRODUCTS
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16",
+        "precision": "3xBF16 split (hi*hi + hi*lo + lo*hi), FP32 accumulation",
+        "data": "synthetic (seeded U[-1,1], shapes of the paper's polybench 2mm at the 2048 workload)",
+        "config": dict(WORKLOAD, parallelism=f"replicas x{ws}"),
+        "plain": {"value": FLOPS / (ms_plain / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms_plain,
+                  "form": "plain", "precision": "fp32"},
+        "fp32_tiled": {"value": FLOPS / (ms_tiled / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms_tiled,
+                       "form": "internalized", "precision": "fp32"},
+        "speedup_vs_plain": ms_plain / ms,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "k_umma<2,0> (tcgen05 3xBF16 contraction)",
+                     "peak_note": f"{peak_src} bf16 burst {bf16_peak} TFLOP/s / {PRODUCTS} products",
+                     "launches": umma_n, "ms_per_launch": (umma_ms / umma_n) if umma_n else None,
+                     "pack_ms_per_step": fams.get("pack", (0.0, 0))[0] / max(args.steps, 1)},
+        "e2e": {"value": FLOPS / (ms_e2e / 1e3) / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu, R, E_rows, F_rows = cpu_sample(d, args.cpu_seconds)
+        line["cpu_baseline"] = cpu
+        got = E_int[:R].cpu().numpy()
+        line["rel_err"] = {"value": inputs.rel_fro(got, E_rows), "gate": 1e-5,
+                           "sample": f"rows 0..{R - 1} of E against the FP64 oracle"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_own(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

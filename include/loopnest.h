@@ -1,0 +1,259 @@
+/*
+ * libloopnest — GB300 (sm_103a) kernels for the loop nests that loop
+ * internalization and array-reduction detection speed up
+ * ("Experiences Building an MLIR-based SYCL Compiler", arXiv 2312.13170):
+ * GEMM, a chain of two GEMMs (polybench 2mm), covariance, correlation, SYRK
+ * and SYR2K, plus the vector-Jacobian products of the chain, covariance and
+ * correlation.
+ *
+ * Every operation exists in two forms:
+ *   LN_FORM_PLAIN        one thread per output element, reading global memory
+ *                        in its inner loop with a register accumulator: the
+ *                        loop nest of paper Sec. VI-C, Listing 5, after the
+ *                        array-reduction detection of Sec. VI-B.
+ *   LN_FORM_INTERNALIZED the inner loop's operands are staged in on-chip
+ *                        memory tile by tile, as loop internalization does
+ *                        with work-group local memory (Sec. VI-C, Listing 6):
+ *                        with LN_PREC_FP32 a shared-memory tiled FP32 SIMT
+ *                        kernel; with a tensor-core precision, operands are
+ *                        split into BF16 terms, packed in tcgen05 operand
+ *                        tiles, copied into shared memory by the bulk-copy
+ *                        (TMA) engine and multiplied by tcgen05.mma into
+ *                        TMEM accumulators.
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are FP32, row-major; ld* are leading dimensions in elements
+ *    (ld >= number of columns). Sizes are int; negative sizes or ld < columns
+ *    give LN_ERR_INVALID_VALUE. A size of 0 makes the call a no-op (GEMM with
+ *    K = 0 scales C by beta).
+ *  - Every pointer argument that names an array (inputs, outputs, workspace)
+ *    is a DEVICE pointer unless the comment says "host". The caller owns all
+ *    memory and the stream; the library never allocates device memory.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are
+ *    asynchronous: the returned status covers argument validation and kernel
+ *    launch only. Errors raised on the device (a bounded wait that ran out)
+ *    are reported by ln_stream_check() after the work has finished.
+ *  - beta == 0 means the input C (or D) is never read, so NaN/Inf there is not
+ *    propagated (BLAS convention).
+ *  - Outputs must not overlap any input, except where the comment allows
+ *    in-place C: overlapping ranges give LN_ERR_ALIASING. This is the
+ *    no-alias guarantee that the paper's alias analysis proves before it
+ *    transforms a loop (Sec. V-A, Sec. VI-A), checked here at run time.
+ *  - Internalized tensor-core calls need a workspace of at least the size the
+ *    matching *_workspace_size function returns (256-byte aligned device
+ *    memory); too small a workspace gives LN_ERR_WORKSPACE. Plain and FP32
+ *    SIMT calls need none except where noted (workspace may then be NULL).
+ *  - On any error the call launches nothing and ln_get_last_error() returns a
+ *    message for the calling thread.
+ */
+#ifndef LOOPNEST_H
+#define LOOPNEST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LN_SUCCESS = 0,
+    LN_ERR_INVALID_VALUE = 1, /* bad size, leading dimension, enum or NULL pointer */
+    LN_ERR_ALIASING = 2,      /* an output range overlaps an input range */
+    LN_ERR_MISALIGNED = 3,    /* a pointer does not meet a stated alignment */
+    LN_ERR_UNSUPPORTED = 4,   /* form/precision combination not available */
+    LN_ERR_CUDA = 5,          /* a CUDA runtime call or launch failed */
+    LN_ERR_TIMEOUT = 6,       /* a bounded device wait ran out (ln_stream_check) */
+    LN_ERR_WORKSPACE = 7      /* workspace missing or smaller than required */
+} ln_status;
+
+typedef enum { LN_FORM_PLAIN = 0, LN_FORM_INTERNALIZED = 1 } ln_form;
+
+/*
+ * Arithmetic of the contraction. FP32 is exact-FP32 FFMA (both forms). The
+ * others run on tcgen05 tensor cores with FP32 accumulation (internalized form
+ * only): BF16 = one product of BF16-rounded operands; 3XBF16 = each operand
+ * split x = hi + lo into two BF16 terms, products hi*hi + hi*lo + lo*hi;
+ * 6XBF16 = three BF16 terms (hi + mid + lo), the six products whose order is
+ * at least 2^-16. FP32, 3XBF16 and 6XBF16 meet a 1e-5 relative Frobenius error
+ * against exact arithmetic on the shipped workloads; BF16 does not.
+ */
+typedef enum {
+    LN_PREC_FP32 = 0,
+    LN_PREC_BF16 = 1,
+    LN_PREC_3XBF16 = 2,
+    LN_PREC_6XBF16 = 3
+} ln_precision;
+
+/* Triangle of a symmetric output (SYRK/SYR2K): LOWER/UPPER read and write only
+ * that triangle of C; FULL computes the lower triangle from C's lower triangle
+ * and writes each value to both (i,j) and (j,i). */
+typedef enum { LN_FILL_FULL = 0, LN_FILL_LOWER = 1, LN_FILL_UPPER = 2 } ln_fill;
+
+/* Message for the last failed call on this host thread ("" if none). */
+const char *ln_get_last_error(void);
+/* Static name of a status code. */
+const char *ln_status_string(ln_status s);
+/* Library version as major*10000 + minor*100 + patch. */
+int ln_version(void);
+
+/*
+ * Wait for `stream`, then read and clear the library's device error word.
+ * Returns LN_ERR_TIMEOUT if a kernel on this device gave up a bounded wait
+ * since the last check, LN_ERR_CUDA if the stream reports a CUDA error, else
+ * LN_SUCCESS.
+ */
+ln_status ln_stream_check(void *stream);
+
+/*
+ * Launch accounting for benchmarks and profiling. ln_launch_count() is the
+ * number of kernels this library has launched in the process (always
+ * counted). While timing is enabled, every launch of a kernel family is
+ * bracketed by CUDA events recorded on the stream it is launched on;
+ * ln_timing_read() waits for those events and returns the total time in
+ * milliseconds and the number of launches of one family since the last read
+ * (families: "umma" = tcgen05 contraction, "pack" = split-and-pack,
+ * "simt" = FP32 tiled contraction, "plain" = one-thread-per-output kernels,
+ * "stats" = column statistics and element-wise helpers). Enabling and reading
+ * must not happen during CUDA graph capture. Not thread-safe.
+ */
+long long ln_launch_count(void);
+ln_status ln_timing_enable(int on);
+ln_status ln_timing_read(const char *family, double *total_ms /*host*/, int *launches /*host*/);
+
+/*
+ * GEMM, polybench form (paper Sec. VI-C, Listings 5-6; Sec. VIII "GEMM"):
+ *   C[i][j] = alpha * sum_k A[i][k] * B[k][j] + beta * C[i][j]
+ * A is M x K (lda), B is K x N (ldb), C is M x N (ldc), in place.
+ */
+ln_status ln_gemm_workspace_size(int M, int N, int K, ln_form form, ln_precision prec, size_t *bytes /*host*/);
+ln_status ln_gemm(int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb,
+                  float beta, float *C, int ldc, void *workspace, size_t workspace_bytes, ln_form form,
+                  ln_precision prec, void *stream);
+
+/*
+ * Chained product (polybench 2mm, Sec. VIII):
+ *   T = A * B;  E = T * C;  F = alpha * E + beta * D
+ * A is ni x nk, B is nk x nj, C is nj x nl, D/E/F are ni x nl; all contiguous
+ * (ld = columns). T lives in the workspace (FP32 for FP32 forms; as packed
+ * BF16 split terms for tensor-core forms), so every form needs a workspace.
+ * D may be NULL when beta == 0. E and F must not overlap each other or inputs.
+ */
+ln_status ln_gemm_chain_workspace_size(int ni, int nj, int nk, int nl, ln_form form, ln_precision prec,
+                                       size_t *bytes /*host*/);
+ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float *A, const float *B,
+                        const float *C, float beta, const float *D, float *E, float *F, void *workspace,
+                        size_t workspace_bytes, ln_form form, ln_precision prec, void *stream);
+
+/*
+ * Column statistics of a data matrix X (nsamples x nfeat, ldx), the array
+ * reductions of polybench covariance/correlation (Sec. VI-B, Sec. VIII), two
+ * passes: mean[j] = sum_s X[s][j] / n; ss[j] = sum_s (X[s][j] - mean[j])^2.
+ * mean and ss are FP64 device arrays of nfeat elements (nsamples >= 1). The
+ * internalized form needs a workspace for its per-block partial sums; the
+ * plain form needs none. Both forms accumulate in FP64.
+ */
+ln_status ln_col_stats_workspace_size(int nsamples, int nfeat, ln_form form, size_t *bytes /*host*/);
+ln_status ln_col_stats(int nsamples, int nfeat, const float *X, int ldx, double *mean, double *ss,
+                       void *workspace, size_t workspace_bytes, ln_form form, void *stream);
+
+/*
+ * Covariance (polybench covariance, Sec. VIII): with Xc = X - 1 mean^T,
+ *   cov[i][j] = sum_s Xc[s][i] * Xc[s][j] / (nsamples - 1)      (nsamples >= 2)
+ * The full symmetric nfeat x nfeat matrix is written.
+ * Correlation (polybench correlation): corr[i][j] = sum_s Xc[s][i] Xc[s][j] /
+ * (sqrt(ss_i) sqrt(ss_j)) for i != j, corr[i][i] = 1 exactly, and 0 off the
+ * diagonal for a zero-variance column. Both need a workspace (the FP64
+ * column statistics; packed operands for tensor-core forms).
+ */
+ln_status ln_covariance_workspace_size(int nsamples, int nfeat, ln_form form, ln_precision prec,
+                                       size_t *bytes /*host*/);
+ln_status ln_covariance(int nsamples, int nfeat, const float *X, int ldx, float *cov, int ldcov,
+                        void *workspace, size_t workspace_bytes, ln_form form, ln_precision prec,
+                        void *stream);
+ln_status ln_correlation(int nsamples, int nfeat, const float *X, int ldx, float *corr, int ldcorr,
+                         void *workspace, size_t workspace_bytes, ln_form form, ln_precision prec,
+                         void *stream);
+
+/*
+ * SYRK (polybench syrk, Sec. VIII): on the triangle chosen by `fill`,
+ *   C[i][j] = alpha * sum_k A[i][k] * A[j][k] + beta * C[i][j]       A: n x k
+ * SYR2K (polybench syr2k): C[i][j] = alpha * sum_k (A[i][k] B[j][k] +
+ * B[i][k] A[j][k]) + beta * C[i][j]; A and B are n x k. C is n x n, in place.
+ */
+ln_status ln_syrk_workspace_size(int n, int k, ln_form form, ln_precision prec, size_t *bytes /*host*/);
+ln_status ln_syrk(ln_fill fill, int n, int k, float alpha, const float *A, int lda, float beta, float *C,
+                  int ldc, void *workspace, size_t workspace_bytes, ln_form form, ln_precision prec,
+                  void *stream);
+ln_status ln_syr2k_workspace_size(int n, int k, ln_form form, ln_precision prec, size_t *bytes /*host*/);
+ln_status ln_syr2k(ln_fill fill, int n, int k, float alpha, const float *A, int lda, const float *B, int ldb,
+                   float beta, float *C, int ldc, void *workspace, size_t workspace_bytes, ln_form form,
+                   ln_precision prec, void *stream);
+
+/*
+ * Batched SYRK / SYR2K over instances of uneven sizes in one persistent
+ * launch fed by a device-side tile queue (polybench syrk/syr2k, Sec. VIII,
+ * batched). Each instance i is described by descs[i]; B/ldb are ignored by
+ * SYRK. `h_descs` (host) and `d_descs` (device) must hold the same `count`
+ * descriptors: the host copy sizes the launch and is validated, the device
+ * copy is what the kernels read (so a captured CUDA graph may be replayed
+ * after the caller rewrites d_descs with instances of the same sizes).
+ * The same alpha, beta and fill apply to every instance. Instances' outputs
+ * must not overlap each other or any input.
+ */
+typedef struct {
+    int n, k;
+    const float *A;
+    int lda;
+    const float *B;
+    int ldb;
+    float *C;
+    int ldc;
+} ln_sym_desc;
+
+ln_status ln_syrk_batched_workspace_size(int count, const ln_sym_desc *h_descs /*host*/, ln_form form,
+                                         ln_precision prec, size_t *bytes /*host*/);
+ln_status ln_syrk_batched(ln_fill fill, int count, const ln_sym_desc *h_descs /*host*/,
+                          const ln_sym_desc *d_descs, float alpha, float beta, void *workspace,
+                          size_t workspace_bytes, ln_form form, ln_precision prec, void *stream);
+ln_status ln_syr2k_batched_workspace_size(int count, const ln_sym_desc *h_descs /*host*/, ln_form form,
+                                          ln_precision prec, size_t *bytes /*host*/);
+ln_status ln_syr2k_batched(ln_fill fill, int count, const ln_sym_desc *h_descs /*host*/,
+                           const ln_sym_desc *d_descs, float alpha, float beta, void *workspace,
+                           size_t workspace_bytes, ln_form form, ln_precision prec, void *stream);
+
+/*
+ * Vector-Jacobian products (hand-written adjoints).
+ *
+ * Chain: for E = (A*B)*C and an upstream gradient G = dL/dE (ni x nl),
+ *   dA = G (B C)^T,  dB = A^T G C^T,  dC = (A B)^T G.
+ * All contiguous; dA/dB/dC must not overlap the inputs or each other.
+ *
+ * Covariance: for an upstream gradient W = dL/dcov (nfeat x nfeat, ldw),
+ *   dX = Xc (W + W^T) / (nsamples - 1).
+ * Correlation: with s_j = sqrt(ss_j), Z = Xc diag(1/s), W' = W with a zero
+ * diagonal: dZ = Z (W' + W'^T); dXc_j = (dZ_j - Z_j (Z_j . dZ_j)) / s_j;
+ * dX = dXc - 1 (1^T dXc) / nsamples.
+ * `stats` (nullable) holds 2*nfeat doubles, mean then ss, from a forward call
+ * (ln_col_stats); when NULL they are recomputed from X. The centred matrix is
+ * always recomputed from X rather than stored.
+ */
+ln_status ln_gemm_chain_bwd_workspace_size(int ni, int nj, int nk, int nl, ln_form form, ln_precision prec,
+                                           size_t *bytes /*host*/);
+ln_status ln_gemm_chain_bwd(int ni, int nj, int nk, int nl, const float *A, const float *B, const float *C,
+                            const float *G, float *dA, float *dB, float *dC, void *workspace,
+                            size_t workspace_bytes, ln_form form, ln_precision prec, void *stream);
+ln_status ln_covariance_bwd_workspace_size(int nsamples, int nfeat, ln_form form, ln_precision prec,
+                                           size_t *bytes /*host*/);
+ln_status ln_covariance_bwd(int nsamples, int nfeat, const float *X, int ldx, const float *W, int ldw,
+                            const double *stats, float *dX, int lddx, void *workspace, size_t workspace_bytes,
+                            ln_form form, ln_precision prec, void *stream);
+ln_status ln_correlation_bwd(int nsamples, int nfeat, const float *X, int ldx, const float *W, int ldw,
+                             const double *stats, float *dX, int lddx, void *workspace,
+                             size_t workspace_bytes, ln_form form, ln_precision prec, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LOOPNEST_H */

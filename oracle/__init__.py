@@ -65,6 +65,7 @@ def _load():
         "oracle_gemm_chain_vjp": (None, [i, i, i, i, P, P, P, P, P, P, P]),
         "oracle_covariance_vjp": (None, [i, i, P, P, P]),
         "oracle_correlation_vjp": (None, [i, i, P, P, P]),
+        "oracle_cov_rows": (None, [i, i, P, i, i, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -188,3 +189,13 @@ def correlation_vjp(X, W):
     dX = np.empty((n, m), np.float64)
     _load().oracle_correlation_vjp(n, m, _p(X), _p(W), _p(dX))
     return dX
+
+
+def cov_rows(X, rows, corr=False):
+    """Rows `rows` of covariance (or correlation) of X, by the same definition."""
+    X = _f64(X)
+    n, m = X.shape
+    r = np.ascontiguousarray(np.asarray(rows, dtype=np.int32))
+    out = np.empty((len(r), m), np.float64)
+    _load().oracle_cov_rows(n, m, _p(X), 1 if corr else 0, len(r), _p(r), _p(out))
+    return out

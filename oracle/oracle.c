@@ -343,3 +343,32 @@ void oracle_correlation_vjp(int n, int m, const double *X, const double *W, doub
     free(dot);
     free(colsum);
 }
+
+/*
+ * Selected rows of the covariance (corr == 0) or correlation (corr != 0)
+ * matrix, by the same definitions as oracle_covariance / oracle_correlation:
+ * out[q][j] for q < nrows is entry (rows[q], j). Lets a test check sampled
+ * outputs of a full-size matrix without forming all of it.
+ */
+void oracle_cov_rows(int n, int m, const double *X, int corr, int nrows, const int *rows, double *out) {
+    double *mean = (double *)malloc(sizeof(double) * (size_t)m + 1);
+    double *ss = (double *)malloc(sizeof(double) * (size_t)m + 1);
+    oracle_col_stats(n, m, X, mean, ss);
+#pragma omp parallel for schedule(static)
+    for (int q = 0; q < nrows; ++q) {
+        const int i = rows[q];
+        for (int j = 0; j < m; ++j) {
+            double acc = 0.0;
+            for (int r = 0; r < n; ++r)
+                acc += (X[(size_t)r * m + i] - mean[i]) * (X[(size_t)r * m + j] - mean[j]);
+            double v;
+            if (!corr) v = acc / (double)(n - 1);
+            else if (i == j) v = 1.0;
+            else if (ss[i] > 0.0 && ss[j] > 0.0) v = acc / (sqrt(ss[i]) * sqrt(ss[j]));
+            else v = 0.0;
+            out[(size_t)q * m + j] = v;
+        }
+    }
+    free(mean);
+    free(ss);
+}

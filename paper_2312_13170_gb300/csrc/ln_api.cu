@@ -1,0 +1,983 @@
+// The C ABI of libloopnest: argument validation, aliasing checks, workspace
+// planning and dispatch to the plain, FP32-tiled and tcgen05 engines.
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "ln_internal.h"
+
+namespace ln {
+
+namespace {
+thread_local char g_msg[512] = "";
+}
+
+ln_status fail(ln_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+void clear_error() { g_msg[0] = '\0'; }
+
+ln_status check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(LN_ERR_CUDA, "%s launch failed: %s", what, cudaGetErrorString(e));
+    return LN_SUCCESS;
+}
+
+// ------------------------------------------------------------------ launch accounting
+namespace {
+struct TimingState {
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[FAM_COUNT];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
+};
+TimingState g_timing;
+std::atomic<long long> g_launches{0};
+const char *const kFamilies[FAM_COUNT] = {"umma", "pack", "simt", "plain", "stats"};
+}  // namespace
+
+LaunchScope::LaunchScope(Family fam, cudaStream_t s) : slot(-1), st(s), f(fam) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (!g_timing.on) return;
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (!g_timing.pool.empty()) {
+        ev = g_timing.pool.back();
+        g_timing.pool.pop_back();
+    } else if (cudaEventCreate(&ev.first) != cudaSuccess || cudaEventCreate(&ev.second) != cudaSuccess) {
+        return;
+    }
+    cudaEventRecord(ev.first, st);
+    g_timing.pending[f].push_back(ev);
+    slot = (int)g_timing.pending[f].size() - 1;
+}
+
+LaunchScope::~LaunchScope() {
+    if (slot >= 0) cudaEventRecord(g_timing.pending[f][slot].second, st);
+}
+
+bool inject_timeout_requested() {
+    const char *v = getenv("LN_FAULT_INJECT");
+    return v && strcmp(v, "timeout") == 0;
+}
+
+int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (cache[dev] == 0) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = n > 0 ? n : 1;
+    }
+    return cache[dev];
+}
+
+namespace {
+
+// ------------------------------------------------------------------ workspace planning
+// A bump allocator over the caller's workspace. With base == nullptr it only
+// counts, so the size query and the call run the very same plan.
+struct Ws {
+    char *base;
+    size_t off = 0;
+    explicit Ws(void *b) : base(static_cast<char *>(b)) {}
+    template <class T>
+    T *take(size_t bytes) {
+        off = align_up(off, 256);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += align_up(bytes, 256);
+        return p;
+    }
+};
+
+// ------------------------------------------------------------------ validation helpers
+struct Span {
+    const void *p;
+    size_t bytes;
+};
+
+Span mspan(const void *p, long long rows, long long cols, long long ld, size_t elem = 4) {
+    if (!p || rows <= 0 || cols <= 0) return {p, 0};
+    return {p, (size_t)(((rows - 1) * ld + cols) * (long long)elem)};
+}
+
+bool overlap(Span a, Span b) {
+    if (!a.p || !b.p || a.bytes == 0 || b.bytes == 0) return false;
+    auto x = reinterpret_cast<uintptr_t>(a.p), y = reinterpret_cast<uintptr_t>(b.p);
+    return x < y + b.bytes && y < x + a.bytes;
+}
+
+constexpr long long MAX_DIM = 1 << 22;
+
+ln_status check_dims(std::initializer_list<long long> dims) {
+    for (long long d : dims)
+        if (d < 0 || d > MAX_DIM) return fail(LN_ERR_INVALID_VALUE, "size %lld out of range [0, %lld]", d, MAX_DIM);
+    return LN_SUCCESS;
+}
+
+ln_status check_form(ln_form form, ln_precision prec) {
+    if (form != LN_FORM_PLAIN && form != LN_FORM_INTERNALIZED)
+        return fail(LN_ERR_INVALID_VALUE, "unknown form %d", (int)form);
+    if (prec < LN_PREC_FP32 || prec > LN_PREC_6XBF16) return fail(LN_ERR_INVALID_VALUE, "unknown precision %d", (int)prec);
+    if (form == LN_FORM_PLAIN && prec != LN_PREC_FP32)
+        return fail(LN_ERR_UNSUPPORTED, "the plain form computes in FP32 only (precision %d requested)", (int)prec);
+    return LN_SUCCESS;
+}
+
+ln_status check_ws(void *ws, size_t have, size_t need) {
+    if (need == 0) return LN_SUCCESS;
+    if (!ws) return fail(LN_ERR_WORKSPACE, "workspace of %zu bytes required, got NULL", need);
+    if (have < need) return fail(LN_ERR_WORKSPACE, "workspace of %zu bytes required, got %zu", need, have);
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(LN_ERR_MISALIGNED, "workspace must be 256-byte aligned");
+    return LN_SUCCESS;
+}
+
+#define LN_TRY(expr)                           \
+    do {                                       \
+        ln_status s_ = (expr);                 \
+        if (s_ != LN_SUCCESS) return s_;       \
+    } while (0)
+
+inline bool tensor_prec(ln_precision p) { return prec_terms(p) > 0; }
+inline cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
+
+// ------------------------------------------------------------------ generic contraction
+// out(i,j) <- epi( sum_k opA(i,k) * opB(k,j) ), M x N x K, with
+//   opA(i,k) = A[i*lda+k] (a_t == 0) or A[k*lda+i] (a_t == 1)
+//   opB(k,j) = B[k*ldb+j] (b_t == 0) or B[j*ldb+k] (b_t == 1)
+struct Operand {
+    const float *p;
+    long long ld;
+    int t;
+};
+
+struct ContractPlan {
+    char *px = nullptr, *py = nullptr;
+    int mt = 0, nt = 0, kt = 0;
+};
+
+void plan_contract(Ws &w, int M, int N, int K, ln_form form, ln_precision prec, ContractPlan &cp) {
+    if (form != LN_FORM_INTERNALIZED || !tensor_prec(prec)) return;
+    const int P = prec_terms(prec);
+    cp.mt = (int)ceil_div(M, PK_ROWS);
+    cp.nt = (int)ceil_div(N, PK_ROWS);
+    cp.kt = (int)ceil_div(K, PK_K);
+    cp.px = w.take<char>(packed_bytes(cp.mt, cp.kt, P));
+    cp.py = w.take<char>(packed_bytes(cp.nt, cp.kt, P));
+}
+
+ln_status run_contract(int M, int N, int K, Operand a, Operand b, const EpiParams &epi, ln_form form,
+                       ln_precision prec, const ContractPlan &cp, cudaStream_t st) {
+    if (M == 0 || N == 0) return LN_SUCCESS;
+    if (form == LN_FORM_PLAIN || K == 0) {
+        long long sai = a.t ? 1 : a.ld, sak = a.t ? a.ld : 1;
+        long long sbk = b.t ? 1 : b.ld, sbj = b.t ? b.ld : 1;
+        return plain_gemm(M, N, K, a.p, sai, sak, b.p, sbk, sbj, epi, st);
+    }
+    if (!tensor_prec(prec)) {
+        SimtOperands op{};
+        op.A[0] = op.A[1] = a.p;
+        op.B[0] = op.B[1] = b.p;
+        op.lda[0] = op.lda[1] = a.ld;
+        op.ldb[0] = op.ldb[1] = b.ld;
+        op.a_t = a.t;
+        op.b_t = b.t;
+        op.nseg = 1;
+        return simt_contract(M, N, K, op, epi, st);
+    }
+    const int P = prec_terms(prec);
+    PackSrc px{a.p, a.ld, a.t ? 1 : 0, M, K, nullptr, nullptr, cp.px, cp.mt, cp.kt};
+    PackSrc py{b.p, b.ld, b.t ? 0 : 1, N, K, nullptr, nullptr, cp.py, cp.nt, cp.kt};
+    LN_TRY(pack_operand(px, P, st));
+    LN_TRY(pack_operand(py, P, st));
+    UmmaProblem pb{};
+    pb.seg[0] = {cp.px, cp.py};
+    pb.nseg = 1;
+    pb.kt = cp.kt;
+    pb.x_kt = cp.kt;
+    pb.y_kt = cp.kt;
+    pb.mt = cp.mt;
+    pb.nt = cp.nt;
+    pb.sym = 0;
+    pb.inject_timeout = inject_timeout_requested();
+    pb.epi = epi;
+    return umma_contract(pb, P, st);
+}
+
+EpiParams epi_gemm(int M, int N, float alpha, float beta, float *C, long long ldc) {
+    EpiParams e{};
+    e.mode = EPI_GEMM;
+    e.M = M;
+    e.N = N;
+    e.alpha = alpha;
+    e.beta = beta;
+    e.C = C;
+    e.ldc = ldc;
+    return e;
+}
+
+EpiParams epi_store(int M, int N, float alpha, float *C, long long ldc) {
+    EpiParams e = epi_gemm(M, N, alpha, 0.0f, C, ldc);
+    e.mode = EPI_STORE;
+    return e;
+}
+
+// ------------------------------------------------------------------ chain
+struct ChainPlan {
+    float *T = nullptr;
+    ContractPlan c1, c2;
+};
+
+void plan_chain(Ws &w, int ni, int nj, int nk, int nl, ln_form form, ln_precision prec, ChainPlan &p) {
+    p.T = w.take<float>(sizeof(float) * (size_t)ni * nj);
+    plan_contract(w, ni, nj, nk, form, prec, p.c1);
+    plan_contract(w, ni, nl, nj, form, prec, p.c2);
+}
+
+// ------------------------------------------------------------------ covariance / correlation
+struct CovPlan {
+    double *mean = nullptr, *ss = nullptr, *partials = nullptr;
+    float *hi = nullptr, *lo = nullptr, *rs = nullptr;
+    char *pack = nullptr;
+    int mt = 0, kt = 0;
+};
+
+void plan_cov(Ws &w, int n, int m, ln_form form, ln_precision prec, CovPlan &p) {
+    p.mean = w.take<double>(sizeof(double) * m);
+    p.ss = w.take<double>(sizeof(double) * m);
+    p.hi = w.take<float>(sizeof(float) * m);
+    p.lo = w.take<float>(sizeof(float) * m);
+    p.rs = w.take<float>(sizeof(float) * m);
+    if (form == LN_FORM_INTERNALIZED) p.partials = w.take<double>(col_stats_partials_bytes(n, m));
+    if (form == LN_FORM_INTERNALIZED && tensor_prec(prec)) {
+        p.mt = (int)ceil_div(m, PK_ROWS);
+        p.kt = (int)ceil_div(n, PK_K);
+        p.pack = w.take<char>(packed_bytes(p.mt, p.kt, prec_terms(prec)));
+    }
+}
+
+ln_status run_cov(bool corr, int n, int m, const float *X, int ldx, float *out, int ldo, void *ws, size_t wsb,
+                  ln_form form, ln_precision prec, cudaStream_t st) {
+    LN_TRY(check_dims({n, m}));
+    LN_TRY(check_form(form, prec));
+    if (m == 0) return LN_SUCCESS;
+    if (n < 2) return fail(LN_ERR_INVALID_VALUE, "covariance/correlation need nsamples >= 2 (got %d)", n);
+    if (!X || !out) return fail(LN_ERR_INVALID_VALUE, "NULL X or output");
+    if (ldx < m || ldo < m) return fail(LN_ERR_INVALID_VALUE, "leading dimension smaller than nfeat");
+    if (overlap(mspan(out, m, m, ldo), mspan(X, n, m, ldx))) return fail(LN_ERR_ALIASING, "output overlaps X");
+    Ws count(nullptr);
+    CovPlan p;
+    plan_cov(count, n, m, form, prec, p);
+    LN_TRY(check_ws(ws, wsb, count.off));
+    Ws w(ws);
+    plan_cov(w, n, m, form, prec, p);
+
+    EpiParams e{};
+    e.mode = EPI_SYM;
+    e.M = e.N = m;
+    e.C = out;
+    e.ldc = ldo;
+    e.fill = LN_FILL_FULL;
+    e.sym_kind = corr ? SYM_CORR : SYM_SCALE;
+    e.alpha = (float)(1.0 / (double)(n - 1));
+    e.rs = p.rs;
+
+    if (form == LN_FORM_PLAIN) {
+        LN_TRY(plain_col_stats(n, m, X, ldx, p.mean, p.ss, st));
+        LN_TRY(stats_derive(m, p.mean, p.ss, nullptr, nullptr, p.rs, st));
+        return plain_cov(n, m, X, ldx, p.mean, e, st);
+    }
+    LN_TRY(col_stats(n, m, X, ldx, p.mean, p.ss, p.hi, p.lo, p.rs, p.partials, st));
+    if (!tensor_prec(prec)) {
+        SimtOperands op{};
+        op.A[0] = op.A[1] = X;
+        op.B[0] = op.B[1] = X;
+        op.lda[0] = op.lda[1] = ldx;
+        op.ldb[0] = op.ldb[1] = ldx;
+        op.a_t = 1;
+        op.b_t = 0;
+        op.nseg = 1;
+        op.a_off_hi = op.b_off_hi = p.hi;
+        op.a_off_lo = op.b_off_lo = p.lo;
+        return simt_contract(m, m, n, op, e, st);
+    }
+    const int P = prec_terms(prec);
+    PackSrc ps{X, ldx, 1, m, n, p.hi, p.lo, p.pack, p.mt, p.kt};
+    LN_TRY(pack_operand(ps, P, st));
+    UmmaProblem pb{};
+    pb.seg[0] = {p.pack, p.pack};
+    pb.nseg = 1;
+    pb.kt = p.kt;
+    pb.x_kt = pb.y_kt = p.kt;
+    pb.mt = pb.nt = p.mt;
+    pb.sym = 1;
+    pb.epi = e;
+    return umma_contract(pb, P, st);
+}
+
+// ------------------------------------------------------------------ SYRK / SYR2K
+struct SymPlan {
+    char *pa = nullptr, *pb = nullptr;
+    int mt = 0, kt = 0;
+};
+
+void plan_sym(Ws &w, bool two, int n, int k, ln_form form, ln_precision prec, SymPlan &p) {
+    if (form != LN_FORM_INTERNALIZED || !tensor_prec(prec)) return;
+    p.mt = (int)ceil_div(n, PK_ROWS);
+    p.kt = (int)ceil_div(k, PK_K);
+    p.pa = w.take<char>(packed_bytes(p.mt, p.kt, prec_terms(prec)));
+    if (two) p.pb = w.take<char>(packed_bytes(p.mt, p.kt, prec_terms(prec)));
+}
+
+ln_status run_sym(bool two, ln_fill fill, int n, int k, float alpha, const float *A, int lda, const float *B, int ldb,
+                  float beta, float *C, int ldc, void *ws, size_t wsb, ln_form form, ln_precision prec,
+                  cudaStream_t st) {
+    LN_TRY(check_dims({n, k}));
+    LN_TRY(check_form(form, prec));
+    if (fill != LN_FILL_FULL && fill != LN_FILL_LOWER && fill != LN_FILL_UPPER)
+        return fail(LN_ERR_INVALID_VALUE, "unknown fill %d", (int)fill);
+    if (n == 0) return LN_SUCCESS;
+    if (!C || (k > 0 && (!A || (two && !B)))) return fail(LN_ERR_INVALID_VALUE, "NULL operand");
+    if (ldc < n || (k > 0 && (lda < k || (two && ldb < k))))
+        return fail(LN_ERR_INVALID_VALUE, "leading dimension too small");
+    Span sc = mspan(C, n, n, ldc);
+    if (overlap(sc, mspan(A, n, k, lda)) || (two && overlap(sc, mspan(B, n, k, ldb))))
+        return fail(LN_ERR_ALIASING, "C overlaps an input");
+    if (k == 0) return sym_fill_zero_k(n, fill, beta, C, ldc, st);
+    Ws count(nullptr);
+    SymPlan p;
+    plan_sym(count, two, n, k, form, prec, p);
+    LN_TRY(check_ws(ws, wsb, count.off));
+    Ws w(ws);
+    plan_sym(w, two, n, k, form, prec, p);
+
+    EpiParams e{};
+    e.mode = EPI_SYM;
+    e.M = e.N = n;
+    e.alpha = alpha;
+    e.beta = beta;
+    e.C = C;
+    e.ldc = ldc;
+    e.fill = fill;
+    e.sym_kind = SYM_AXPBY;
+    if (form == LN_FORM_PLAIN) return plain_sym(n, k, A, lda, two ? B : nullptr, ldb, e, st);
+    if (!tensor_prec(prec)) {
+        SimtOperands op{};
+        op.a_t = 0;
+        op.b_t = 1;
+        op.nseg = two ? 2 : 1;
+        op.A[0] = A;
+        op.lda[0] = lda;
+        op.B[0] = two ? B : A;
+        op.ldb[0] = two ? ldb : lda;
+        op.A[1] = op.B[0];
+        op.lda[1] = op.ldb[0];
+        op.B[1] = A;
+        op.ldb[1] = lda;
+        return simt_contract(n, n, k, op, e, st);
+    }
+    const int P = prec_terms(prec);
+    PackSrc pa{A, lda, 0, n, k, nullptr, nullptr, p.pa, p.mt, p.kt};
+    LN_TRY(pack_operand(pa, P, st));
+    UmmaProblem pb{};
+    if (two) {
+        PackSrc pbs{B, ldb, 0, n, k, nullptr, nullptr, p.pb, p.mt, p.kt};
+        LN_TRY(pack_operand(pbs, P, st));
+        pb.seg[0] = {p.pa, p.pb};
+        pb.seg[1] = {p.pb, p.pa};
+        pb.nseg = 2;
+    } else {
+        pb.seg[0] = {p.pa, p.pa};
+        pb.nseg = 1;
+    }
+    pb.kt = p.kt;
+    pb.x_kt = pb.y_kt = p.kt;
+    pb.mt = pb.nt = p.mt;
+    pb.sym = 1;
+    pb.epi = e;
+    return umma_contract(pb, P, st);
+}
+
+// ------------------------------------------------------------------ batched
+struct BatchPlan {
+    UmmaProblem *probs = nullptr;
+    int *tile_prefix = nullptr;
+    long long *pack_off = nullptr;
+    int *pack_prefix = nullptr;
+    int *order = nullptr;
+    int *queue = nullptr;
+    char *pack = nullptr;
+    long long total_tiles = 0, total_pack_tiles = 0;
+    int max_n = 0;
+};
+
+ln_status validate_batch(bool two, int count, const ln_sym_desc *h, BatchPlan &bp) {
+    if (count < 0 || count > (1 << 20)) return fail(LN_ERR_INVALID_VALUE, "batch count %d out of range", count);
+    if (count > 0 && !h) return fail(LN_ERR_INVALID_VALUE, "NULL host descriptor array");
+    std::vector<Span> outs, ins;
+    outs.reserve(count);
+    for (int i = 0; i < count; ++i) {
+        const ln_sym_desc &d = h[i];
+        if (d.n < 0 || d.k < 0 || d.n > MAX_DIM || d.k > MAX_DIM)
+            return fail(LN_ERR_INVALID_VALUE, "instance %d: size out of range", i);
+        if (d.n == 0) continue;
+        if (!d.C || (d.k > 0 && (!d.A || (two && !d.B))))
+            return fail(LN_ERR_INVALID_VALUE, "instance %d: NULL operand", i);
+        if (d.ldc < d.n || (d.k > 0 && (d.lda < d.k || (two && d.ldb < d.k))))
+            return fail(LN_ERR_INVALID_VALUE, "instance %d: leading dimension too small", i);
+        outs.push_back(mspan(d.C, d.n, d.n, d.ldc));
+        ins.push_back(mspan(d.A, d.n, d.k, d.lda));
+        if (two) ins.push_back(mspan(d.B, d.n, d.k, d.ldb));
+        long long t = ceil_div(d.n, PK_ROWS);
+        bp.total_tiles += t * (t + 1) / 2;
+        bp.total_pack_tiles += t * ceil_div(d.k, PK_K) * (two ? 2 : 1);
+        bp.max_n = std::max(bp.max_n, d.n);
+    }
+    auto by_addr = [](const Span &a, const Span &b) { return a.p < b.p; };
+    std::sort(outs.begin(), outs.end(), by_addr);
+    for (size_t i = 1; i < outs.size(); ++i)
+        if (overlap(outs[i - 1], outs[i])) return fail(LN_ERR_ALIASING, "two instances' outputs overlap");
+    std::sort(ins.begin(), ins.end(), by_addr);
+    for (const Span &o : outs) {  // binary search the inputs around each output
+        auto it = std::lower_bound(ins.begin(), ins.end(), o, by_addr);
+        for (auto jt = (it == ins.begin() ? it : it - 1); jt != ins.end() && jt->p < (const char *)o.p + o.bytes; ++jt)
+            if (overlap(o, *jt)) return fail(LN_ERR_ALIASING, "an instance's output overlaps an input");
+        // inputs that start before o and reach into it
+        for (auto jt = ins.begin(); jt != it; ++jt)
+            if (overlap(o, *jt)) return fail(LN_ERR_ALIASING, "an instance's output overlaps an input");
+    }
+    if (bp.total_tiles > 0x7fffffffLL || bp.total_pack_tiles > 0x7fffffffLL)
+        return fail(LN_ERR_INVALID_VALUE, "batch too large");
+    return LN_SUCCESS;
+}
+
+size_t batch_pack_bytes(bool two, int count, const ln_sym_desc *h, int P) {
+    size_t b = 0;
+    for (int i = 0; i < count; ++i) {
+        if (h[i].n == 0) continue;
+        size_t one = packed_bytes(ceil_div(h[i].n, PK_ROWS), ceil_div(h[i].k, PK_K), P);
+        b += one * (two ? 2 : 1);
+    }
+    return b;
+}
+
+void plan_batch(Ws &w, bool two, int count, const ln_sym_desc *h, ln_form form, ln_precision prec, BatchPlan &bp) {
+    if (form != LN_FORM_INTERNALIZED) return;
+    bp.tile_prefix = w.take<int>(sizeof(int) * (count + 1));
+    if (!tensor_prec(prec)) return;
+    bp.probs = w.take<UmmaProblem>(sizeof(UmmaProblem) * (size_t)std::max(count, 1));
+    bp.pack_off = w.take<long long>(sizeof(long long) * 2 * (size_t)std::max(count, 1));
+    bp.pack_prefix = w.take<int>(sizeof(int) * (count + 1));
+    bp.order = w.take<int>(sizeof(int) * (size_t)std::max(count, 1));
+    bp.queue = w.take<int>(sizeof(int));
+    bp.pack = w.take<char>(batch_pack_bytes(two, count, h, prec_terms(prec)));
+}
+
+ln_status run_batch(bool two, ln_fill fill, int count, const ln_sym_desc *h, const ln_sym_desc *d, float alpha,
+                    float beta, void *ws, size_t wsb, ln_form form, ln_precision prec, cudaStream_t st) {
+    LN_TRY(check_form(form, prec));
+    if (fill != LN_FILL_FULL && fill != LN_FILL_LOWER && fill != LN_FILL_UPPER)
+        return fail(LN_ERR_INVALID_VALUE, "unknown fill %d", (int)fill);
+    BatchPlan bp;
+    LN_TRY(validate_batch(two, count, h, bp));
+    if (count == 0 || bp.max_n == 0) return LN_SUCCESS;
+    if (!d) return fail(LN_ERR_INVALID_VALUE, "NULL device descriptor array");
+    for (int i = 0; i < count; ++i)
+        if (h[i].n > 0 && h[i].k == 0) {
+            // k == 0 instances only scale C; not worth a special path in the batched kernels
+            return fail(LN_ERR_UNSUPPORTED, "batched call with an instance of k == 0 (instance %d)", i);
+        }
+    Ws count_ws(nullptr);
+    BatchPlan tmp = bp;
+    plan_batch(count_ws, two, count, h, form, prec, tmp);
+    LN_TRY(check_ws(ws, wsb, count_ws.off));
+    Ws w(ws);
+    plan_batch(w, two, count, h, form, prec, bp);
+    if (form == LN_FORM_PLAIN) return plain_sym_batched(two, count, d, bp.max_n, fill, alpha, beta, st);
+    if (!tensor_prec(prec)) {
+        LN_TRY(simt_sym_batched_prefix(count, d, bp.tile_prefix, st));
+        return simt_sym_batched(two, count, d, bp.tile_prefix, (int)bp.total_tiles, fill, alpha, beta, st);
+    }
+    const int P = prec_terms(prec);
+    LN_TRY(sym_batched_plan(two, count, d, fill, alpha, beta, bp.probs, bp.tile_prefix, bp.pack_off, bp.pack_prefix,
+                            bp.order, bp.pack, P, st));
+    LN_TRY(sym_batched_pack(two, count, d, bp.pack_off, bp.pack_prefix, bp.order, (int)bp.total_pack_tiles, bp.pack,
+                            P, st));
+    return umma_contract_batched(bp.probs, bp.tile_prefix, count, (int)bp.total_tiles, bp.queue, P, st);
+}
+
+// ------------------------------------------------------------------ backward
+struct ChainBwdPlan {
+    float *BC = nullptr, *GCt = nullptr, *T = nullptr;
+    ContractPlan c;  // sized for the largest of the contractions, reused in stream order
+};
+
+void plan_chain_bwd(Ws &w, int ni, int nj, int nk, int nl, ln_form form, ln_precision prec, ChainBwdPlan &p) {
+    p.BC = w.take<float>(sizeof(float) * (size_t)nk * nl);
+    p.GCt = w.take<float>(sizeof(float) * (size_t)ni * nj);
+    p.T = w.take<float>(sizeof(float) * (size_t)ni * nj);
+    if (form == LN_FORM_INTERNALIZED && tensor_prec(prec)) {
+        // contractions (M, N, K): BC (nk,nl,nj), dA (ni,nk,nl), GCt (ni,nj,nl), dB (nk,nj,ni), T (ni,nj,nk), dC (nj,nl,ni)
+        const int P = prec_terms(prec);
+        size_t best = 0;
+        int dims[6][3] = {{nk, nl, nj}, {ni, nk, nl}, {ni, nj, nl}, {nk, nj, ni}, {ni, nj, nk}, {nj, nl, ni}};
+        for (auto &d : dims) {
+            size_t b = packed_bytes(ceil_div(d[0], PK_ROWS), ceil_div(d[2], PK_K), P) +
+                       packed_bytes(ceil_div(d[1], PK_ROWS), ceil_div(d[2], PK_K), P);
+            best = std::max(best, b);
+        }
+        p.c.px = w.take<char>(best);
+    }
+}
+
+ln_status contract_into(int M, int N, int K, Operand a, Operand b, const EpiParams &e, ln_form form, ln_precision prec,
+                        char *pack_area, cudaStream_t st) {
+    ContractPlan cp;
+    if (form == LN_FORM_INTERNALIZED && tensor_prec(prec)) {
+        const int P = prec_terms(prec);
+        cp.mt = (int)ceil_div(M, PK_ROWS);
+        cp.nt = (int)ceil_div(N, PK_ROWS);
+        cp.kt = (int)ceil_div(K, PK_K);
+        cp.px = pack_area;
+        cp.py = pack_area + packed_bytes(cp.mt, cp.kt, P);
+    }
+    return run_contract(M, N, K, a, b, e, form, prec, cp, st);
+}
+
+struct CovBwdPlan {
+    double *mean = nullptr, *ss = nullptr, *partials = nullptr;
+    float *hi = nullptr, *lo = nullptr, *rs = nullptr;
+    float *Z = nullptr, *Ws_ = nullptr, *dZ = nullptr;
+    char *pack = nullptr;
+};
+
+void plan_cov_bwd(Ws &w, bool corr, int n, int m, ln_form form, ln_precision prec, CovBwdPlan &p) {
+    p.mean = w.take<double>(sizeof(double) * m);
+    p.ss = w.take<double>(sizeof(double) * m);
+    p.hi = w.take<float>(sizeof(float) * m);
+    p.lo = w.take<float>(sizeof(float) * m);
+    p.rs = w.take<float>(sizeof(float) * m);
+    p.partials = w.take<double>(std::max(col_stats_partials_bytes(n, m), corr_bwd_partials_bytes(n, m)));
+    p.Z = w.take<float>(sizeof(float) * (size_t)n * m);
+    p.Ws_ = w.take<float>(sizeof(float) * (size_t)m * m);
+    if (corr) p.dZ = w.take<float>(sizeof(float) * (size_t)n * m);
+    if (form == LN_FORM_INTERNALIZED && tensor_prec(prec)) {
+        const int P = prec_terms(prec);
+        p.pack = w.take<char>(packed_bytes(ceil_div(n, PK_ROWS), ceil_div(m, PK_K), P) +
+                              packed_bytes(ceil_div(m, PK_ROWS), ceil_div(m, PK_K), P));
+    }
+}
+
+__global__ void k_copy_stats(int m, const double *src, double *mean, double *ss) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) {
+        mean[j] = src[j];
+        ss[j] = src[m + j];
+    }
+}
+
+ln_status run_cov_bwd(bool corr, int n, int m, const float *X, int ldx, const float *W, int ldw, const double *stats,
+                      float *dX, int lddx, void *ws, size_t wsb, ln_form form, ln_precision prec, cudaStream_t st) {
+    LN_TRY(check_dims({n, m}));
+    LN_TRY(check_form(form, prec));
+    if (m == 0 || n == 0) return LN_SUCCESS;
+    if (n < 2) return fail(LN_ERR_INVALID_VALUE, "nsamples >= 2 required (got %d)", n);
+    if (!X || !W || !dX) return fail(LN_ERR_INVALID_VALUE, "NULL operand");
+    if (ldx < m || ldw < m || lddx < m) return fail(LN_ERR_INVALID_VALUE, "leading dimension too small");
+    Span so = mspan(dX, n, m, lddx);
+    if (overlap(so, mspan(X, n, m, ldx)) || overlap(so, mspan(W, m, m, ldw)) ||
+        (stats && overlap(so, {stats, sizeof(double) * 2 * (size_t)m})))
+        return fail(LN_ERR_ALIASING, "dX overlaps an input");
+    Ws count(nullptr);
+    CovBwdPlan p;
+    plan_cov_bwd(count, corr, n, m, form, prec, p);
+    LN_TRY(check_ws(ws, wsb, count.off));
+    Ws w(ws);
+    plan_cov_bwd(w, corr, n, m, form, prec, p);
+
+    if (stats) {
+        {
+            LaunchScope ls(FAM_STATS, st);
+            k_copy_stats<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(m, stats, p.mean, p.ss);
+        }
+        LN_TRY(check_launch("copy statistics"));
+        LN_TRY(stats_derive(m, p.mean, p.ss, p.hi, p.lo, p.rs, st));
+    } else if (form == LN_FORM_PLAIN) {
+        LN_TRY(plain_col_stats(n, m, X, ldx, p.mean, p.ss, st));
+        LN_TRY(stats_derive(m, p.mean, p.ss, p.hi, p.lo, p.rs, st));
+    } else {
+        LN_TRY(col_stats(n, m, X, ldx, p.mean, p.ss, p.hi, p.lo, p.rs, p.partials, st));
+    }
+    // Z = Xc (covariance) or Xc * diag(1/s) (correlation), recomputed from X
+    LN_TRY(center_matrix(n, m, X, ldx, p.hi, p.lo, corr ? p.rs : nullptr, p.Z, m, st));
+    LN_TRY(symmetrize_weights(m, W, ldw, corr ? 1.0f : (float)(1.0 / (double)(n - 1)), corr ? 1 : 0, p.Ws_, st));
+    Operand z{p.Z, m, 0}, wsop{p.Ws_, m, 0};
+    if (!corr) return contract_into(n, m, m, z, wsop, epi_store(n, m, 1.0f, dX, lddx), form, prec, p.pack, st);
+    LN_TRY(contract_into(n, m, m, z, wsop, epi_store(n, m, 1.0f, p.dZ, m), form, prec, p.pack, st));
+    return corr_bwd_finish(n, m, p.Z, m, p.dZ, m, p.rs, dX, lddx, p.partials, st);
+}
+
+}  // namespace
+
+}  // namespace ln
+
+// ====================================================================== C ABI
+using namespace ln;
+
+extern "C" {
+
+const char *ln_get_last_error(void) { return g_msg; }
+
+const char *ln_status_string(ln_status s) {
+    switch (s) {
+        case LN_SUCCESS: return "LN_SUCCESS";
+        case LN_ERR_INVALID_VALUE: return "LN_ERR_INVALID_VALUE";
+        case LN_ERR_ALIASING: return "LN_ERR_ALIASING";
+        case LN_ERR_MISALIGNED: return "LN_ERR_MISALIGNED";
+        case LN_ERR_UNSUPPORTED: return "LN_ERR_UNSUPPORTED";
+        case LN_ERR_CUDA: return "LN_ERR_CUDA";
+        case LN_ERR_TIMEOUT: return "LN_ERR_TIMEOUT";
+        case LN_ERR_WORKSPACE: return "LN_ERR_WORKSPACE";
+    }
+    return "LN_UNKNOWN_STATUS";
+}
+
+int ln_version(void) { return 100; }
+
+long long ln_launch_count(void) { return g_launches.load(); }
+
+ln_status ln_timing_enable(int on) {
+    clear_error();
+    g_timing.on = on != 0;
+    return LN_SUCCESS;
+}
+
+ln_status ln_timing_read(const char *family, double *total_ms, int *launches) {
+    clear_error();
+    if (!family || !total_ms || !launches) return fail(LN_ERR_INVALID_VALUE, "NULL argument");
+    int f = -1;
+    for (int i = 0; i < FAM_COUNT; ++i)
+        if (strcmp(family, kFamilies[i]) == 0) f = i;
+    if (f < 0) return fail(LN_ERR_INVALID_VALUE, "unknown kernel family '%s'", family);
+    double total = 0.0;
+    int n = 0;
+    for (auto &ev : g_timing.pending[f]) {
+        LN_CUDA_TRY(cudaEventSynchronize(ev.second));
+        float ms = 0.0f;
+        LN_CUDA_TRY(cudaEventElapsedTime(&ms, ev.first, ev.second));
+        total += ms;
+        ++n;
+        g_timing.pool.push_back(ev);
+    }
+    g_timing.pending[f].clear();
+    *total_ms = total;
+    *launches = n;
+    return LN_SUCCESS;
+}
+
+ln_status ln_stream_check(void *stream) {
+    clear_error();
+    cudaError_t e = cudaStreamSynchronize(S(stream));
+    if (e != cudaSuccess) return fail(LN_ERR_CUDA, "stream error: %s", cudaGetErrorString(e));
+    int v = 0;
+    LN_TRY(umma_read_error(&v));
+    if (v) return fail(LN_ERR_TIMEOUT, "a bounded device wait ran out (roles 0x%x)", v);
+    return LN_SUCCESS;
+}
+
+// ------------------------------------------------------------------ GEMM
+ln_status ln_gemm_workspace_size(int M, int N, int K, ln_form form, ln_precision prec, size_t *bytes) {
+    clear_error();
+    LN_TRY(check_dims({M, N, K}));
+    LN_TRY(check_form(form, prec));
+    if (!bytes) return fail(LN_ERR_INVALID_VALUE, "NULL bytes");
+    Ws w(nullptr);
+    ContractPlan cp;
+    plan_contract(w, M, N, K, form, prec, cp);
+    *bytes = w.off;
+    return LN_SUCCESS;
+}
+
+ln_status ln_gemm(int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb, float beta,
+                  float *C, int ldc, void *ws, size_t wsb, ln_form form, ln_precision prec, void *stream) {
+    clear_error();
+    LN_TRY(check_dims({M, N, K}));
+    LN_TRY(check_form(form, prec));
+    if (M == 0 || N == 0) return LN_SUCCESS;
+    if (!C || (K > 0 && (!A || !B))) return fail(LN_ERR_INVALID_VALUE, "NULL operand");
+    if (ldc < N || (K > 0 && (lda < K || ldb < N))) return fail(LN_ERR_INVALID_VALUE, "leading dimension too small");
+    Span sc = mspan(C, M, N, ldc);
+    if (overlap(sc, mspan(A, M, K, lda)) || overlap(sc, mspan(B, K, N, ldb)))
+        return fail(LN_ERR_ALIASING, "C overlaps A or B");
+    if (K == 0) return scale_matrix(M, N, beta, C, ldc, S(stream));
+    Ws count(nullptr);
+    ContractPlan cp;
+    plan_contract(count, M, N, K, form, prec, cp);
+    LN_TRY(check_ws(ws, wsb, count.off));
+    Ws w(ws);
+    plan_contract(w, M, N, K, form, prec, cp);
+    return run_contract(M, N, K, {A, lda, 0}, {B, ldb, 0}, epi_gemm(M, N, alpha, beta, C, ldc), form, prec, cp,
+                        S(stream));
+}
+
+// ------------------------------------------------------------------ chain
+ln_status ln_gemm_chain_workspace_size(int ni, int nj, int nk, int nl, ln_form form, ln_precision prec,
+                                       size_t *bytes) {
+    clear_error();
+    LN_TRY(check_dims({ni, nj, nk, nl}));
+    LN_TRY(check_form(form, prec));
+    if (!bytes) return fail(LN_ERR_INVALID_VALUE, "NULL bytes");
+    Ws w(nullptr);
+    ChainPlan p;
+    plan_chain(w, ni, nj, nk, nl, form, prec, p);
+    *bytes = w.off;
+    return LN_SUCCESS;
+}
+
+ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float *A, const float *B, const float *C,
+                        float beta, const float *D, float *E, float *F, void *ws, size_t wsb, ln_form form,
+                        ln_precision prec, void *stream) {
+    clear_error();
+    LN_TRY(check_dims({ni, nj, nk, nl}));
+    LN_TRY(check_form(form, prec));
+    if (ni == 0 || nl == 0) return LN_SUCCESS;
+    if (!E || !F || (nk > 0 && nj > 0 && (!A || !B || !C)) || (beta != 0.0f && !D))
+        return fail(LN_ERR_INVALID_VALUE, "NULL operand");
+    Span se = mspan(E, ni, nl, nl), sf = mspan(F, ni, nl, nl);
+    Span ins[4] = {mspan(A, ni, nk, nk), mspan(B, nk, nj, nj), mspan(C, nj, nl, nl),
+                   mspan(beta != 0.0f ? D : nullptr, ni, nl, nl)};
+    if (overlap(se, sf)) return fail(LN_ERR_ALIASING, "E overlaps F");
+    for (const Span &s : ins)
+        if (overlap(se, s) || overlap(sf, s)) return fail(LN_ERR_ALIASING, "E or F overlaps an input");
+    cudaStream_t st = S(stream);
+    EpiParams ef{};
+    ef.mode = EPI_EF;
+    ef.M = ni;
+    ef.N = nl;
+    ef.alpha = alpha;
+    ef.beta = beta;
+    ef.D = D;
+    ef.E = E;
+    ef.F = F;
+    ef.ld_ef = nl;
+    if (nk == 0 || nj == 0)  // T = 0, so E = 0 and F = beta * D
+        return plain_gemm(ni, nl, 0, nullptr, 0, 0, nullptr, 0, 0, ef, st);
+    Ws count(nullptr);
+    ChainPlan p;
+    plan_chain(count, ni, nj, nk, nl, form, prec, p);
+    LN_TRY(check_ws(ws, wsb, count.off));
+    Ws w(ws);
+    plan_chain(w, ni, nj, nk, nl, form, prec, p);
+    LN_TRY(run_contract(ni, nj, nk, {A, nk, 0}, {B, nj, 0}, epi_store(ni, nj, 1.0f, p.T, nj), form, prec, p.c1, st));
+    return run_contract(ni, nl, nj, {p.T, nj, 0}, {C, nl, 0}, ef, form, prec, p.c2, st);
+}
+
+// ------------------------------------------------------------------ statistics, covariance, correlation
+ln_status ln_col_stats_workspace_size(int nsamples, int nfeat, ln_form form, size_t *bytes) {
+    clear_error();
+    LN_TRY(check_dims({nsamples, nfeat}));
+    LN_TRY(check_form(form, LN_PREC_FP32));
+    if (!bytes) return fail(LN_ERR_INVALID_VALUE, "NULL bytes");
+    *bytes = form == LN_FORM_INTERNALIZED ? align_up(col_stats_partials_bytes(nsamples, nfeat), 256) : 0;
+    return LN_SUCCESS;
+}
+
+ln_status ln_col_stats(int nsamples, int nfeat, const float *X, int ldx, double *mean, double *ss, void *ws,
+                       size_t wsb, ln_form form, void *stream) {
+    clear_error();
+    LN_TRY(check_dims({nsamples, nfeat}));
+    LN_TRY(check_form(form, LN_PREC_FP32));
+    if (nfeat == 0) return LN_SUCCESS;
+    if (nsamples < 1) return fail(LN_ERR_INVALID_VALUE, "nsamples >= 1 required");
+    if (!X || !mean || !ss) return fail(LN_ERR_INVALID_VALUE, "NULL operand");
+    if (ldx < nfeat) return fail(LN_ERR_INVALID_VALUE, "ldx smaller than nfeat");
+    Span sx = mspan(X, nsamples, nfeat, ldx);
+    Span sm = {mean, sizeof(double) * (size_t)nfeat}, sq = {ss, sizeof(double) * (size_t)nfeat};
+    if (overlap(sm, sx) || overlap(sq, sx) || overlap(sm, sq)) return fail(LN_ERR_ALIASING, "outputs overlap");
+    if (form == LN_FORM_PLAIN) return plain_col_stats(nsamples, nfeat, X, ldx, mean, ss, S(stream));
+    LN_TRY(check_ws(ws, wsb, align_up(col_stats_partials_bytes(nsamples, nfeat), 256)));
+    return col_stats(nsamples, nfeat, X, ldx, mean, ss, nullptr, nullptr, nullptr, static_cast<double *>(ws),
+                     S(stream));
+}
+
+ln_status ln_covariance_workspace_size(int nsamples, int nfeat, ln_form form, ln_precision prec, size_t *bytes) {
+    clear_error();
+    LN_TRY(check_dims({nsamples, nfeat}));
+    LN_TRY(check_form(form, prec));
+    if (!bytes) return fail(LN_ERR_INVALID_VALUE, "NULL bytes");
+    Ws w(nullptr);
+    CovPlan p;
+    plan_cov(w, nsamples, nfeat, form, prec, p);
+    *bytes = w.off;
+    return LN_SUCCESS;
+}
+
+ln_status ln_covariance(int nsamples, int nfeat, const float *X, int ldx, float *cov, int ldcov, void *ws, size_t wsb,
+                        ln_form form, ln_precision prec, void *stream) {
+    clear_error();
+    return run_cov(false, nsamples, nfeat, X, ldx, cov, ldcov, ws, wsb, form, prec, S(stream));
+}
+
+ln_status ln_correlation(int nsamples, int nfeat, const float *X, int ldx, float *corr, int ldcorr, void *ws,
+                         size_t wsb, ln_form form, ln_precision prec, void *stream) {
+    clear_error();
+    return run_cov(true, nsamples, nfeat, X, ldx, corr, ldcorr, ws, wsb, form, prec, S(stream));
+}
+
+// ------------------------------------------------------------------ SYRK / SYR2K
+ln_status ln_syrk_workspace_size(int n, int k, ln_form form, ln_precision prec, size_t *bytes) {
+    clear_error();
+    LN_TRY(check_dims({n, k}));
+    LN_TRY(check_form(form, prec));
+    if (!bytes) return fail(LN_ERR_INVALID_VALUE, "NULL bytes");
+    Ws w(nullptr);
+    SymPlan p;
+    plan_sym(w, false, n, k, form, prec, p);
+    *bytes = w.off;
+    return LN_SUCCESS;
+}
+
+ln_status ln_syr2k_workspace_size(int n, int k, ln_form form, ln_precision prec, size_t *bytes) {
+    clear_error();
+    LN_TRY(check_dims({n, k}));
+    LN_TRY(check_form(form, prec));
+    if (!bytes) return fail(LN_ERR_INVALID_VALUE, "NULL bytes");
+    Ws w(nullptr);
+    SymPlan p;
+    plan_sym(w, true, n, k, form, prec, p);
+    *bytes = w.off;
+    return LN_SUCCESS;
+}
+
+ln_status ln_syrk(ln_fill fill, int n, int k, float alpha, const float *A, int lda, float beta, float *C, int ldc,
+                  void *ws, size_t wsb, ln_form form, ln_precision prec, void *stream) {
+    clear_error();
+    return run_sym(false, fill, n, k, alpha, A, lda, nullptr, 0, beta, C, ldc, ws, wsb, form, prec, S(stream));
+}
+
+ln_status ln_syr2k(ln_fill fill, int n, int k, float alpha, const float *A, int lda, const float *B, int ldb,
+                   float beta, float *C, int ldc, void *ws, size_t wsb, ln_form form, ln_precision prec,
+                   void *stream) {
+    clear_error();
+    return run_sym(true, fill, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, wsb, form, prec, S(stream));
+}
+
+// ------------------------------------------------------------------ batched
+static ln_status batched_ws(bool two, int count, const ln_sym_desc *h, ln_form form, ln_precision prec,
+                            size_t *bytes) {
+    clear_error();
+    LN_TRY(check_form(form, prec));
+    if (!bytes) return fail(LN_ERR_INVALID_VALUE, "NULL bytes");
+    BatchPlan bp;
+    LN_TRY(validate_batch(two, count, h, bp));
+    Ws w(nullptr);
+    plan_batch(w, two, count, h, form, prec, bp);
+    *bytes = w.off;
+    return LN_SUCCESS;
+}
+
+ln_status ln_syrk_batched_workspace_size(int count, const ln_sym_desc *h, ln_form form, ln_precision prec,
+                                         size_t *bytes) {
+    return batched_ws(false, count, h, form, prec, bytes);
+}
+
+ln_status ln_syr2k_batched_workspace_size(int count, const ln_sym_desc *h, ln_form form, ln_precision prec,
+                                          size_t *bytes) {
+    return batched_ws(true, count, h, form, prec, bytes);
+}
+
+ln_status ln_syrk_batched(ln_fill fill, int count, const ln_sym_desc *h, const ln_sym_desc *d, float alpha, float beta,
+                          void *ws, size_t wsb, ln_form form, ln_precision prec, void *stream) {
+    clear_error();
+    return run_batch(false, fill, count, h, d, alpha, beta, ws, wsb, form, prec, S(stream));
+}
+
+ln_status ln_syr2k_batched(ln_fill fill, int count, const ln_sym_desc *h, const ln_sym_desc *d, float alpha,
+                           float beta, void *ws, size_t wsb, ln_form form, ln_precision prec, void *stream) {
+    clear_error();
+    return run_batch(true, fill, count, h, d, alpha, beta, ws, wsb, form, prec, S(stream));
+}
+
+// ------------------------------------------------------------------ backward
+ln_status ln_gemm_chain_bwd_workspace_size(int ni, int nj, int nk, int nl, ln_form form, ln_precision prec,
+                                           size_t *bytes) {
+    clear_error();
+    LN_TRY(check_dims({ni, nj, nk, nl}));
+    LN_TRY(check_form(form, prec));
+    if (!bytes) return fail(LN_ERR_INVALID_VALUE, "NULL bytes");
+    Ws w(nullptr);
+    ChainBwdPlan p;
+    plan_chain_bwd(w, ni, nj, nk, nl, form, prec, p);
+    *bytes = w.off;
+    return LN_SUCCESS;
+}
+
+ln_status ln_gemm_chain_bwd(int ni, int nj, int nk, int nl, const float *A, const float *B, const float *C,
+                            const float *G, float *dA, float *dB, float *dC, void *ws, size_t wsb, ln_form form,
+                            ln_precision prec, void *stream) {
+    clear_error();
+    LN_TRY(check_dims({ni, nj, nk, nl}));
+    LN_TRY(check_form(form, prec));
+    if (!A || !B || !C || !G || !dA || !dB || !dC) return fail(LN_ERR_INVALID_VALUE, "NULL operand");
+    Span outs[3] = {mspan(dA, ni, nk, nk), mspan(dB, nk, nj, nj), mspan(dC, nj, nl, nl)};
+    Span ins[4] = {mspan(A, ni, nk, nk), mspan(B, nk, nj, nj), mspan(C, nj, nl, nl), mspan(G, ni, nl, nl)};
+    for (int i = 0; i < 3; ++i) {
+        for (int j = i + 1; j < 3; ++j)
+            if (overlap(outs[i], outs[j])) return fail(LN_ERR_ALIASING, "gradient outputs overlap");
+        for (const Span &s : ins)
+            if (overlap(outs[i], s)) return fail(LN_ERR_ALIASING, "a gradient output overlaps an input");
+    }
+    Ws count(nullptr);
+    ChainBwdPlan p;
+    plan_chain_bwd(count, ni, nj, nk, nl, form, prec, p);
+    LN_TRY(check_ws(ws, wsb, count.off));
+    Ws w(ws);
+    plan_chain_bwd(w, ni, nj, nk, nl, form, prec, p);
+    cudaStream_t st = S(stream);
+    char *pk = p.c.px;
+    // BC = B C (nk x nl); dA = G BC^T
+    LN_TRY(contract_into(nk, nl, nj, {B, nj, 0}, {C, nl, 0}, epi_store(nk, nl, 1.0f, p.BC, nl), form, prec, pk, st));
+    LN_TRY(contract_into(ni, nk, nl, {G, nl, 0}, {p.BC, nl, 1}, epi_store(ni, nk, 1.0f, dA, nk), form, prec, pk, st));
+    // GCt = G C^T (ni x nj); dB = A^T GCt
+    LN_TRY(contract_into(ni, nj, nl, {G, nl, 0}, {C, nl, 1}, epi_store(ni, nj, 1.0f, p.GCt, nj), form, prec, pk, st));
+    LN_TRY(contract_into(nk, nj, ni, {A, nk, 1}, {p.GCt, nj, 0}, epi_store(nk, nj, 1.0f, dB, nj), form, prec, pk, st));
+    // T = A B (ni x nj); dC = T^T G
+    LN_TRY(contract_into(ni, nj, nk, {A, nk, 0}, {B, nj, 0}, epi_store(ni, nj, 1.0f, p.T, nj), form, prec, pk, st));
+    return contract_into(nj, nl, ni, {p.T, nj, 1}, {G, nl, 0}, epi_store(nj, nl, 1.0f, dC, nl), form, prec, pk, st);
+}
+
+ln_status ln_covariance_bwd_workspace_size(int nsamples, int nfeat, ln_form form, ln_precision prec, size_t *bytes) {
+    clear_error();
+    LN_TRY(check_dims({nsamples, nfeat}));
+    LN_TRY(check_form(form, prec));
+    if (!bytes) return fail(LN_ERR_INVALID_VALUE, "NULL bytes");
+    Ws w(nullptr);
+    CovBwdPlan p;
+    plan_cov_bwd(w, true, nsamples, nfeat, form, prec, p);  // the correlation plan covers both
+    *bytes = w.off;
+    return LN_SUCCESS;
+}
+
+ln_status ln_covariance_bwd(int nsamples, int nfeat, const float *X, int ldx, const float *W, int ldw,
+                            const double *stats, float *dX, int lddx, void *ws, size_t wsb, ln_form form,
+                            ln_precision prec, void *stream) {
+    clear_error();
+    return run_cov_bwd(false, nsamples, nfeat, X, ldx, W, ldw, stats, dX, lddx, ws, wsb, form, prec, S(stream));
+}
+
+ln_status ln_correlation_bwd(int nsamples, int nfeat, const float *X, int ldx, const float *W, int ldw,
+                             const double *stats, float *dX, int lddx, void *ws, size_t wsb, ln_form form,
+                             ln_precision prec, void *stream) {
+    clear_error();
+    return run_cov_bwd(true, nsamples, nfeat, X, ldx, W, ldw, stats, dX, lddx, ws, wsb, form, prec, S(stream));
+}
+
+}  // extern "C"

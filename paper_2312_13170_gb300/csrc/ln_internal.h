@@ -1,0 +1,194 @@
+// Internal declarations of libloopnest: error reporting, the epilogue
+// description shared by every contraction engine, the packed tensor-core
+// operand format, and the host-side launchers of each translation unit.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "loopnest.h"
+
+namespace ln {
+
+// ------------------------------------------------------------------ errors
+ln_status fail(ln_status s, const char *fmt, ...);
+void clear_error();
+
+#define LN_CUDA_TRY(expr)                                                                     \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess) return ::ln::fail(LN_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Check for a launch error right after <<<>>>.
+ln_status check_launch(const char *what);
+
+// Launch accounting (ln_launch_count / ln_timing_*): construct one of these
+// right before a kernel launch; it counts the launch and, while timing is
+// enabled, records start/stop events around it on the launch stream.
+enum Family : int { FAM_UMMA = 0, FAM_PACK, FAM_SIMT, FAM_PLAIN, FAM_STATS, FAM_COUNT };
+struct LaunchScope {
+    LaunchScope(Family f, cudaStream_t st);
+    ~LaunchScope();
+    int slot;
+    cudaStream_t st;
+    Family f;
+};
+
+int sm_count();
+
+// ------------------------------------------------------------------ epilogue
+// What a contraction engine does with the accumulated value acc(i, j) of the
+// logical output element (i, j). Every engine (plain, FP32 SIMT, tcgen05)
+// funnels its results through the same description, so the three forms agree
+// on alpha/beta, fill and scaling semantics by construction.
+enum EpiMode : int {
+    EPI_GEMM = 0,  // C[i][j] = alpha*acc + beta*C[i][j]
+    EPI_EF = 1,    // E[i][j] = acc; F[i][j] = alpha*acc + beta*D[i][j]
+    EPI_SYM = 2,   // symmetric output, see SymKind; only i >= j is produced
+    EPI_STORE = 3  // C[i][j] = alpha*acc (no read of C)
+};
+enum SymKind : int {
+    SYM_AXPBY = 0,  // alpha*acc + beta*C on the requested fill (SYRK/SYR2K)
+    SYM_SCALE = 1,  // alpha*acc, full matrix written (covariance, alpha = 1/(n-1))
+    SYM_CORR = 2    // acc*rs[i]*rs[j] for i != j, 1 on the diagonal, full matrix
+};
+
+struct EpiParams {
+    int mode;
+    int M, N;  // logical output extent
+    float alpha, beta;
+    float *C;
+    long long ldc;
+    const float *D;
+    float *E, *F;
+    long long ld_ef;
+    int fill;      // ln_fill, for EPI_SYM
+    int sym_kind;  // SymKind
+    const float *rs;
+};
+
+// ------------------------------------------------------------------ packed tensor-core operands
+// A packed operand holds a logical matrix R (rows x K) as tiles of 128 rows by
+// 64 K-elements, each tile one 16 KiB block per BF16 split term, laid out the
+// way tcgen05.mma reads a K-major operand with 128-byte swizzling:
+//   tile (rt, kt, term) at byte ((rt * KT + kt) * P + term) * 16384,
+//   element (r, k) of the tile in row r, 16-byte chunk c = k / 8, stored at
+//   chunk position c ^ (r % 8) of that row (128 bytes per row).
+// Rows >= rows and k >= K are zero. Because the layout in global memory is the
+// layout in shared memory, one bulk copy moves a tile (no tensor map needed).
+constexpr int PK_ROWS = 128;
+constexpr int PK_K = 64;
+constexpr int PK_TILE_BYTES = PK_ROWS * PK_K * 2;
+
+inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+inline int prec_terms(ln_precision p) {
+    switch (p) {
+        case LN_PREC_BF16: return 1;
+        case LN_PREC_3XBF16: return 2;
+        case LN_PREC_6XBF16: return 3;
+        default: return 0;
+    }
+}
+
+// bytes of a packed operand with `rt` row tiles and `kt` k tiles
+inline size_t packed_bytes(long long rt, long long kt, int terms) {
+    return (size_t)(rt * kt * terms) * PK_TILE_BYTES;
+}
+
+struct PackSrc {
+    const float *S;  // source matrix
+    long long ld;
+    int trans;       // 0: element (r,k) = S[r*ld+k]; 1: element (r,k) = S[k*ld+r]
+    int rows, K;     // logical extent
+    const float *off_hi, *off_lo;  // optional per-row centring, v = (x - hi) - lo
+    char *dst;       // packed destination
+    int rt, kt;      // tile counts of the destination (>= ceil(rows/128), ceil(K/64))
+};
+
+// ------------------------------------------------------------------ launchers (one per .cu)
+// ln_plain.cu
+ln_status plain_gemm(int M, int N, int K, const float *A, long long sai, long long sak, const float *B,
+                     long long sbk, long long sbj, const EpiParams &epi, cudaStream_t st);
+ln_status plain_col_stats(int n, int m, const float *X, long long ldx, double *mean, double *ss, cudaStream_t st);
+ln_status plain_cov(int n, int m, const float *X, long long ldx, const double *mean, const EpiParams &epi,
+                    cudaStream_t st);
+ln_status plain_sym(int n, int k, const float *A, long long lda, const float *B, long long ldb,
+                    const EpiParams &epi, cudaStream_t st);
+
+// ln_simt.cu: FP32 shared-memory tiled contraction
+//   acc(i,j) = sum_seg sum_k opA_seg(i,k) * opB_seg(k,j)
+//   opA(i,k) = A[i*lda+k] (a_t == 0, A is M x K) or A[k*lda+i] (a_t == 1), minus a_off[i]
+//   opB(k,j) = B[k*ldb+j] (b_t == 0, B is K x N) or B[j*ldb+k] (b_t == 1), minus b_off[j]
+struct SimtOperands {
+    const float *A[2];
+    const float *B[2];
+    long long lda[2], ldb[2];  // per segment
+    int a_t, b_t;
+    int nseg;
+    const float *a_off_hi, *a_off_lo, *b_off_hi, *b_off_lo;
+};
+ln_status simt_contract(int M, int N, int K, const SimtOperands &op, const EpiParams &epi, cudaStream_t st);
+
+// ln_stats.cu
+// Two-pass column statistics; also writes the centring split (hi, lo) of the
+// mean and rs = 1/sqrt(ss) as floats when those pointers are non-null.
+ln_status col_stats(int n, int m, const float *X, long long ldx, double *mean, double *ss, float *off_hi,
+                    float *off_lo, float *rs, double *partials, cudaStream_t st);
+size_t col_stats_partials_bytes(int n, int m);
+ln_status stats_derive(int m, const double *mean, const double *ss, float *off_hi, float *off_lo, float *rs,
+                       cudaStream_t st);
+ln_status scale_matrix(int M, int N, float beta, float *C, long long ldc, cudaStream_t st);
+ln_status sym_fill_zero_k(int n, int fill, float beta, float *C, long long ldc, cudaStream_t st);
+ln_status center_matrix(int n, int m, const float *X, long long ldx, const float *off_hi, const float *off_lo,
+                        const float *rs, float *Y, long long ldy, cudaStream_t st);
+ln_status symmetrize_weights(int m, const float *W, long long ldw, float scale, int zero_diag, float *Ws,
+                             cudaStream_t st);
+ln_status corr_bwd_finish(int n, int m, const float *Z, long long ldz, const float *dZ, long long lddz,
+                          const float *rs, float *dX, long long lddx, double *partials, cudaStream_t st);
+size_t corr_bwd_partials_bytes(int n, int m);
+
+// ln_pack.cu
+ln_status pack_operand(const PackSrc &p, int terms, cudaStream_t st);
+
+// ln_umma.cu: tcgen05 contraction over packed operands
+struct UmmaSeg {
+    const char *X;  // packed M-side operand (row tiles of 128)
+    const char *Y;  // packed N-side operand (row tiles of 128)
+};
+struct UmmaProblem {
+    UmmaSeg seg[2];
+    int nseg;
+    int kt;          // k tiles per segment
+    int x_kt, y_kt;  // k-tile pitch of the packed X and Y buffers
+    int mt, nt;      // 128-row tiles on the M side, BN-wide tiles on the N side
+    int sym;         // lower-triangle tiles only (mt == nt)
+    int inject_timeout;  // test hook: the producer issues no copy, so a bounded wait runs out
+    EpiParams epi;
+};
+// True when LN_FAULT_INJECT=timeout is set in the environment (read per call).
+bool inject_timeout_requested();
+ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st);
+ln_status umma_contract_batched(const UmmaProblem *d_probs, const int *d_tile_prefix, int nprob, int total_tiles,
+                                int *d_queue, int terms, cudaStream_t st);
+ln_status umma_read_error(int *value);
+// batched planning on the device
+// ln_pack.cu: batched layout. The plan kernel orders instances by decreasing
+// work, assigns each its packed-operand offsets, and writes its contraction
+// descriptor and tile prefix sums (rank order); the pack kernel then packs
+// every instance's operands in one launch.
+ln_status sym_batched_plan(int is_syr2k, int count, const ln_sym_desc *d_descs, int fill, float alpha, float beta,
+                           UmmaProblem *d_probs, int *d_tile_prefix, long long *d_pack_off, int *d_pack_prefix,
+                           int *d_order, char *pack_base, int terms, cudaStream_t st);
+ln_status sym_batched_pack(int is_syr2k, int count, const ln_sym_desc *d_descs, const long long *d_pack_off,
+                           const int *d_pack_prefix, const int *d_order, int total_pack_tiles, char *pack_base,
+                           int terms, cudaStream_t st);
+ln_status plain_sym_batched(int is_syr2k, int count, const ln_sym_desc *d_descs, int max_n, int fill, float alpha,
+                            float beta, cudaStream_t st);
+ln_status simt_sym_batched(int is_syr2k, int count, const ln_sym_desc *d_descs, const int *d_tile_prefix,
+                           int total_tiles, int fill, float alpha, float beta, cudaStream_t st);
+ln_status simt_sym_batched_prefix(int count, const ln_sym_desc *d_descs, int *d_tile_prefix, cudaStream_t st);
+
+}  // namespace ln

@@ -1,0 +1,536 @@
+// Internalized tensor-core form: loop internalization (paper Sec. VI-C,
+// Listing 6) on sm_103a. The work-group tile becomes a 128 x 128 CTA output
+// tile; the "prefetch one tile of each operand into local memory, barrier,
+// inner loop over the tile, barrier" sequence becomes a ring of shared-memory
+// stages filled by the bulk-copy (TMA) engine and guarded by mbarriers, and
+// the inner loop over the tile becomes tcgen05.mma instructions accumulating
+// in tensor memory (TMEM), stored once per tile (Sec. VI-B).
+//
+// Operands arrive pre-split into BF16 terms and pre-packed in the tensor
+// core's K-major 128-byte-swizzled layout (ln_pack.cu), so each stage is a
+// couple of contiguous bulk copies. The kernel is persistent: one CTA per SM
+// takes output tiles from a static stride or from a device-side queue (an
+// atomic counter), and double-buffers its TMEM accumulator so that the
+// epilogue of one tile overlaps the MMAs of the next.
+//
+// Warp roles (192 threads): warp 0 issues bulk copies, warp 1 allocates TMEM
+// and issues MMAs (one lane each), warps 2-5 read the accumulator back with
+// tcgen05.ld (each warp owns the 32 TMEM lanes = output rows its warp index
+// may access) and run the shared epilogue.
+//
+// Every mbarrier wait is bounded by the global timer: a wait that runs out
+// sets the CTA's abort flag and the library's device error word, every role
+// leaves its loop, in-flight copies and MMAs are waited for (again bounded),
+// TMEM is freed and the kernel returns. ln_stream_check() reports it.
+#include "ln_epilogue.cuh"
+#include "ln_internal.h"
+
+namespace ln {
+
+__device__ int g_umma_error;
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN = 128;
+constexpr int NTHREADS = 192;
+constexpr int SCHED = 4;
+constexpr int MAX_STAGES = 8;
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
+constexpr int CTL_BYTES = 1024;
+constexpr int SMEM_BUDGET = 227 * 1024;
+
+enum : int { ERR_PRODUCER = 1, ERR_MMA = 2, ERR_EPILOGUE = 4, ERR_DRAIN = 8 };
+
+struct Ctl {
+    uint64_t full[MAX_STAGES];
+    uint64_t empty[MAX_STAGES];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint64_t sfull[SCHED];
+    uint64_t sempty[SCHED];
+    uint64_t drain;
+    int sched[SCHED];
+    uint32_t tmem_base;
+    volatile int abort;
+};
+static_assert(sizeof(Ctl) <= CTL_BYTES, "control block too large");
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase of `b` with the given parity. With honor_abort,
+// returns false as soon as another role has aborted.
+__device__ bool wait_phase(Ctl *ctl, uint64_t *b, uint32_t parity, int who, bool honor_abort = true) {
+    if (mbar_try_wait(b, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (uint32_t n = 1;; ++n) {
+        if (mbar_try_wait(b, parity)) return true;
+        if ((n & 31) == 0) {
+            if (honor_abort && ctl->abort) return false;
+            if (gtimer() - t0 > WAIT_NS) {
+                ctl->abort = 1;
+                atomicOr(&g_umma_error, who);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(saddr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major operand with 128-byte swizzle:
+// 8-row groups 1024 bytes apart, descriptor version 1, swizzle mode 2.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M x N.
+constexpr uint32_t IDESC_BF16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(IDESC_BF16), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// ---------------------------------------------------------------- tile scheduling
+__device__ __forceinline__ void tri_tile(int t, int &ti, int &tj) {
+    int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    while (r * (r + 1) / 2 > t) --r;
+    ti = r;
+    tj = t - r * (r + 1) / 2;
+}
+
+struct TileRef {
+    const UmmaProblem *p;
+    int mi, ni;
+};
+
+template <int BATCHED>
+__device__ __forceinline__ TileRef resolve(int t, const UmmaProblem *single, const UmmaProblem *probs,
+                                           const int *prefix, int nprob) {
+    TileRef r;
+    int local = t;
+    if (BATCHED) {
+        int lo = 0, hi = nprob - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (__ldg(prefix + mid) <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        r.p = probs + lo;
+        local = t - __ldg(prefix + lo);
+    } else {
+        r.p = single;
+    }
+    if (r.p->sym) {
+        tri_tile(local, r.mi, r.ni);
+    } else {
+        r.mi = local / r.p->nt;
+        r.ni = local - r.mi * r.p->nt;
+    }
+    return r;
+}
+
+template <int P>
+struct Products;
+template <>
+struct Products<1> {
+    static constexpr int n = 1;
+    __device__ static int a(int i) { return 0; }
+    __device__ static int b(int i) { return 0; }
+};
+template <>
+struct Products<2> {  // hi*hi + hi*lo + lo*hi
+    static constexpr int n = 3;
+    __device__ static int a(int i) { return i == 2 ? 1 : 0; }
+    __device__ static int b(int i) { return i == 1 ? 1 : 0; }
+};
+template <>
+struct Products<3> {  // the six products of order >= 2^-16
+    static constexpr int n = 6;
+    __device__ static int a(int i) { return (i == 2 || i == 3) ? 1 : (i == 5 ? 2 : 0); }
+    __device__ static int b(int i) { return (i == 1 || i == 3) ? 1 : (i == 4 ? 2 : 0); }
+};
+
+template <int P>
+struct Cfg {
+    static constexpr int OPERAND_BYTES = P * PK_TILE_BYTES;  // one k-tile of one side, all terms
+    static constexpr int STAGE_BYTES = 2 * OPERAND_BYTES;
+    static constexpr int STAGES_RAW = (SMEM_BUDGET - 2 * CTL_BYTES) / STAGE_BYTES;
+    static constexpr int STAGES = STAGES_RAW > MAX_STAGES ? MAX_STAGES : STAGES_RAW;
+    static constexpr int SMEM = 2 * CTL_BYTES + STAGES * STAGE_BYTES;
+};
+
+// ---------------------------------------------------------------- epilogue of one 32 x 32 chunk
+__device__ __forceinline__ void epi_chunk(const EpiParams &e, int row, int col0, const float (&v)[32]) {
+    if (row >= e.M) return;
+    const bool full_cols = col0 + 31 < e.N;
+    if (full_cols && (e.mode == EPI_GEMM || e.mode == EPI_STORE)) {
+        float *c = e.C + (long long)row * e.ldc + col0;
+        if (((reinterpret_cast<uintptr_t>(c) & 15) == 0)) {
+#pragma unroll
+            for (int q = 0; q < 32; q += 4) {
+                float4 o;
+                o.x = e.alpha * v[q + 0];
+                o.y = e.alpha * v[q + 1];
+                o.z = e.alpha * v[q + 2];
+                o.w = e.alpha * v[q + 3];
+                if (e.mode == EPI_GEMM && e.beta != 0.0f) {
+                    float4 ci = *reinterpret_cast<const float4 *>(c + q);
+                    o.x = fmaf(e.beta, ci.x, o.x);
+                    o.y = fmaf(e.beta, ci.y, o.y);
+                    o.z = fmaf(e.beta, ci.z, o.z);
+                    o.w = fmaf(e.beta, ci.w, o.w);
+                }
+                *reinterpret_cast<float4 *>(c + q) = o;
+            }
+            return;
+        }
+    }
+    if (full_cols && e.mode == EPI_EF) {
+        const long long o = (long long)row * e.ld_ef + col0;
+        if (((reinterpret_cast<uintptr_t>(e.E + o) & 15) == 0) && ((reinterpret_cast<uintptr_t>(e.F + o) & 15) == 0) &&
+            (e.beta == 0.0f || (reinterpret_cast<uintptr_t>(e.D + o) & 15) == 0)) {
+#pragma unroll
+            for (int q = 0; q < 32; q += 4) {
+                float4 ev = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+                *reinterpret_cast<float4 *>(e.E + o + q) = ev;
+                float4 f;
+                f.x = e.alpha * ev.x;
+                f.y = e.alpha * ev.y;
+                f.z = e.alpha * ev.z;
+                f.w = e.alpha * ev.w;
+                if (e.beta != 0.0f) {
+                    float4 d = *reinterpret_cast<const float4 *>(e.D + o + q);
+                    f.x = fmaf(e.beta, d.x, f.x);
+                    f.y = fmaf(e.beta, d.y, f.y);
+                    f.z = fmaf(e.beta, d.z, f.z);
+                    f.w = fmaf(e.beta, d.w, f.w);
+                }
+                *reinterpret_cast<float4 *>(e.F + o + q) = f;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) epi_store(e, row, col0 + q, v[q]);
+}
+
+// ---------------------------------------------------------------- the kernel
+template <int P, int BATCHED>
+__global__ __launch_bounds__(NTHREADS, 1) void k_umma(const __grid_constant__ UmmaProblem single,
+                                                      const UmmaProblem *__restrict__ probs,
+                                                      const int *__restrict__ prefix, int nprob, int total_tiles,
+                                                      int *queue) {
+    using C = Cfg<P>;
+    using PR = Products<P>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte alignment of the stage area is required by the 128-byte swizzle.
+    const uint32_t raw = saddr(smem_raw);
+    const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
+    Ctl *ctl = reinterpret_cast<Ctl *>(smem_raw + pad);
+    const uint32_t stage0 = raw + pad + CTL_BYTES;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(&ctl->full[s], 1);
+            mbar_init(&ctl->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&ctl->tfull[b], 1);
+            mbar_init(&ctl->tempty[b], 4);
+        }
+        for (int s = 0; s < SCHED; ++s) {
+            mbar_init(&ctl->sfull[s], 1);
+            mbar_init(&ctl->sempty[s], 1 + 4);
+        }
+        mbar_init(&ctl->drain, 1);
+        ctl->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&ctl->tmem_base)),
+                     "r"(2 * BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = ctl->tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            int it = 0, sidx = 0;
+            int next = blockIdx.x;
+            for (;;) {
+                int t;
+                if (queue) t = atomicAdd(queue, 1);
+                else {
+                    t = next;
+                    next += gridDim.x;
+                }
+                if (t >= total_tiles) t = -1;
+                const int s = sidx % SCHED;
+                if (!wait_phase(ctl, &ctl->sempty[s], ((sidx / SCHED) & 1) ^ 1, ERR_PRODUCER)) break;
+                ctl->sched[s] = t;
+                mbar_arrive(&ctl->sfull[s]);
+                ++sidx;
+                if (t < 0) break;
+                const TileRef tr = resolve<BATCHED>(t, &single, probs, prefix, nprob);
+                const UmmaProblem &pb = *tr.p;
+                if (pb.inject_timeout) break;  // nothing arrives on full[]: the MMA wait runs out
+                bool ok = true;
+                for (int sg = 0; sg < pb.nseg && ok; ++sg) {
+                    const char *xb = pb.seg[sg].X + (size_t)tr.mi * pb.x_kt * C::OPERAND_BYTES;
+                    const char *yb = pb.seg[sg].Y + (size_t)tr.ni * pb.y_kt * C::OPERAND_BYTES;
+                    for (int kt = 0; kt < pb.kt; ++kt) {
+                        const int st = it % C::STAGES;
+                        if (!wait_phase(ctl, &ctl->empty[st], ((it / C::STAGES) & 1) ^ 1, ERR_PRODUCER)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(&ctl->full[st], C::STAGE_BYTES);
+                        const uint32_t dst = stage0 + st * C::STAGE_BYTES;
+                        bulk_g2s(dst, xb + (size_t)kt * C::OPERAND_BYTES, C::OPERAND_BYTES, &ctl->full[st]);
+                        bulk_g2s(dst + C::OPERAND_BYTES, yb + (size_t)kt * C::OPERAND_BYTES, C::OPERAND_BYTES,
+                                 &ctl->full[st]);
+                        ++it;
+                    }
+                }
+                if (!ok) break;
+            }
+            // wait for this CTA's copies still in flight
+            for (int j = (it > C::STAGES ? it - C::STAGES : 0); j < it; ++j)
+                wait_phase(ctl, &ctl->full[j % C::STAGES], (j / C::STAGES) & 1, ERR_DRAIN, false);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int it = 0, sidx = 0, acc = 0;
+            for (;;) {
+                const int s = sidx % SCHED;
+                if (!wait_phase(ctl, &ctl->sfull[s], (sidx / SCHED) & 1, ERR_MMA)) break;
+                const int t = ctl->sched[s];
+                mbar_arrive(&ctl->sempty[s]);
+                ++sidx;
+                if (t < 0) break;
+                const TileRef tr = resolve<BATCHED>(t, &single, probs, prefix, nprob);
+                const UmmaProblem &pb = *tr.p;
+                const int b = acc & 1;
+                if (!wait_phase(ctl, &ctl->tempty[b], ((acc >> 1) & 1) ^ 1, ERR_MMA)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * BN);
+                const int ktot = pb.nseg * pb.kt;
+                bool ok = true;
+                for (int q = 0; q < ktot; ++q) {
+                    const int st = it % C::STAGES;
+                    if (!wait_phase(ctl, &ctl->full[st], (it / C::STAGES) & 1, ERR_MMA)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = stage0 + st * C::STAGE_BYTES;
+                    const uint32_t b0 = a0 + C::OPERAND_BYTES;
+#pragma unroll
+                    for (int pr = 0; pr < PR::n; ++pr) {
+#pragma unroll
+                        for (int ks = 0; ks < PK_K / 16; ++ks) {
+                            const uint64_t ad = sw128_desc(a0 + PR::a(pr) * PK_TILE_BYTES + ks * 32);
+                            const uint64_t bd = sw128_desc(b0 + PR::b(pr) * PK_TILE_BYTES + ks * 32);
+                            umma_bf16(d, ad, bd, (q | pr | ks) ? 1u : 0u);
+                        }
+                    }
+                    umma_commit(&ctl->empty[st]);
+                    ++it;
+                }
+                if (!ok) break;
+                if (ktot == 0) mbar_arrive(&ctl->tfull[b]);
+                else umma_commit(&ctl->tfull[b]);
+                ++acc;
+            }
+            // every MMA this thread issued has completed before TMEM is freed
+            umma_commit(&ctl->drain);
+            wait_phase(ctl, &ctl->drain, 0, ERR_DRAIN, false);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue warps 2..5
+        const int quarter = warp & 3;  // TMEM lanes this warp may access
+        int sidx = 0, acc = 0;
+        for (;;) {
+            const int s = sidx % SCHED;
+            bool ok = wait_phase(ctl, &ctl->sfull[s], (sidx / SCHED) & 1, ERR_EPILOGUE);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            const int t = ctl->sched[s];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->sempty[s]);
+            ++sidx;
+            if (t < 0) break;
+            const TileRef tr = resolve<BATCHED>(t, &single, probs, prefix, nprob);
+            const UmmaProblem &pb = *tr.p;
+            const int b = acc & 1;
+            ok = wait_phase(ctl, &ctl->tfull[b], (acc >> 1) & 1, ERR_EPILOGUE);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            const int row = tr.mi * BM + quarter * 32 + lane;
+            const bool have = (pb.nseg * pb.kt) > 0;
+            const EpiParams e = pb.epi;
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                float v[32];
+                if (have) {
+                    tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c * 32), v);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) v[q] = 0.0f;
+                }
+                const int col0 = tr.ni * BN + c * 32;
+                if (e.mode == EPI_SYM && tr.mi == tr.ni) {
+                    // diagonal tile: elements above the diagonal are skipped
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) epi_store(e, row, col0 + q, v[q]);
+                } else {
+                    epi_chunk(e, row, col0, v);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->tempty[b]);
+            ++acc;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+    }
+}
+
+template <int P, int BATCHED>
+ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int *prefix, int nprob, int total,
+                 int *queue, cudaStream_t st) {
+    using C = Cfg<P>;
+    auto kern = k_umma<P, BATCHED>;
+    // the shared-memory opt-in is set once per device (so nothing but launches
+    // happens while a caller captures a graph)
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    LN_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        LN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    const int grid = total < sm_count() ? total : sm_count();
+    UmmaProblem dummy{};
+    { LaunchScope ls_(FAM_UMMA, st); kern<<<grid, NTHREADS, C::SMEM, st>>>(single ? *single : dummy, probs, prefix, nprob, total, queue); }
+    return check_launch("tcgen05 contraction");
+}
+
+template <int BATCHED>
+ln_status dispatch(int terms, const UmmaProblem *single, const UmmaProblem *probs, const int *prefix, int nprob,
+                   int total, int *queue, cudaStream_t st) {
+    switch (terms) {
+        case 1: return launch<1, BATCHED>(single, probs, prefix, nprob, total, queue, st);
+        case 2: return launch<2, BATCHED>(single, probs, prefix, nprob, total, queue, st);
+        case 3: return launch<3, BATCHED>(single, probs, prefix, nprob, total, queue, st);
+        default: return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
+    }
+}
+
+}  // namespace
+
+ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st) {
+    long long tiles = p.sym ? (long long)p.mt * (p.mt + 1) / 2 : (long long)p.mt * p.nt;
+    if (tiles == 0) return LN_SUCCESS;
+    if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many output tiles");
+    return dispatch<0>(terms, &p, nullptr, nullptr, 1, (int)tiles, nullptr, st);
+}
+
+ln_status umma_contract_batched(const UmmaProblem *d_probs, const int *d_tile_prefix, int nprob, int total_tiles,
+                                int *d_queue, int terms, cudaStream_t st) {
+    if (total_tiles == 0) return LN_SUCCESS;
+    LN_CUDA_TRY(cudaMemsetAsync(d_queue, 0, sizeof(int), st));
+    return dispatch<1>(terms, nullptr, d_probs, d_tile_prefix, nprob, total_tiles, d_queue, st);
+}
+
+ln_status umma_read_error(int *value) {
+    int v = 0, zero = 0;
+    LN_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_umma_error, sizeof(int)));
+    if (v) LN_CUDA_TRY(cudaMemcpyToSymbol(g_umma_error, &zero, sizeof(int)));
+    *value = v;
+    return LN_SUCCESS;
+}
+
+}  // namespace ln

@@ -1,0 +1,123 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+The library must load and export every entry point declared in
+include/loopnest.h, and argument validation, aliasing checks and workspace
+queries must behave as the header states. The pointers used here are fake
+device addresses that the library never dereferences: every call below fails
+validation (or is a size query) before any CUDA call is made.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2312_13170_gb300 import api, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "loopnest.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return api.lib()
+
+
+def declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ln_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_symbols_exported(L):
+    names = declared()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(L, n), f"{n} declared in loopnest.h but not exported"
+    assert set(names) == set(api.EXPORTS), "binding and header disagree"
+
+
+def test_version_and_status_strings(L):
+    assert L.ln_version() >= 100
+    assert L.ln_status_string(2) == b"LN_ERR_ALIASING"
+    assert L.ln_status_string(99) == b"LN_UNKNOWN_STATUS"
+
+
+FAKE_A = 0x7F0000000000
+FAKE_B = 0x7F0000100000
+FAKE_C = 0x7F0000200000
+
+
+def P(x):
+    return ctypes.c_void_p(x)
+
+
+def last(L):
+    return L.ln_get_last_error().decode()
+
+
+def test_gemm_validation(L):
+    # negative size
+    assert L.ln_gemm(-1, 4, 4, 1.0, P(FAKE_A), 4, P(FAKE_B), 4, 0.0, P(FAKE_C), 4, None, 0, 0, 0, None) == 1
+    # ld smaller than the column count
+    assert L.ln_gemm(4, 4, 4, 1.0, P(FAKE_A), 3, P(FAKE_B), 4, 0.0, P(FAKE_C), 4, None, 0, 0, 0, None) == 1
+    # NULL operand
+    assert L.ln_gemm(4, 4, 4, 1.0, None, 4, P(FAKE_B), 4, 0.0, P(FAKE_C), 4, None, 0, 0, 0, None) == 1
+    # C overlapping A -> aliasing (the alias contract of the transformation)
+    s = L.ln_gemm(64, 64, 64, 1.0, P(FAKE_A), 64, P(FAKE_B), 64, 0.0, P(FAKE_A + 256), 64, None, 0, 0, 0, None)
+    assert s == 2 and "overlap" in last(L)
+    # plain form supports only FP32
+    assert L.ln_gemm(4, 4, 4, 1.0, P(FAKE_A), 4, P(FAKE_B), 4, 0.0, P(FAKE_C), 4, None, 0, 0, 2, None) == 4
+    # unknown enum
+    assert L.ln_gemm(4, 4, 4, 1.0, P(FAKE_A), 4, P(FAKE_B), 4, 0.0, P(FAKE_C), 4, None, 0, 7, 0, None) == 1
+    # tensor-core path without a workspace
+    s = L.ln_gemm(256, 256, 256, 1.0, P(FAKE_A), 256, P(FAKE_B), 256, 0.0, P(FAKE_C), 256, None, 0, 1, 2, None)
+    assert s == 7 and "workspace" in last(L)
+    # zero-size is a no-op that succeeds without touching anything
+    assert L.ln_gemm(0, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, None, 0, 1, 2, None) == 0
+
+
+def test_workspace_queries(L):
+    n = ctypes.c_size_t()
+    assert L.ln_gemm_workspace_size(256, 256, 256, 0, 0, ctypes.byref(n)) == 0 and n.value == 0
+    assert L.ln_gemm_workspace_size(256, 256, 256, 1, 0, ctypes.byref(n)) == 0 and n.value == 0
+    assert L.ln_gemm_workspace_size(256, 256, 256, 1, 2, ctypes.byref(n)) == 0
+    # two packed operands of 2 x 4 k-tiles x 2 terms x 16 KiB
+    assert n.value == 2 * (2 * 4 * 2 * 16384)
+    assert L.ln_gemm_workspace_size(200, 100, 70, 1, 3, ctypes.byref(n)) == 0
+    assert n.value == (2 * 2 * 3 + 1 * 2 * 3) * 16384
+    assert L.ln_gemm_chain_workspace_size(2048, 2048, 2048, 2048, 1, 2, ctypes.byref(n)) == 0
+    assert n.value == 4 * 2048 * 2048 + 4 * (16 * 32 * 2 * 16384)
+    assert L.ln_covariance_workspace_size(8192, 2048, 1, 2, ctypes.byref(n)) == 0 and n.value > 0
+    assert L.ln_syr2k_workspace_size(100, 50, 1, 2, ctypes.byref(n)) == 0 and n.value == 2 * 2 * 16384
+
+
+def test_sym_validation(L):
+    s = L.ln_syrk(5, 8, 8, 1.0, P(FAKE_A), 8, 0.0, P(FAKE_C), 8, None, 0, 0, 0, None)
+    assert s == 1 and "fill" in last(L)
+    s = L.ln_syr2k(0, 64, 64, 1.0, P(FAKE_A), 64, P(FAKE_B), 64, 0.0, P(FAKE_B + 1024), 64, None, 0, 0, 0, None)
+    assert s == 2
+
+
+def test_cov_validation(L):
+    assert L.ln_covariance(1, 8, P(FAKE_A), 8, P(FAKE_C), 8, None, 0, 0, 0, None) == 1
+    assert L.ln_correlation(16, 8, P(FAKE_A), 8, P(FAKE_A + 64), 8, None, 0, 0, 0, None) == 2
+
+
+def test_batched_validation(L):
+    descs = (api.SymDesc * 2)()
+    descs[0] = api.SymDesc(64, 32, FAKE_A, 32, None, 0, FAKE_C, 64)
+    descs[1] = api.SymDesc(64, 32, FAKE_B, 32, None, 0, FAKE_C + 1024, 64)  # overlaps instance 0's C
+    n = ctypes.c_size_t()
+    assert L.ln_syrk_batched_workspace_size(2, ctypes.byref(descs), 1, 2, ctypes.byref(n)) == 2
+    descs[1] = api.SymDesc(64, 32, FAKE_B, 32, None, 0, FAKE_C + 64 * 64 * 4, 64)
+    assert L.ln_syrk_batched_workspace_size(2, ctypes.byref(descs), 1, 2, ctypes.byref(n)) == 0
+    # rank-ordered packed operands: 2 instances x 1 row tile x 1 k tile x 2 terms, plus descriptors
+    assert n.value >= 2 * 2 * 16384
+    descs[1] = api.SymDesc(64, 32, FAKE_C + 4, 32, None, 0, FAKE_C + 64 * 64 * 4, 64)  # input inside an output
+    assert L.ln_syrk_batched_workspace_size(2, ctypes.byref(descs), 1, 2, ctypes.byref(n)) == 2
+
+
+def test_stream_check_symbol_present(L):
+    assert callable(L.ln_stream_check)

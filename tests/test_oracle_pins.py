@@ -311,3 +311,10 @@ def test_pins_reject_planted_mistakes():
     _, _, S = exact_cov(X)
     wrong = [[S[i][j] / 8 for j in range(4)] for i in range(4)]  # divisor n instead of n-1
     assert not close(oracle.covariance(X), wrong)
+
+
+def test_cov_rows_matches_full():
+    X = inputs.cov_inputs(64, 20, seed=4)["X"]
+    rows = [0, 7, 19, 3]
+    assert np.array_equal(oracle.cov_rows(X, rows), oracle.covariance(X)[rows])
+    assert np.array_equal(oracle.cov_rows(X, rows, corr=True), oracle.correlation(X)[rows])
