@@ -159,19 +159,32 @@ struct Operand {
     int t;
 };
 
+// Tile geometry of a general (non-symmetric) tcgen05 contraction: mt row
+// tiles of 128, nt column tiles of the engine's width, kt k tiles of 64; the
+// packed N-side operand holds yrt = nt * width/128 row tiles (zero padded).
 struct ContractPlan {
     char *px = nullptr, *py = nullptr;
-    int mt = 0, nt = 0, kt = 0;
+    int mt = 0, nt = 0, kt = 0, yrt = 0;
 };
+
+void contract_geometry(int M, int N, int K, int P, ContractPlan &cp) {
+    const int bn = umma_tile_n(P, 0);
+    cp.mt = (int)ceil_div(M, PK_ROWS);
+    cp.nt = (int)ceil_div(N, bn);
+    cp.kt = (int)ceil_div(K, PK_K);
+    cp.yrt = cp.nt * (bn / PK_ROWS);
+}
+
+size_t contract_pack_bytes(const ContractPlan &cp, int P) {
+    return align_up(packed_bytes(cp.mt, cp.kt, P), 256) + packed_bytes(cp.yrt, cp.kt, P);
+}
 
 void plan_contract(Ws &w, int M, int N, int K, ln_form form, ln_precision prec, ContractPlan &cp) {
     if (form != LN_FORM_INTERNALIZED || !tensor_prec(prec)) return;
     const int P = prec_terms(prec);
-    cp.mt = (int)ceil_div(M, PK_ROWS);
-    cp.nt = (int)ceil_div(N, PK_ROWS);
-    cp.kt = (int)ceil_div(K, PK_K);
+    contract_geometry(M, N, K, P, cp);
     cp.px = w.take<char>(packed_bytes(cp.mt, cp.kt, P));
-    cp.py = w.take<char>(packed_bytes(cp.nt, cp.kt, P));
+    cp.py = w.take<char>(packed_bytes(cp.yrt, cp.kt, P));
 }
 
 ln_status run_contract(int M, int N, int K, Operand a, Operand b, const EpiParams &epi, ln_form form,
@@ -194,10 +207,9 @@ ln_status run_contract(int M, int N, int K, Operand a, Operand b, const EpiParam
         return simt_contract(M, N, K, op, epi, st);
     }
     const int P = prec_terms(prec);
-    PackSrc px{a.p, a.ld, a.t ? 1 : 0, M, K, nullptr, nullptr, cp.px, cp.mt, cp.kt};
-    PackSrc py{b.p, b.ld, b.t ? 0 : 1, N, K, nullptr, nullptr, cp.py, cp.nt, cp.kt};
-    LN_TRY(pack_operand(px, P, st));
-    LN_TRY(pack_operand(py, P, st));
+    PackSrc ps[2] = {{a.p, a.ld, a.t ? 1 : 0, M, K, nullptr, nullptr, cp.px, cp.mt, cp.kt},
+                     {b.p, b.ld, b.t ? 0 : 1, N, K, nullptr, nullptr, cp.py, cp.yrt, cp.kt}};
+    LN_TRY(pack_operands(ps, 2, P, st));
     UmmaProblem pb{};
     pb.seg[0] = {cp.px, cp.py};
     pb.nseg = 1;
@@ -207,6 +219,7 @@ ln_status run_contract(int M, int N, int K, Operand a, Operand b, const EpiParam
     pb.mt = cp.mt;
     pb.nt = cp.nt;
     pb.sym = 0;
+    pb.chunk_kt = UMMA_CHUNK_KT;
     pb.inject_timeout = inject_timeout_requested();
     pb.epi = epi;
     return umma_contract(pb, P, st);
@@ -231,15 +244,29 @@ EpiParams epi_store(int M, int N, float alpha, float *C, long long ldc) {
 }
 
 // ------------------------------------------------------------------ chain
+// FP32 forms keep T = A*B in FP32. The tensor-core form never materialises T
+// in FP32: the first contraction's epilogue writes it straight into the packed
+// split operand of the second (rows = ni, K = nj, k-tile pitch 2*ceil(nj/128)).
 struct ChainPlan {
     float *T = nullptr;
-    ContractPlan c1, c2;
+    char *pa = nullptr, *pb = nullptr, *pt = nullptr, *pc = nullptr;
+    ContractPlan g1, g2;
+    int ktT = 0;
 };
 
 void plan_chain(Ws &w, int ni, int nj, int nk, int nl, ln_form form, ln_precision prec, ChainPlan &p) {
-    p.T = w.take<float>(sizeof(float) * (size_t)ni * nj);
-    plan_contract(w, ni, nj, nk, form, prec, p.c1);
-    plan_contract(w, ni, nl, nj, form, prec, p.c2);
+    if (form != LN_FORM_INTERNALIZED || !tensor_prec(prec)) {
+        p.T = w.take<float>(sizeof(float) * (size_t)ni * nj);
+        return;
+    }
+    const int P = prec_terms(prec);
+    contract_geometry(ni, nj, nk, P, p.g1);
+    contract_geometry(ni, nl, nj, P, p.g2);
+    p.ktT = p.g1.yrt * (PK_ROWS / PK_K);  // the first contraction's column tiles, in k tiles of T
+    p.pa = w.take<char>(packed_bytes(p.g1.mt, p.g1.kt, P));
+    p.pb = w.take<char>(packed_bytes(p.g1.yrt, p.g1.kt, P));
+    p.pt = w.take<char>(packed_bytes(p.g1.mt, p.ktT, P));
+    p.pc = w.take<char>(packed_bytes(p.g2.yrt, p.g2.kt, P));
 }
 
 // ------------------------------------------------------------------ covariance / correlation
@@ -319,6 +346,7 @@ ln_status run_cov(bool corr, int n, int m, const float *X, int ldx, float *out, 
     pb.x_kt = pb.y_kt = p.kt;
     pb.mt = pb.nt = p.mt;
     pb.sym = 1;
+    pb.chunk_kt = UMMA_CHUNK_KT;
     pb.epi = e;
     return umma_contract(pb, P, st);
 }
@@ -385,12 +413,11 @@ ln_status run_sym(bool two, ln_fill fill, int n, int k, float alpha, const float
         return simt_contract(n, n, k, op, e, st);
     }
     const int P = prec_terms(prec);
-    PackSrc pa{A, lda, 0, n, k, nullptr, nullptr, p.pa, p.mt, p.kt};
-    LN_TRY(pack_operand(pa, P, st));
+    PackSrc ps[2] = {{A, lda, 0, n, k, nullptr, nullptr, p.pa, p.mt, p.kt},
+                     {B, ldb, 0, n, k, nullptr, nullptr, p.pb, p.mt, p.kt}};
+    LN_TRY(pack_operands(ps, two ? 2 : 1, P, st));
     UmmaProblem pb{};
     if (two) {
-        PackSrc pbs{B, ldb, 0, n, k, nullptr, nullptr, p.pb, p.mt, p.kt};
-        LN_TRY(pack_operand(pbs, P, st));
         pb.seg[0] = {p.pa, p.pb};
         pb.seg[1] = {p.pb, p.pa};
         pb.nseg = 2;
@@ -402,6 +429,7 @@ ln_status run_sym(bool two, ln_fill fill, int n, int k, float alpha, const float
     pb.x_kt = pb.y_kt = p.kt;
     pb.mt = pb.nt = p.mt;
     pb.sym = 1;
+    pb.chunk_kt = UMMA_CHUNK_KT;
     pb.epi = e;
     return umma_contract(pb, P, st);
 }
@@ -530,9 +558,9 @@ void plan_chain_bwd(Ws &w, int ni, int nj, int nk, int nl, ln_form form, ln_prec
         size_t best = 0;
         int dims[6][3] = {{nk, nl, nj}, {ni, nk, nl}, {ni, nj, nl}, {nk, nj, ni}, {ni, nj, nk}, {nj, nl, ni}};
         for (auto &d : dims) {
-            size_t b = packed_bytes(ceil_div(d[0], PK_ROWS), ceil_div(d[2], PK_K), P) +
-                       packed_bytes(ceil_div(d[1], PK_ROWS), ceil_div(d[2], PK_K), P);
-            best = std::max(best, b);
+            ContractPlan g;
+            contract_geometry(d[0], d[1], d[2], P, g);
+            best = std::max(best, contract_pack_bytes(g, P));
         }
         p.c.px = w.take<char>(best);
     }
@@ -543,11 +571,9 @@ ln_status contract_into(int M, int N, int K, Operand a, Operand b, const EpiPara
     ContractPlan cp;
     if (form == LN_FORM_INTERNALIZED && tensor_prec(prec)) {
         const int P = prec_terms(prec);
-        cp.mt = (int)ceil_div(M, PK_ROWS);
-        cp.nt = (int)ceil_div(N, PK_ROWS);
-        cp.kt = (int)ceil_div(K, PK_K);
+        contract_geometry(M, N, K, P, cp);
         cp.px = pack_area;
-        cp.py = pack_area + packed_bytes(cp.mt, cp.kt, P);
+        cp.py = pack_area + align_up(packed_bytes(cp.mt, cp.kt, P), 256);
     }
     return run_contract(M, N, K, a, b, e, form, prec, cp, st);
 }
@@ -571,8 +597,9 @@ void plan_cov_bwd(Ws &w, bool corr, int n, int m, ln_form form, ln_precision pre
     if (corr) p.dZ = w.take<float>(sizeof(float) * (size_t)n * m);
     if (form == LN_FORM_INTERNALIZED && tensor_prec(prec)) {
         const int P = prec_terms(prec);
-        p.pack = w.take<char>(packed_bytes(ceil_div(n, PK_ROWS), ceil_div(m, PK_K), P) +
-                              packed_bytes(ceil_div(m, PK_ROWS), ceil_div(m, PK_K), P));
+        ContractPlan g;
+        contract_geometry(n, m, m, P, g);
+        p.pack = w.take<char>(contract_pack_bytes(g, P));
     }
 }
 
@@ -776,8 +803,43 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
     LN_TRY(check_ws(ws, wsb, count.off));
     Ws w(ws);
     plan_chain(w, ni, nj, nk, nl, form, prec, p);
-    LN_TRY(run_contract(ni, nj, nk, {A, nk, 0}, {B, nj, 0}, epi_store(ni, nj, 1.0f, p.T, nj), form, prec, p.c1, st));
-    return run_contract(ni, nl, nj, {p.T, nj, 0}, {C, nl, 0}, ef, form, prec, p.c2, st);
+    if (p.T) {
+        ContractPlan none;
+        LN_TRY(run_contract(ni, nj, nk, {A, nk, 0}, {B, nj, 0}, epi_store(ni, nj, 1.0f, p.T, nj), form, prec, none, st));
+        return run_contract(ni, nl, nj, {p.T, nj, 0}, {C, nl, 0}, ef, form, prec, none, st);
+    }
+    const int P = prec_terms(prec);
+    PackSrc ps[3] = {{A, nk, 0, ni, nk, nullptr, nullptr, p.pa, p.g1.mt, p.g1.kt},
+                     {B, nj, 1, nj, nk, nullptr, nullptr, p.pb, p.g1.yrt, p.g1.kt},
+                     {C, nl, 1, nl, nj, nullptr, nullptr, p.pc, p.g2.yrt, p.g2.kt}};
+    LN_TRY(pack_operands(ps, 3, P, st));
+    UmmaProblem g1{};
+    g1.seg[0] = {p.pa, p.pb};
+    g1.nseg = 1;
+    g1.kt = p.g1.kt;
+    g1.x_kt = g1.y_kt = p.g1.kt;
+    g1.mt = p.g1.mt;
+    g1.nt = p.g1.nt;
+    g1.chunk_kt = UMMA_CHUNK_KT;
+    g1.inject_timeout = inject_timeout_requested();
+    g1.epi.mode = EPI_PACK;
+    g1.epi.M = ni;
+    g1.epi.N = nj;
+    g1.epi.pack = p.pt;
+    g1.epi.pack_kt = p.ktT;
+    LN_TRY(umma_contract(g1, P, st));
+    UmmaProblem g2{};
+    g2.seg[0] = {p.pt, p.pc};
+    g2.nseg = 1;
+    g2.kt = p.g2.kt;
+    g2.x_kt = p.ktT;
+    g2.y_kt = p.g2.kt;
+    g2.mt = p.g2.mt;
+    g2.nt = p.g2.nt;
+    g2.chunk_kt = UMMA_CHUNK_KT;
+    g2.inject_timeout = g1.inject_timeout;
+    g2.epi = ef;
+    return umma_contract(g2, P, st);
 }
 
 // ------------------------------------------------------------------ statistics, covariance, correlation

@@ -46,7 +46,9 @@ enum EpiMode : int {
     EPI_GEMM = 0,  // C[i][j] = alpha*acc + beta*C[i][j]
     EPI_EF = 1,    // E[i][j] = acc; F[i][j] = alpha*acc + beta*D[i][j]
     EPI_SYM = 2,   // symmetric output, see SymKind; only i >= j is produced
-    EPI_STORE = 3  // C[i][j] = alpha*acc (no read of C)
+    EPI_STORE = 3, // C[i][j] = alpha*acc (no read of C)
+    EPI_PACK = 4   // tcgen05 engine only: acc written as split BF16 terms into a packed
+                   // operand (rows = i, K = j) for the next contraction
 };
 enum SymKind : int {
     SYM_AXPBY = 0,  // alpha*acc + beta*C on the requested fill (SYRK/SYR2K)
@@ -66,6 +68,8 @@ struct EpiParams {
     int fill;      // ln_fill, for EPI_SYM
     int sym_kind;  // SymKind
     const float *rs;
+    char *pack;    // EPI_PACK destination and its k-tile pitch
+    int pack_kt;
 };
 
 // ------------------------------------------------------------------ packed tensor-core operands
@@ -152,6 +156,10 @@ size_t corr_bwd_partials_bytes(int n, int m);
 
 // ln_pack.cu
 ln_status pack_operand(const PackSrc &p, int terms, cudaStream_t st);
+// Packs up to four operands in one launch.
+ln_status pack_operands(const PackSrc *ps, int count, int terms, cudaStream_t st);
+// k tiles per TMEM accumulation chunk of the tcgen05 engine
+constexpr int UMMA_CHUNK_KT = 2;
 
 // ln_umma.cu: tcgen05 contraction over packed operands
 struct UmmaSeg {
@@ -165,11 +173,18 @@ struct UmmaProblem {
     int x_kt, y_kt;  // k-tile pitch of the packed X and Y buffers
     int mt, nt;      // 128-row tiles on the M side, BN-wide tiles on the N side
     int sym;         // lower-triangle tiles only (mt == nt)
+    int chunk_kt;    // k tiles accumulated in TMEM before the partial sum is added (in FP32
+                     // registers) to the running sum; <= 0 means the whole reduction
     int inject_timeout;  // test hook: the producer issues no copy, so a bounded wait runs out
     EpiParams epi;
 };
 // True when LN_FAULT_INJECT=timeout is set in the environment (read per call).
 bool inject_timeout_requested();
+// Output tile width the engine uses: 256 for general contractions with one or
+// two split terms, else 128. Symmetric problems always use square 128 tiles.
+// `nt` of a problem counts tiles of this width, and the packed N-side operand
+// must hold 128 * (width / 128) * nt rows (zero padded).
+int umma_tile_n(int terms, int sym);
 ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st);
 ln_status umma_contract_batched(const UmmaProblem *d_probs, const int *d_tile_prefix, int nprob, int total_tiles,
                                 int *d_queue, int terms, cudaStream_t st);

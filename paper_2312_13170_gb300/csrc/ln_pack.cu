@@ -3,104 +3,108 @@
 // shared-memory operand layout (K-major, 128-byte swizzle; see the packed
 // operand description in ln_internal.h).
 //
-// Split: hi = bf16(x), lo = bf16(x - hi) and, for three terms,
-// lo2 = bf16((x - hi) - lo), each rounded to nearest even. x - hi is exact in
-// FP32, so x = hi + lo + O(2^-16 |x|) with two terms and O(2^-24 |x|) with
-// three.
+// The split itself is in ln_split.cuh.
 //
 // Optional centring subtracts a per-row offset given as an FP32 pair
 // (hi + lo = the FP64 mean), so the centred value is correct to about one
 // FP32 rounding even when the mean is large compared to the spread.
-#include <cuda_bf16.h>
-
 #include "ln_internal.h"
+#include "ln_split.cuh"
 
 namespace ln {
 
 namespace {
 
-template <int P>
-__device__ __forceinline__ void split8(const float (&v)[8], uint4 (&out)[P]) {
-    uint32_t w[P][4];
-#pragma unroll
-    for (int q = 0; q < 8; q += 2) {
-        float x0 = v[q], x1 = v[q + 1];
-#pragma unroll
-        for (int t = 0; t < P; ++t) {
-            __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-            w[t][q / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-            x0 = x0 - __bfloat162float(h0);
-            x1 = x1 - __bfloat162float(h1);
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < P; ++t) out[t] = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
-}
-
-template <int P>
-__device__ __forceinline__ void store_chunk(char *tile0, int r, int c, const float (&v)[8]) {
-    uint4 o[P];
-    split8<P>(v, o);
-    const int off = r * 128 + ((c ^ (r & 7)) << 4);
-#pragma unroll
-    for (int t = 0; t < P; ++t) *reinterpret_cast<uint4 *>(tile0 + (size_t)t * PK_TILE_BYTES + off) = o[t];
-}
-
 // One 128-row x 64-k tile (all P terms) of the packed operand described by p.
 // `s` is a 64 x 129 shared-memory staging block used by the transposed case.
+// All global loads of a thread are issued before any split or store.
 template <int TRANS, int P>
 __device__ __forceinline__ void pack_tile(const PackSrc &p, int kt, int rt, float (*s)[PK_ROWS + 1]) {
     const int tid = threadIdx.x;
     const int r0 = rt * PK_ROWS, k0 = kt * PK_K;
     char *tile0 = p.dst + (size_t)((long long)rt * p.kt + kt) * P * PK_TILE_BYTES;
     if (TRANS == 0) {
+        // thread -> (row r = pass*32 + tid/8, 16-byte chunk c = tid%8): a warp
+        // reads 4 rows x 256 contiguous bytes and writes 512 contiguous bytes
         const bool vec = ((reinterpret_cast<uintptr_t>(p.S) & 15) == 0) && ((p.ld & 3) == 0);
+        const int c = tid & 7, gk = k0 + c * 8;
+        float v[4][8];
 #pragma unroll
         for (int pass = 0; pass < 4; ++pass) {
-            const int r = pass * 32 + (tid >> 3), c = tid & 7;
-            const int gr = r0 + r, gk = k0 + c * 8;
-            float v[8];
+            const int gr = r0 + pass * 32 + (tid >> 3);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = 0.0f;
+            for (int q = 0; q < 8; ++q) v[pass][q] = 0.0f;
             if (gr < p.rows) {
                 const float *src = p.S + (long long)gr * p.ld + gk;
                 if (vec && gk + 7 < p.K) {
                     float4 a = __ldg(reinterpret_cast<const float4 *>(src));
                     float4 b = __ldg(reinterpret_cast<const float4 *>(src + 4));
-                    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-                    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+                    v[pass][0] = a.x; v[pass][1] = a.y; v[pass][2] = a.z; v[pass][3] = a.w;
+                    v[pass][4] = b.x; v[pass][5] = b.y; v[pass][6] = b.z; v[pass][7] = b.w;
                 } else {
 #pragma unroll
                     for (int q = 0; q < 8; ++q)
-                        if (gk + q < p.K) v[q] = __ldg(src + q);
-                }
-                if (p.off_hi) {
-                    const float h = p.off_hi[gr], l = p.off_lo[gr];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        if (gk + q < p.K) v[q] = (v[q] - h) - l;
+                        if (gk + q < p.K) v[pass][q] = __ldg(src + q);
                 }
             }
-            store_chunk<P>(tile0, r, c, v);
+        }
+#pragma unroll
+        for (int pass = 0; pass < 4; ++pass) {
+            const int r = pass * 32 + (tid >> 3), gr = r0 + r;
+            if (p.off_hi && gr < p.rows) {
+                const float h = p.off_hi[gr], l = p.off_lo[gr];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (gk + q < p.K) v[pass][q] = (v[pass][q] - h) - l;
+            }
+            store_chunk<P>(tile0, r, c, v[pass]);
         }
     } else {
         // element (r, k) = S[k*ld + r]: stage the 64 x 128 block through shared
-        // memory (coalesced along r) and read it back along k.
+        // memory, loading along r (one 512-byte k-row per warp instruction when
+        // aligned) and reading back along k.
         const int lane = tid & 31, warp = tid >> 5;
+        const bool vec = ((reinterpret_cast<uintptr_t>(p.S) & 15) == 0) && ((p.ld & 3) == 0) &&
+                         r0 + PK_ROWS <= p.rows;
+        const int rr = lane * 4;
+        float4 x[8];
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int gk = k0 + warp + 8 * it;
+            x[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gk < p.K) {
+                const float *src = p.S + (long long)gk * p.ld + r0 + rr;
+                if (vec) {
+                    x[it] = __ldg(reinterpret_cast<const float4 *>(src));
+                } else {
+                    if (r0 + rr + 0 < p.rows) x[it].x = __ldg(src + 0);
+                    if (r0 + rr + 1 < p.rows) x[it].y = __ldg(src + 1);
+                    if (r0 + rr + 2 < p.rows) x[it].z = __ldg(src + 2);
+                    if (r0 + rr + 3 < p.rows) x[it].w = __ldg(src + 3);
+                }
+            }
+        }
+        float h[4] = {0, 0, 0, 0}, l[4] = {0, 0, 0, 0};
+        if (p.off_hi) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (r0 + rr + q < p.rows) {
+                    h[q] = p.off_hi[r0 + rr + q];
+                    l[q] = p.off_lo[r0 + rr + q];
+                }
+        }
 #pragma unroll
         for (int it = 0; it < 8; ++it) {
             const int kk = warp + 8 * it;
-            const int gk = k0 + kk;
+            const bool live = k0 + kk < p.K;
+            float e[4] = {x[it].x, x[it].y, x[it].z, x[it].w};
+            // rotate the four stores by lane/8 so the 32 lanes hit 32 banks
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int rr = lane + 32 * q;
-                const int gr = r0 + rr;
-                float x = 0.0f;
-                if (gk < p.K && gr < p.rows) {
-                    x = __ldg(p.S + (long long)gk * p.ld + gr);
-                    if (p.off_hi) x = (x - p.off_hi[gr]) - p.off_lo[gr];
-                }
-                s[kk][rr] = x;
+            for (int q0 = 0; q0 < 4; ++q0) {
+                const int q = (q0 + (lane >> 3)) & 3;
+                float val = e[q];
+                if (p.off_hi && live && r0 + rr + q < p.rows) val = (val - h[q]) - l[q];
+                s[kk][rr + q] = val;
             }
         }
         __syncthreads();
@@ -120,6 +124,25 @@ template <int TRANS, int P>
 __global__ __launch_bounds__(256) void k_pack(PackSrc p) {
     __shared__ float s[TRANS ? PK_K : 1][PK_ROWS + 1];
     pack_tile<TRANS, P>(p, blockIdx.x, blockIdx.y, s);
+}
+
+struct PackMulti {
+    PackSrc op[4];
+    int prefix[5];
+    int count;
+};
+
+// Several operands in one launch: a flat grid over all their tiles.
+template <int P>
+__global__ __launch_bounds__(256) void k_pack_multi(const __grid_constant__ PackMulti m) {
+    __shared__ float s[PK_K][PK_ROWS + 1];
+    const int t = blockIdx.x;
+    int i = 0;
+    while (i + 1 < m.count && m.prefix[i + 1] <= t) ++i;
+    const PackSrc &p = m.op[i];
+    const int local = t - m.prefix[i];
+    if (p.trans) pack_tile<1, P>(p, local % p.kt, local / p.kt, s);
+    else pack_tile<0, P>(p, local % p.kt, local / p.kt, s);
 }
 
 // Ranks instances by decreasing work n*n*k (ties by index): order[rank] = i.
@@ -159,6 +182,7 @@ __global__ void k_batch_layout(int is_syr2k, int count, const ln_sym_desc *__res
         p.x_kt = p.y_kt = kt;
         p.mt = p.nt = mt;
         p.sym = 1;
+        p.chunk_kt = UMMA_CHUNK_KT;
         const char *pa = pack_base + off;
         const char *pb = is_syr2k ? pa + one : pa;
         pack_off[2 * r] = off;
@@ -248,6 +272,29 @@ ln_status pack_operand(const PackSrc &p, int terms, cudaStream_t st) {
     else return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
 #undef LN_PACK_CASE
     return check_launch("split-and-pack");
+}
+
+ln_status pack_operands(const PackSrc *ps, int count, int terms, cudaStream_t st) {
+    if (count < 1 || count > 4) return fail(LN_ERR_INVALID_VALUE, "pack_operands: bad operand count %d", count);
+    PackMulti m{};
+    m.count = count;
+    long long tiles = 0;
+    for (int i = 0; i < count; ++i) {
+        m.op[i] = ps[i];
+        m.prefix[i] = (int)tiles;
+        tiles += (long long)ps[i].rt * ps[i].kt;
+    }
+    m.prefix[count] = (int)tiles;
+    if (tiles == 0) return LN_SUCCESS;
+    if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many tiles to pack");
+    LaunchScope ls_(FAM_PACK, st);
+    switch (terms) {
+        case 1: k_pack_multi<1><<<(unsigned)tiles, 256, 0, st>>>(m); break;
+        case 2: k_pack_multi<2><<<(unsigned)tiles, 256, 0, st>>>(m); break;
+        case 3: k_pack_multi<3><<<(unsigned)tiles, 256, 0, st>>>(m); break;
+        default: return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
+    }
+    return check_launch("split-and-pack (multi)");
 }
 
 ln_status sym_batched_plan(int is_syr2k, int count, const ln_sym_desc *d_descs, int fill, float alpha, float beta,

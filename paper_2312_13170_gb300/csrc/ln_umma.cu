@@ -1,6 +1,6 @@
 // Internalized tensor-core form: loop internalization (paper Sec. VI-C,
-// Listing 6) on sm_103a. The work-group tile becomes a 128 x 128 CTA output
-// tile; the "prefetch one tile of each operand into local memory, barrier,
+// Listing 6) on sm_103a. The work-group tile becomes a 128 x BN CTA output
+// tile (BN = 256 for general contractions, 128 for symmetric ones); the "prefetch one tile of each operand into local memory, barrier,
 // inner loop over the tile, barrier" sequence becomes a ring of shared-memory
 // stages filled by the bulk-copy (TMA) engine and guarded by mbarriers, and
 // the inner loop over the tile becomes tcgen05.mma instructions accumulating
@@ -13,10 +13,16 @@
 // atomic counter), and double-buffers its TMEM accumulator so that the
 // epilogue of one tile overlaps the MMAs of the next.
 //
-// Warp roles (192 threads): warp 0 issues bulk copies, warp 1 allocates TMEM
-// and issues MMAs (one lane each), warps 2-5 read the accumulator back with
+// Warp roles: warp 0 issues bulk copies, warp 1 allocates TMEM and issues
+// MMAs (one lane each), BN/32 epilogue warps read the accumulator back with
 // tcgen05.ld (each warp owns the 32 TMEM lanes = output rows its warp index
-// may access) and run the shared epilogue.
+// may access, and 128 of the tile's columns) and run the shared epilogue.
+//
+// Accumulation precision: the tensor core's FP32 accumulation into TMEM loses
+// accuracy in proportion to the number of accumulation steps, so every
+// UMMA_CHUNK_KT k tiles the partial sum moves to a fresh TMEM buffer and the
+// epilogue warps add it, with round-to-nearest FP32 adds, into a running sum
+// kept in registers (128 values per thread).
 //
 // Every mbarrier wait is bounded by the global timer: a wait that runs out
 // sets the CTA's abort flag and the library's device error word, every role
@@ -24,6 +30,7 @@
 // TMEM is freed and the kernel returns. ln_stream_check() reports it.
 #include "ln_epilogue.cuh"
 #include "ln_internal.h"
+#include "ln_split.cuh"
 
 namespace ln {
 
@@ -32,9 +39,9 @@ __device__ int g_umma_error;
 namespace {
 
 constexpr int BM = 128;
-constexpr int BN = 128;
-constexpr int NTHREADS = 192;
 constexpr int SCHED = 4;
+constexpr int MAX_NACC = 4;
+constexpr int TMEM_COLS = 512;
 constexpr int MAX_STAGES = 8;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
 constexpr int CTL_BYTES = 1024;
@@ -45,8 +52,8 @@ enum : int { ERR_PRODUCER = 1, ERR_MMA = 2, ERR_EPILOGUE = 4, ERR_DRAIN = 8 };
 struct Ctl {
     uint64_t full[MAX_STAGES];
     uint64_t empty[MAX_STAGES];
-    uint64_t tfull[2];
-    uint64_t tempty[2];
+    uint64_t tfull[MAX_NACC];
+    uint64_t tempty[MAX_NACC];
     uint64_t sfull[SCHED];
     uint64_t sempty[SCHED];
     uint64_t drain;
@@ -125,15 +132,17 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
 }
 
 // Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M x N.
-constexpr uint32_t IDESC_BF16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                                ((uint32_t)(BM >> 4) << 24);
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
+template <int BN>
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(IDESC_BF16), "r"(acc)
+        "l"(a), "l"(b), "r"(idesc_bf16(BN)), "r"(acc)
         : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
@@ -218,17 +227,27 @@ struct Products<3> {  // the six products of order >= 2^-16
     __device__ static int b(int i) { return (i == 1 || i == 3) ? 1 : (i == 4 ? 2 : 0); }
 };
 
-template <int P>
+// Tile configuration: BN columns per CTA tile, P split terms per operand.
+//  shared memory per stage: A (P x 16 KiB) + B (P x BN/128 x 16 KiB), B term q
+//  at q * BN/128 * 16 KiB with its two 128-row halves 16 KiB apart;
+//  TMEM: NACC = 512 / BN accumulator buffers of BN columns.
+template <int P, int BN>
 struct Cfg {
-    static constexpr int OPERAND_BYTES = P * PK_TILE_BYTES;  // one k-tile of one side, all terms
-    static constexpr int STAGE_BYTES = 2 * OPERAND_BYTES;
+    static constexpr int NEPI = BN / 32;  // epilogue warps: 4 per 128 columns
+    static constexpr int NTHREADS = 64 + 32 * NEPI;
+    static constexpr int NACC = TMEM_COLS / BN;
+    static constexpr int HALVES = BN / 128;
+    static constexpr int A_BYTES = P * PK_TILE_BYTES;
+    static constexpr int B_BYTES = P * HALVES * PK_TILE_BYTES;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int STAGES_RAW = (SMEM_BUDGET - 2 * CTL_BYTES) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_RAW > MAX_STAGES ? MAX_STAGES : STAGES_RAW;
     static constexpr int SMEM = 2 * CTL_BYTES + STAGES * STAGE_BYTES;
+    static_assert(NACC <= MAX_NACC && STAGES >= 2, "tile configuration does not fit");
 };
 
 // ---------------------------------------------------------------- epilogue of one 32 x 32 chunk
-__device__ __forceinline__ void epi_chunk(const EpiParams &e, int row, int col0, const float (&v)[32]) {
+__device__ __forceinline__ void epi_chunk(const EpiParams &e, int row, int col0, const float *v) {
     if (row >= e.M) return;
     const bool full_cols = col0 + 31 < e.N;
     if (full_cols && (e.mode == EPI_GEMM || e.mode == EPI_STORE)) {
@@ -283,12 +302,12 @@ __device__ __forceinline__ void epi_chunk(const EpiParams &e, int row, int col0,
 }
 
 // ---------------------------------------------------------------- the kernel
-template <int P, int BATCHED>
-__global__ __launch_bounds__(NTHREADS, 1) void k_umma(const __grid_constant__ UmmaProblem single,
-                                                      const UmmaProblem *__restrict__ probs,
-                                                      const int *__restrict__ prefix, int nprob, int total_tiles,
-                                                      int *queue) {
-    using C = Cfg<P>;
+template <int P, int BN, int BATCHED>
+__global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_constant__ UmmaProblem single,
+                                                                  const UmmaProblem *__restrict__ probs,
+                                                                  const int *__restrict__ prefix, int nprob,
+                                                                  int total_tiles, int *queue) {
+    using C = Cfg<P, BN>;
     using PR = Products<P>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment of the stage area is required by the 128-byte swizzle.
@@ -304,13 +323,13 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_umma(const __grid_constant__ Um
             mbar_init(&ctl->full[s], 1);
             mbar_init(&ctl->empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < C::NACC; ++b) {
             mbar_init(&ctl->tfull[b], 1);
-            mbar_init(&ctl->tempty[b], 4);
+            mbar_init(&ctl->tempty[b], C::NEPI);
         }
         for (int s = 0; s < SCHED; ++s) {
             mbar_init(&ctl->sfull[s], 1);
-            mbar_init(&ctl->sempty[s], 1 + 4);
+            mbar_init(&ctl->sempty[s], 1 + C::NEPI);
         }
         mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
@@ -319,7 +338,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_umma(const __grid_constant__ Um
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&ctl->tmem_base)),
-                     "r"(2 * BN)
+                     "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -352,8 +371,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_umma(const __grid_constant__ Um
                 if (pb.inject_timeout) break;  // nothing arrives on full[]: the MMA wait runs out
                 bool ok = true;
                 for (int sg = 0; sg < pb.nseg && ok; ++sg) {
-                    const char *xb = pb.seg[sg].X + (size_t)tr.mi * pb.x_kt * C::OPERAND_BYTES;
-                    const char *yb = pb.seg[sg].Y + (size_t)tr.ni * pb.y_kt * C::OPERAND_BYTES;
+                    const char *xb = pb.seg[sg].X + (size_t)tr.mi * pb.x_kt * C::A_BYTES;
                     for (int kt = 0; kt < pb.kt; ++kt) {
                         const int st = it % C::STAGES;
                         if (!wait_phase(ctl, &ctl->empty[st], ((it / C::STAGES) & 1) ^ 1, ERR_PRODUCER)) {
@@ -362,9 +380,21 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_umma(const __grid_constant__ Um
                         }
                         mbar_expect_tx(&ctl->full[st], C::STAGE_BYTES);
                         const uint32_t dst = stage0 + st * C::STAGE_BYTES;
-                        bulk_g2s(dst, xb + (size_t)kt * C::OPERAND_BYTES, C::OPERAND_BYTES, &ctl->full[st]);
-                        bulk_g2s(dst + C::OPERAND_BYTES, yb + (size_t)kt * C::OPERAND_BYTES, C::OPERAND_BYTES,
-                                 &ctl->full[st]);
+                        bulk_g2s(dst, xb + (size_t)kt * C::A_BYTES, C::A_BYTES, &ctl->full[st]);
+                        if (C::HALVES == 1) {
+                            const char *yb = pb.seg[sg].Y + ((size_t)tr.ni * pb.y_kt + kt) * C::A_BYTES;
+                            bulk_g2s(dst + C::A_BYTES, yb, C::A_BYTES, &ctl->full[st]);
+                        } else {
+#pragma unroll
+                            for (int h = 0; h < C::HALVES; ++h) {
+                                const char *yb =
+                                    pb.seg[sg].Y + ((size_t)(tr.ni * C::HALVES + h) * pb.y_kt + kt) * C::A_BYTES;
+#pragma unroll
+                                for (int q = 0; q < P; ++q)
+                                    bulk_g2s(dst + C::A_BYTES + (q * C::HALVES + h) * PK_TILE_BYTES,
+                                             yb + q * PK_TILE_BYTES, PK_TILE_BYTES, &ctl->full[st]);
+                            }
+                        }
                         ++it;
                     }
                 }
@@ -387,45 +417,55 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_umma(const __grid_constant__ Um
                 if (t < 0) break;
                 const TileRef tr = resolve<BATCHED>(t, &single, probs, prefix, nprob);
                 const UmmaProblem &pb = *tr.p;
-                const int b = acc & 1;
-                if (!wait_phase(ctl, &ctl->tempty[b], ((acc >> 1) & 1) ^ 1, ERR_MMA)) break;
-                tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(b * BN);
                 const int ktot = pb.nseg * pb.kt;
+                const int ck = pb.chunk_kt > 0 ? pb.chunk_kt : (ktot > 0 ? ktot : 1);
                 bool ok = true;
-                for (int q = 0; q < ktot; ++q) {
-                    const int st = it % C::STAGES;
-                    if (!wait_phase(ctl, &ctl->full[st], (it / C::STAGES) & 1, ERR_MMA)) {
+                // one TMEM accumulator buffer per chunk of ck k tiles
+                for (int q0 = 0; q0 < ktot && ok; q0 += ck) {
+                    const int b = acc % C::NACC;
+                    if (!wait_phase(ctl, &ctl->tempty[b], ((acc / C::NACC) & 1) ^ 1, ERR_MMA)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a0 = stage0 + st * C::STAGE_BYTES;
-                    const uint32_t b0 = a0 + C::OPERAND_BYTES;
-#pragma unroll
-                    for (int pr = 0; pr < PR::n; ++pr) {
-#pragma unroll
-                        for (int ks = 0; ks < PK_K / 16; ++ks) {
-                            const uint64_t ad = sw128_desc(a0 + PR::a(pr) * PK_TILE_BYTES + ks * 32);
-                            const uint64_t bd = sw128_desc(b0 + PR::b(pr) * PK_TILE_BYTES + ks * 32);
-                            umma_bf16(d, ad, bd, (q | pr | ks) ? 1u : 0u);
+                    const uint32_t d = tmem + (uint32_t)(b * BN);
+                    const int q1 = q0 + ck < ktot ? q0 + ck : ktot;
+                    for (int q = q0; q < q1; ++q) {
+                        const int st = it % C::STAGES;
+                        if (!wait_phase(ctl, &ctl->full[st], (it / C::STAGES) & 1, ERR_MMA)) {
+                            ok = false;
+                            break;
                         }
+                        tc_fence_after();
+                        const uint32_t a0 = stage0 + st * C::STAGE_BYTES;
+                        const uint32_t b0 = a0 + C::A_BYTES;
+#pragma unroll
+                        for (int pr = 0; pr < PR::n; ++pr) {
+#pragma unroll
+                            for (int ks = 0; ks < PK_K / 16; ++ks) {
+                                const uint64_t ad = sw128_desc(a0 + PR::a(pr) * PK_TILE_BYTES + ks * 32);
+                                const uint64_t bd = sw128_desc(b0 + PR::b(pr) * C::HALVES * PK_TILE_BYTES + ks * 32);
+                                umma_bf16<BN>(d, ad, bd, ((q - q0) | pr | ks) ? 1u : 0u);
+                            }
+                        }
+                        umma_commit(&ctl->empty[st]);
+                        ++it;
                     }
-                    umma_commit(&ctl->empty[st]);
-                    ++it;
+                    if (!ok) break;
+                    umma_commit(&ctl->tfull[b]);
+                    ++acc;
                 }
                 if (!ok) break;
-                if (ktot == 0) mbar_arrive(&ctl->tfull[b]);
-                else umma_commit(&ctl->tfull[b]);
-                ++acc;
             }
             // every MMA this thread issued has completed before TMEM is freed
             umma_commit(&ctl->drain);
             wait_phase(ctl, &ctl->drain, 0, ERR_DRAIN, false);
         }
     } else {
-        // ------------------------------------------------------------ epilogue warps 2..5
-        const int quarter = warp & 3;  // TMEM lanes this warp may access
+        // ------------------------------------------------------------ epilogue warps
+        const int quarter = warp & 3;          // TMEM lanes (= tile rows) this warp may access
+        const int half = (warp - 2) >> 2;      // which 128 of the tile's BN columns
+        const int col_base = half * 128;
         int sidx = 0, acc = 0;
         for (;;) {
             const int s = sidx % SCHED;
@@ -438,35 +478,54 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_umma(const __grid_constant__ Um
             if (t < 0) break;
             const TileRef tr = resolve<BATCHED>(t, &single, probs, prefix, nprob);
             const UmmaProblem &pb = *tr.p;
-            const int b = acc & 1;
-            ok = wait_phase(ctl, &ctl->tfull[b], (acc >> 1) & 1, ERR_EPILOGUE);
-            if (!__all_sync(0xffffffffu, ok)) break;
-            tc_fence_after();
-            const int row = tr.mi * BM + quarter * 32 + lane;
-            const bool have = (pb.nseg * pb.kt) > 0;
-            const EpiParams e = pb.epi;
-#pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
-                float v[32];
-                if (have) {
-                    tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c * 32), v);
-                } else {
+            const int ktot = pb.nseg * pb.kt;
+            const int ck = pb.chunk_kt > 0 ? pb.chunk_kt : (ktot > 0 ? ktot : 1);
+            const int nch = (ktot + ck - 1) / ck;
+            // running FP32 sum of this thread's 128 outputs: each TMEM chunk is
+            // added here with round-to-nearest adds
+            float sum[128];
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) v[q] = 0.0f;
-                }
-                const int col0 = tr.ni * BN + c * 32;
-                if (e.mode == EPI_SYM && tr.mi == tr.ni) {
-                    // diagonal tile: elements above the diagonal are skipped
+            for (int q = 0; q < 128; ++q) sum[q] = 0.0f;
+            for (int c = 0; c < nch && ok; ++c) {
+                const int b = acc % C::NACC;
+                ok = wait_phase(ctl, &ctl->tfull[b], (acc / C::NACC) & 1, ERR_EPILOGUE);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                tc_fence_after();
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) epi_store(e, row, col0 + q, v[q]);
-                } else {
-                    epi_chunk(e, row, col0, v);
+                for (int g = 0; g < 4; ++g) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + col_base + g * 32), v);
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) sum[g * 32 + q] += v[q];
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ctl->tempty[b]);
+                ++acc;
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&ctl->tempty[b]);
-            ++acc;
+            if (!ok) break;
+            const int rloc = quarter * 32 + lane;
+            const int row = tr.mi * BM + rloc;
+            const int col0 = tr.ni * BN + col_base;
+            const EpiParams &e = pb.epi;
+            if (e.mode == EPI_PACK) {
+                // row rloc of M tile mi; column j of the result is k = j of the packed operand
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const int kt = (col0 + g * 32) / PK_K;
+                    char *tile0 = e.pack + (size_t)((long long)tr.mi * e.pack_kt + kt) * P * PK_TILE_BYTES;
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc)
+                        store_chunk<P>(tile0, rloc, (g & 1) * 4 + cc, &sum[g * 32 + cc * 8]);
+                }
+            } else if (e.mode == EPI_SYM) {
+#pragma unroll
+                for (int q = 0; q < 128; ++q) epi_store(e, row, col0 + q, sum[q]);
+            } else {
+#pragma unroll
+                for (int g = 0; g < 4; ++g) epi_chunk(e, row, col0 + g * 32, &sum[g * 32]);
+            }
         }
     }
 
@@ -474,15 +533,16 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_umma(const __grid_constant__ Um
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
 }
 
-template <int P, int BATCHED>
+template <int P, int BN, int BATCHED>
 ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int *prefix, int nprob, int total,
                  int *queue, cudaStream_t st) {
-    using C = Cfg<P>;
-    auto kern = k_umma<P, BATCHED>;
+    using C = Cfg<P, BN>;
+    auto kern = k_umma<P, BN, BATCHED>;
     // the shared-memory opt-in is set once per device (so nothing but launches
     // happens while a caller captures a graph)
     static bool attr_set[64] = {false};
@@ -494,35 +554,48 @@ ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int 
     }
     const int grid = total < sm_count() ? total : sm_count();
     UmmaProblem dummy{};
-    { LaunchScope ls_(FAM_UMMA, st); kern<<<grid, NTHREADS, C::SMEM, st>>>(single ? *single : dummy, probs, prefix, nprob, total, queue); }
+    {
+        LaunchScope ls_(FAM_UMMA, st);
+        kern<<<grid, C::NTHREADS, C::SMEM, st>>>(single ? *single : dummy, probs, prefix, nprob, total, queue);
+    }
     return check_launch("tcgen05 contraction");
 }
 
 template <int BATCHED>
-ln_status dispatch(int terms, const UmmaProblem *single, const UmmaProblem *probs, const int *prefix, int nprob,
-                   int total, int *queue, cudaStream_t st) {
+ln_status dispatch(int terms, int bn, const UmmaProblem *single, const UmmaProblem *probs, const int *prefix,
+                   int nprob, int total, int *queue, cudaStream_t st) {
+    if (bn == 256) {
+        switch (terms) {
+            case 1: return launch<1, 256, BATCHED>(single, probs, prefix, nprob, total, queue, st);
+            case 2: return launch<2, 256, BATCHED>(single, probs, prefix, nprob, total, queue, st);
+            default: break;
+        }
+        return fail(LN_ERR_INVALID_VALUE, "no 256-wide tile for %d split terms", terms);
+    }
     switch (terms) {
-        case 1: return launch<1, BATCHED>(single, probs, prefix, nprob, total, queue, st);
-        case 2: return launch<2, BATCHED>(single, probs, prefix, nprob, total, queue, st);
-        case 3: return launch<3, BATCHED>(single, probs, prefix, nprob, total, queue, st);
+        case 1: return launch<1, 128, BATCHED>(single, probs, prefix, nprob, total, queue, st);
+        case 2: return launch<2, 128, BATCHED>(single, probs, prefix, nprob, total, queue, st);
+        case 3: return launch<3, 128, BATCHED>(single, probs, prefix, nprob, total, queue, st);
         default: return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
     }
 }
 
 }  // namespace
 
+int umma_tile_n(int terms, int sym) { return (!sym && terms <= 2) ? 256 : 128; }
+
 ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st) {
     long long tiles = p.sym ? (long long)p.mt * (p.mt + 1) / 2 : (long long)p.mt * p.nt;
     if (tiles == 0) return LN_SUCCESS;
     if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many output tiles");
-    return dispatch<0>(terms, &p, nullptr, nullptr, 1, (int)tiles, nullptr, st);
+    return dispatch<0>(terms, umma_tile_n(terms, p.sym), &p, nullptr, nullptr, 1, (int)tiles, nullptr, st);
 }
 
 ln_status umma_contract_batched(const UmmaProblem *d_probs, const int *d_tile_prefix, int nprob, int total_tiles,
                                 int *d_queue, int terms, cudaStream_t st) {
     if (total_tiles == 0) return LN_SUCCESS;
     LN_CUDA_TRY(cudaMemsetAsync(d_queue, 0, sizeof(int), st));
-    return dispatch<1>(terms, nullptr, d_probs, d_tile_prefix, nprob, total_tiles, d_queue, st);
+    return dispatch<1>(terms, 128, nullptr, d_probs, d_tile_prefix, nprob, total_tiles, d_queue, st);
 }
 
 ln_status umma_read_error(int *value) {

@@ -83,12 +83,19 @@ def test_workspace_queries(L):
     assert L.ln_gemm_workspace_size(256, 256, 256, 0, 0, ctypes.byref(n)) == 0 and n.value == 0
     assert L.ln_gemm_workspace_size(256, 256, 256, 1, 0, ctypes.byref(n)) == 0 and n.value == 0
     assert L.ln_gemm_workspace_size(256, 256, 256, 1, 2, ctypes.byref(n)) == 0
-    # two packed operands of 2 x 4 k-tiles x 2 terms x 16 KiB
+    # two packed operands of 2 row tiles x 4 k-tiles x 2 terms x 16 KiB
     assert n.value == 2 * (2 * 4 * 2 * 16384)
+    # N = 100 -> one 256-wide column tile, so the N side is padded to 2 row tiles
+    assert L.ln_gemm_workspace_size(200, 100, 70, 1, 2, ctypes.byref(n)) == 0
+    assert n.value == (2 * 2 * 2 + 2 * 2 * 2) * 16384
+    # three split terms use 128-wide tiles: no padding
     assert L.ln_gemm_workspace_size(200, 100, 70, 1, 3, ctypes.byref(n)) == 0
     assert n.value == (2 * 2 * 3 + 1 * 2 * 3) * 16384
     assert L.ln_gemm_chain_workspace_size(2048, 2048, 2048, 2048, 1, 2, ctypes.byref(n)) == 0
-    assert n.value == 4 * 2048 * 2048 + 4 * (16 * 32 * 2 * 16384)
+    # packed A, B^T, T (written by the first contraction's epilogue) and C^T; no FP32 T
+    assert n.value == 4 * (16 * 32 * 2 * 16384)
+    assert L.ln_gemm_chain_workspace_size(2048, 2048, 2048, 2048, 1, 0, ctypes.byref(n)) == 0
+    assert n.value == 4 * 2048 * 2048
     assert L.ln_covariance_workspace_size(8192, 2048, 1, 2, ctypes.byref(n)) == 0 and n.value > 0
     assert L.ln_syr2k_workspace_size(100, 50, 1, 2, ctypes.byref(n)) == 0 and n.value == 2 * 2 * 16384
 
