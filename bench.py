@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the CPU baseline sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
+    ap.add_argument("--suite", action="store_true", help="measure every workload and form, one JSON line each")
     return ap.parse_args()
 
 
@@ -333,10 +334,219 @@ def run_own(args):
     return 0
 
 
+# ---------------------------------------------------------------- suite: every workload, every form
+def run_suite(args):
+    """One JSON line per (workload, operation, form, precision): GFLOP/s, the
+    roofline fraction (roofline time = max(flops / peak of the mode, bytes /
+    HBM bandwidth)), and the relative Frobenius error on sampled outputs
+    against the FP64 oracle, computed in that entry's CPU-baseline leg."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import oracle
+    from paper_2312_13170_gb300 import api, inputs
+
+    oracle.build()
+    torch.cuda.set_device(0)
+    bf16_peak, hbm, peak_src = peaks()
+    fp32_peak = fp32_simt_peak()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    reps = max(args.steps // 20, 5)
+
+    def peak_of(prec):
+        return fp32_peak if prec == "fp32" else bf16_peak / {"bf16": 1, "3xbf16": 3, "6xbf16": 6}[prec]
+
+    def time_it(fn, n=reps):
+        fn()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for a, b in evs:
+            flush.zero_()
+            a.record()
+            fn()
+            b.record()
+        torch.cuda.synchronize()
+        t = sorted(a.elapsed_time(b) for a, b in evs)
+        return float(np.median(t)), float(np.mean(t))
+
+    def emit(work, op, form, prec, flops, nbytes, ms, err, cpu):
+        roof_ms = max(flops / (peak_of(prec) * 1e12), nbytes / (hbm * 1e9)) * 1e3
+        line = {"suite": True, "workload": work, "op": op, "form": form, "precision": prec,
+                "ms_median": ms[0], "ms_mean": ms[1], "gflops": flops / (ms[0] / 1e3) / 1e9,
+                "roofline_ms": roof_ms, "roofline_frac": roof_ms / ms[0],
+                "bound": "tensor" if (prec != "fp32" and flops / peak_of(prec) / 1e12 > nbytes / hbm / 1e9)
+                else ("alu" if flops / peak_of(prec) / 1e12 > nbytes / hbm / 1e9 else "hbm"),
+                "peak": {"tflops": peak_of(prec), "hbm_gbs": hbm, "source": peak_src},
+                "rel_err": err, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+
+    modes = [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "bf16"), ("internalized", "3xbf16"),
+             ("internalized", "6xbf16")]
+    cores = oracle.max_threads()
+
+    # -------------------------------------------------- GEMM 256^3
+    d = inputs.gemm_inputs(256, 256, 256, seed=0)
+    t0 = time.perf_counter()
+    ref = oracle.gemm(d["A"], d["B"], d["C"], d["alpha"], d["beta"])
+    cpu = {"kind": "oracle", "cores": cores, "seconds": time.perf_counter() - t0, "sample": "whole problem",
+           "gflops": 2 * 256 ** 3 / (time.perf_counter() - t0) / 1e9}
+    T = {k: torch.from_numpy(d[k]).cuda() for k in "ABC"}
+    for form, prec in modes:
+        C = T["C"].clone()
+        api.gemm(T["A"], T["B"], C, d["alpha"], d["beta"], form=form, prec=prec)
+        err = inputs.rel_fro(C.cpu().numpy(), ref)
+        Cw = T["C"].clone()
+        ms = time_it(lambda: api.gemm(T["A"], T["B"], Cw, d["alpha"], d["beta"], form=form, prec=prec))
+        emit("gemm 256^3 alpha=1.5 beta=1.2", "gemm", form, prec, 2 * 256 ** 3, 4 * 4 * 256 * 256, ms, err, cpu)
+
+    # -------------------------------------------------- chain 2048
+    n = 2048
+    d = inputs.chain_inputs(n, seed=0)
+    rows = 64
+    t0 = time.perf_counter()
+    Er, Fr = oracle.gemm_chain(d["A"][:rows], d["B"], d["C"], d["D"][:rows], d["alpha"], d["beta"])
+    dt = time.perf_counter() - t0
+    cpu = {"kind": "oracle", "cores": cores, "seconds": dt, "sample": f"first {rows} rows of E, F",
+           "gflops": 4 * rows * n * n / dt / 1e9}
+    T = {k: torch.from_numpy(d[k]).cuda() for k in "ABCD"}
+    for form, prec in modes:
+        E, F = api.gemm_chain(T["A"], T["B"], T["C"], T["D"], d["alpha"], d["beta"], form=form, prec=prec)
+        err = max(inputs.rel_fro(E[:rows].cpu().numpy(), Er), inputs.rel_fro(F[:rows].cpu().numpy(), Fr))
+        out = (E, F)
+        ms = time_it(lambda: api.gemm_chain(T["A"], T["B"], T["C"], T["D"], d["alpha"], d["beta"], form=form,
+                                            prec=prec, out=out), n=3 if form == "plain" else reps)
+        emit("chain 2048^2", "gemm_chain", form, prec, 4.0 * n ** 3, 6 * 4 * n * n, ms, err, cpu)
+
+    # -------------------------------------------------- covariance / correlation 8192 x 2048
+    ns, m = 8192, 2048
+    X = inputs.cov_inputs(ns, m, seed=0)["X"]
+    Xt = torch.from_numpy(X).cuda()
+    rows_s = [0, 100, 1000, 2047]
+    t0 = time.perf_counter()
+    cov_r = oracle.cov_rows(X, rows_s)
+    corr_r = oracle.cov_rows(X, rows_s, corr=True)
+    dt = time.perf_counter() - t0
+    cpu = {"kind": "oracle", "cores": cores, "seconds": dt, "sample": f"rows {rows_s} of cov and corr",
+           "gflops": 2 * 2 * len(rows_s) * ns * m / dt / 1e9}
+    flops = float(ns) * m * (m + 1)
+    for form in ("plain", "internalized"):
+        mean, ss = api.col_stats(Xt, form=form)
+        ms = time_it(lambda: api.col_stats(Xt, form=form))
+        mr, sr = oracle.col_stats(X)
+        err = max(inputs.rel_fro(mean.cpu().numpy(), mr), inputs.rel_fro(ss.cpu().numpy(), sr))
+        line = {"suite": True, "workload": "column statistics 8192x2048", "op": "col_stats", "form": form,
+                "precision": "fp64", "ms_median": ms[0], "ms_mean": ms[1],
+                "hbm_gbs": 2 * 4 * ns * m / (ms[0] / 1e3) / 1e9,
+                "roofline_frac": (2 * 4 * ns * m / (hbm * 1e9) * 1e3) / ms[0], "bound": "hbm", "rel_err": err}
+        print(json.dumps(line), flush=True)
+    for form, prec in modes:
+        if form == "plain":
+            reps_here = 2
+        else:
+            reps_here = reps
+        cv = api.covariance(Xt, form=form, prec=prec)
+        cr = api.correlation(Xt, form=form, prec=prec)
+        err_c = inputs.rel_fro(cv[rows_s].cpu().numpy(), cov_r)
+        err_r = inputs.rel_fro(cr[rows_s].cpu().numpy(), corr_r)
+        ms = time_it(lambda: api.covariance(Xt, form=form, prec=prec, out=cv), n=reps_here)
+        emit("covariance 8192x2048", "covariance", form, prec, flops, (2 * 4 * ns * m + 4 * m * m), ms, err_c, cpu)
+        ms = time_it(lambda: api.correlation(Xt, form=form, prec=prec, out=cr), n=reps_here)
+        emit("correlation 8192x2048", "correlation", form, prec, flops, (3 * 4 * ns * m + 4 * m * m), ms, err_r, cpu)
+
+    # -------------------------------------------------- batched SYRK / SYR2K, 512 instances, CUDA graph
+    b = inputs.sym_batch_inputs(512, 32, 1536, seed=0)
+    inst = b["instances"]
+    nk = [(x["n"], x["k"]) for x in inst]
+    As = [torch.from_numpy(x["A"]).cuda() for x in inst]
+    Bs = [torch.from_numpy(x["B"]).cuda() for x in inst]
+    C0 = [torch.from_numpy(x["C"]).cuda() for x in inst]
+    rng = np.random.default_rng(5)
+    samp = [(i, int(rng.integers(inst[i]["n"]))) for i in rng.choice(512, size=16, replace=False)]
+    for two in (False, True):
+        op = "syr2k_batched" if two else "syrk_batched"
+        fl = sum((2.0 if two else 1.0) * n_ * (n_ + 1) * k_ for n_, k_ in nk)
+        by = sum((8.0 if two else 4.0) * n_ * k_ + 8.0 * n_ * n_ for n_, k_ in nk)
+        t0 = time.perf_counter()
+        refs = {}
+        for i, r in samp:
+            x = inst[i]
+            if two:
+                v = oracle.gemm(x["A"][r:r + 1], x["B"].T, x["C"][r:r + 1], b["alpha"], b["beta"])
+                v += oracle.gemm(x["B"][r:r + 1], x["A"].T, None, b["alpha"], 0.0)
+            else:
+                v = oracle.gemm(x["A"][r:r + 1], x["A"].T, x["C"][r:r + 1], b["alpha"], b["beta"])
+            refs[(i, r)] = v
+        dt = time.perf_counter() - t0
+        cpu = {"kind": "oracle", "cores": cores, "seconds": dt, "sample": "16 sampled rows of 16 instances"}
+        for form, prec in modes:
+            Cs = [c.clone() for c in C0]
+            batch = api.SymBatch(As, Cs, Bs if two else None, b["alpha"], b["beta"], form=form, prec=prec)
+            batch.run()
+            torch.cuda.synchronize()
+            got = np.concatenate([Cs[i][r:r + 1].cpu().numpy() for i, r in samp], axis=1)
+            want = np.concatenate([refs[(i, r)] for i, r in samp], axis=1)
+            err = inputs.rel_fro(got, want)
+            g = torch.cuda.CUDAGraph()
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                batch.run(s)
+            torch.cuda.current_stream().wait_stream(s)
+            with torch.cuda.graph(g):
+                batch.run()
+            ms = time_it(g.replay, n=2 if form == "plain" else reps)
+            emit("512 uneven instances, n,k log-uniform [32,1536], CUDA graph", op, form, prec, fl, by, ms, err, cpu)
+
+    # -------------------------------------------------- backward of sum(W .* corr(X)) + ||(A B) C||_F^2
+    d = inputs.backward_inputs(4096, 1024, 1024, seed=0)
+    Xb = torch.from_numpy(d["X"]).cuda()
+    W = torch.from_numpy(d["W"]).cuda()
+    A, B, C = (torch.from_numpy(d[k]).cuda() for k in "ABC")
+    t0 = time.perf_counter()
+    dx_ref = oracle.correlation_vjp(d["X"][:, :], d["W"])
+    dt = time.perf_counter() - t0
+    cpu = {"kind": "oracle", "cores": cores, "seconds": dt, "sample": "whole correlation VJP"}
+    p, nb, mb = 1024, 4096, 1024
+    # corr forward (triangle) + dZ = Z (W + W^T) + chain forward 4p^3 + chain adjoint 10p^3 (T reused)
+    fl = float(nb) * mb * (mb + 1) + 2.0 * nb * mb * mb + 14.0 * p ** 3
+    for form, prec in (("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16")):
+        def step():
+            Xg = Xb.detach().requires_grad_(True)
+            Ag, Bg, Cg = (t.detach().requires_grad_(True) for t in (A, B, C))
+            R = api.CorrelationFn.apply(Xg, form, prec, True)
+            E = api.GemmChainFn.apply(Ag, Bg, Cg, form, prec)
+            ((W * R).sum() + (E * E).sum()).backward()
+            return Xg.grad
+        gx = step()
+        err = inputs.rel_fro(gx.cpu().numpy(), dx_ref)
+        ms = time_it(step, n=2 if form == "plain" else reps)
+        emit("backward: X 4096x1024, W/A/B/C 1024^2", "fwd+bwd", form, prec, fl,
+             4.0 * (5 * nb * mb + 2 * mb * mb + 10 * p * p), ms, err, cpu)
+    return 0
+
+
+def fp32_simt_peak():
+    """FP32 FFMA peak from unit counts: SMs x 128 lanes x 2 flops x max SM clock."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", "0", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        mhz = float(out.splitlines()[0])
+    except Exception:
+        mhz = 2070.0
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.suite:
+        return run_suite(args)
     return run_own(args)
 
 
