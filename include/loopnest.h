@@ -176,6 +176,26 @@ ln_status ln_correlation(int nsamples, int nfeat, const float *X, int ldx, float
                          void *stream);
 
 /*
+ * Covariance for callers that cannot allocate device memory (code that runs
+ * where cudaMalloc is not allowed or would exceed a fixed memory budget, such
+ * as inside an allocator, a memory-capped sandbox or a loop that must never
+ * enter the allocator). The paper has no counterpart to this entry point; it
+ * computes exactly what ln_covariance computes with LN_FORM_INTERNALIZED and
+ * LN_PREC_FP32, but takes no workspace: its scratch (the FP64 column
+ * statistics and per-block partial sums) is one fixed 8 MiB device array in
+ * the library, held on every GPU that loads the library until the process
+ * exits. Sizes whose scratch exceeds 8 MiB -- about
+ * 40*nfeat + 8*nfeat*ceil(nsamples/128) bytes -- give LN_ERR_INVALID_VALUE
+ * with a message; nothing is launched then. The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) and must come
+ * before any CUDA graph capture on that device. All calls share the array, so
+ * calls whose kernels may overlap on the GPU (unordered streams) race; calls
+ * in one stream are safe. X, cov and stream as in ln_covariance.
+ */
+ln_status ln_covariance_noalloc(int nsamples, int nfeat, const float *X, int ldx, float *cov, int ldcov,
+                                void *stream);
+
+/*
  * SYRK (polybench syrk, Sec. VIII): on the triangle chosen by `fill`,
  *   C[i][j] = alpha * sum_k A[i][k] * A[j][k] + beta * C[i][j]       A: n x k
  * SYR2K (polybench syr2k): C[i][j] = alpha * sum_k (A[i][k] B[j][k] +

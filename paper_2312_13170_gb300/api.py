@@ -66,6 +66,7 @@ _SIGS = {
     "ln_covariance_workspace_size": (_I, [_I, _I, _I, _I, _P]),
     "ln_covariance": (_I, [_I, _I, _P, _I, _P, _I, _P, _SZ, _I, _I, _P]),
     "ln_correlation": (_I, [_I, _I, _P, _I, _P, _I, _P, _SZ, _I, _I, _P]),
+    "ln_covariance_noalloc": (_I, [_I, _I, _P, _I, _P, _I, _P]),
     "ln_syrk_workspace_size": (_I, [_I, _I, _I, _I, _P]),
     "ln_syrk": (_I, [_I, _I, _I, _F, _P, _I, _F, _P, _I, _P, _SZ, _I, _I, _P]),
     "ln_syr2k_workspace_size": (_I, [_I, _I, _I, _I, _P]),
