@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the CPU baseline sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
     ap.add_argument("--suite", action="store_true", help="measure every workload and form, one JSON line each")
+    ap.add_argument("--only", default="", help="suite: comma-separated workloads (gemm,chain,cov,batched,backward)")
+    ap.add_argument("--modes", default="", help="suite: comma-separated form/precision pairs, e.g. internalized/3xbf16")
     return ap.parse_args()
 
 
@@ -384,9 +386,25 @@ def run_suite(args):
 
     modes = [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "bf16"), ("internalized", "3xbf16"),
              ("internalized", "6xbf16")]
+    if args.modes:
+        modes = [tuple(x.split("/")) for x in args.modes.split(",")]
+    only = set(args.only.split(",")) if args.only else {"gemm", "chain", "cov", "batched", "backward"}
     cores = oracle.max_threads()
 
     # -------------------------------------------------- GEMM 256^3
+    run_gemm_256(only, modes, api, inputs, oracle, cores, time_it, emit)
+    run_chain_2048(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
+    run_cov(only, modes, api, inputs, oracle, cores, time_it, emit, reps, hbm)
+    run_batched(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
+    run_backward(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
+    return 0
+
+
+def run_gemm_256(only, modes, api, inputs, oracle, cores, time_it, emit):
+    import torch
+
+    if "gemm" not in only:
+        return
     d = inputs.gemm_inputs(256, 256, 256, seed=0)
     t0 = time.perf_counter()
     ref = oracle.gemm(d["A"], d["B"], d["C"], d["alpha"], d["beta"])
@@ -401,7 +419,13 @@ def run_suite(args):
         ms = time_it(lambda: api.gemm(T["A"], T["B"], Cw, d["alpha"], d["beta"], form=form, prec=prec))
         emit("gemm 256^3 alpha=1.5 beta=1.2", "gemm", form, prec, 2 * 256 ** 3, 4 * 4 * 256 * 256, ms, err, cpu)
 
-    # -------------------------------------------------- chain 2048
+
+
+def run_chain_2048(only, modes, api, inputs, oracle, cores, time_it, emit, reps):
+    import torch
+
+    if "chain" not in only:
+        return
     n = 2048
     d = inputs.chain_inputs(n, seed=0)
     rows = 64
@@ -419,7 +443,13 @@ def run_suite(args):
                                             prec=prec, out=out), n=3 if form == "plain" else reps)
         emit("chain 2048^2", "gemm_chain", form, prec, 4.0 * n ** 3, 6 * 4 * n * n, ms, err, cpu)
 
-    # -------------------------------------------------- covariance / correlation 8192 x 2048
+
+
+def run_cov(only, modes, api, inputs, oracle, cores, time_it, emit, reps, hbm):
+    import torch
+
+    if "cov" not in only:
+        return
     ns, m = 8192, 2048
     X = inputs.cov_inputs(ns, m, seed=0)["X"]
     Xt = torch.from_numpy(X).cuda()
@@ -455,7 +485,13 @@ def run_suite(args):
         ms = time_it(lambda: api.correlation(Xt, form=form, prec=prec, out=cr), n=reps_here)
         emit("correlation 8192x2048", "correlation", form, prec, flops, (3 * 4 * ns * m + 4 * m * m), ms, err_r, cpu)
 
-    # -------------------------------------------------- batched SYRK / SYR2K, 512 instances, CUDA graph
+
+
+def run_batched(only, modes, api, inputs, oracle, cores, time_it, emit, reps):
+    import torch
+
+    if "batched" not in only:
+        return
     b = inputs.sym_batch_inputs(512, 32, 1536, seed=0)
     inst = b["instances"]
     nk = [(x["n"], x["k"]) for x in inst]
@@ -499,7 +535,13 @@ def run_suite(args):
             ms = time_it(g.replay, n=2 if form == "plain" else reps)
             emit("512 uneven instances, n,k log-uniform [32,1536], CUDA graph", op, form, prec, fl, by, ms, err, cpu)
 
-    # -------------------------------------------------- backward of sum(W .* corr(X)) + ||(A B) C||_F^2
+
+
+def run_backward(only, modes, api, inputs, oracle, cores, time_it, emit, reps):
+    import torch
+
+    if "backward" not in only:
+        return
     d = inputs.backward_inputs(4096, 1024, 1024, seed=0)
     Xb = torch.from_numpy(d["X"]).cuda()
     W = torch.from_numpy(d["W"]).cuda()
@@ -511,7 +553,7 @@ def run_suite(args):
     p, nb, mb = 1024, 4096, 1024
     # corr forward (triangle) + dZ = Z (W + W^T) + chain forward 4p^3 + chain adjoint 10p^3 (T reused)
     fl = float(nb) * mb * (mb + 1) + 2.0 * nb * mb * mb + 14.0 * p ** 3
-    for form, prec in (("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16")):
+    for form, prec in [m for m in modes if m[1] in ("fp32", "3xbf16")]:
         def step():
             Xg = Xb.detach().requires_grad_(True)
             Ag, Bg, Cg = (t.detach().requires_grad_(True) for t in (A, B, C))
@@ -524,7 +566,6 @@ def run_suite(args):
         ms = time_it(step, n=2 if form == "plain" else reps)
         emit("backward: X 4096x1024, W/A/B/C 1024^2", "fwd+bwd", form, prec, fl,
              4.0 * (5 * nb * mb + 2 * mb * mb + 10 * p * p), ms, err, cpu)
-    return 0
 
 
 def fp32_simt_peak():

@@ -185,7 +185,7 @@ ln_status ln_correlation(int nsamples, int nfeat, const float *X, int ldx, float
  * statistics and per-block partial sums) is one fixed 8 MiB device array in
  * the library, held on every GPU that loads the library until the process
  * exits. Sizes whose scratch exceeds 8 MiB -- about
- * 40*nfeat + 8*nfeat*ceil(nsamples/128) bytes -- give LN_ERR_INVALID_VALUE
+ * 40*nfeat + 8*nfeat*ceil(nsamples/256) bytes -- give LN_ERR_INVALID_VALUE
  * with a message; nothing is launched then. The first call on each device
  * looks up the array's device address (cudaGetSymbolAddress) and must come
  * before any CUDA graph capture on that device. All calls share the array, so

@@ -441,6 +441,7 @@ struct BatchPlan {
     long long *pack_off = nullptr;
     int *pack_prefix = nullptr;
     int *order = nullptr;
+    int *tile_owner = nullptr;
     int *queue = nullptr;
     char *pack = nullptr;
     long long total_tiles = 0, total_pack_tiles = 0;
@@ -505,6 +506,7 @@ void plan_batch(Ws &w, bool two, int count, const ln_sym_desc *h, ln_form form, 
     bp.pack_off = w.take<long long>(sizeof(long long) * 2 * (size_t)std::max(count, 1));
     bp.pack_prefix = w.take<int>(sizeof(int) * (count + 1));
     bp.order = w.take<int>(sizeof(int) * (size_t)std::max(count, 1));
+    bp.tile_owner = w.take<int>(sizeof(int) * (size_t)std::max<long long>(bp.total_tiles, 1));
     bp.queue = w.take<int>(sizeof(int));
     bp.pack = w.take<char>(batch_pack_bytes(two, count, h, prec_terms(prec)));
 }
@@ -535,11 +537,11 @@ ln_status run_batch(bool two, ln_fill fill, int count, const ln_sym_desc *h, con
         return simt_sym_batched(two, count, d, bp.tile_prefix, (int)bp.total_tiles, fill, alpha, beta, st);
     }
     const int P = prec_terms(prec);
-    LN_TRY(sym_batched_plan(two, count, d, fill, alpha, beta, bp.probs, bp.tile_prefix, bp.pack_off, bp.pack_prefix,
-                            bp.order, bp.pack, P, st));
+    LN_TRY(sym_batched_plan(two, count, d, fill, alpha, beta, bp.probs, bp.tile_prefix, bp.tile_owner, bp.pack_off,
+                            bp.pack_prefix, bp.order, bp.pack, P, st));
     LN_TRY(sym_batched_pack(two, count, d, bp.pack_off, bp.pack_prefix, bp.order, (int)bp.total_pack_tiles, bp.pack,
                             P, st));
-    return umma_contract_batched(bp.probs, bp.tile_prefix, count, (int)bp.total_tiles, bp.queue, P, st);
+    return umma_contract_batched(bp.probs, bp.tile_prefix, bp.tile_owner, (int)bp.total_tiles, bp.queue, P, st);
 }
 
 // ------------------------------------------------------------------ backward

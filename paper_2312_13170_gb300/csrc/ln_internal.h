@@ -186,8 +186,9 @@ bool inject_timeout_requested();
 // must hold 128 * (width / 128) * nt rows (zero padded).
 int umma_tile_n(int terms, int sym);
 ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st);
-ln_status umma_contract_batched(const UmmaProblem *d_probs, const int *d_tile_prefix, int nprob, int total_tiles,
-                                int *d_queue, int terms, cudaStream_t st);
+// d_tile_owner[t] = the problem (in d_probs order) that tile t belongs to.
+ln_status umma_contract_batched(const UmmaProblem *d_probs, const int *d_tile_prefix, const int *d_tile_owner,
+                                int total_tiles, int *d_queue, int terms, cudaStream_t st);
 ln_status umma_read_error(int *value);
 // batched planning on the device
 // ln_pack.cu: batched layout. The plan kernel orders instances by decreasing
@@ -195,8 +196,8 @@ ln_status umma_read_error(int *value);
 // descriptor and tile prefix sums (rank order); the pack kernel then packs
 // every instance's operands in one launch.
 ln_status sym_batched_plan(int is_syr2k, int count, const ln_sym_desc *d_descs, int fill, float alpha, float beta,
-                           UmmaProblem *d_probs, int *d_tile_prefix, long long *d_pack_off, int *d_pack_prefix,
-                           int *d_order, char *pack_base, int terms, cudaStream_t st);
+                           UmmaProblem *d_probs, int *d_tile_prefix, int *d_tile_owner, long long *d_pack_off,
+                           int *d_pack_prefix, int *d_order, char *pack_base, int terms, cudaStream_t st);
 ln_status sym_batched_pack(int is_syr2k, int count, const ln_sym_desc *d_descs, const long long *d_pack_off,
                            const int *d_pack_prefix, const int *d_order, int total_pack_tiles, char *pack_base,
                            int terms, cudaStream_t st);

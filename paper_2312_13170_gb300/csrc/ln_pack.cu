@@ -145,36 +145,74 @@ __global__ __launch_bounds__(256) void k_pack_multi(const __grid_constant__ Pack
     else pack_tile<0, P>(p, local % p.kt, local / p.kt, s);
 }
 
-// Ranks instances by decreasing work n*n*k (ties by index): order[rank] = i.
-__global__ void k_batch_rank(int count, const ln_sym_desc *__restrict__ descs, int *order) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    if (count > 8192) {  // too many to rank by counting; keep the caller's order
-        order[i] = i;
-        return;
-    }
-    const ln_sym_desc di = descs[i];
-    const double wi = (double)di.n * di.n * di.k;
-    int rank = 0;
-    for (int j = 0; j < count; ++j) {
-        const ln_sym_desc dj = descs[j];
-        const double wj = (double)dj.n * dj.n * dj.k;
-        rank += (wj > wi) || (wj == wi && j < i);
-    }
-    order[rank] = i;
-}
+// Batched layout, one CTA of 1024 threads: (1) rank instances by decreasing
+// work n*n*k (ties by index) so the queue hands out the largest first, keeping
+// the weights and the order in shared memory; (2) an exclusive block scan, in
+// rank order, of each instance's packed-operand bytes, lower-triangle tiles and
+// pack tiles; (3) write every instance's contraction descriptor. Batches of
+// more than RANK_MAX instances keep the caller's order.
+constexpr int PLAN_THREADS = 1024;
+constexpr int RANK_MAX = 8192;
 
-// Sequential layout in rank order (one thread): packed-operand offsets, tile
-// prefix sums and the contraction descriptor of every instance.
-__global__ void k_batch_layout(int is_syr2k, int count, const ln_sym_desc *__restrict__ descs, const int *order,
-                               int fill, float alpha, float beta, UmmaProblem *probs, int *tile_prefix,
-                               long long *pack_off, int *pack_prefix, char *pack_base, int terms) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    long long off = 0;
+__global__ __launch_bounds__(PLAN_THREADS) void k_batch_plan(int is_syr2k, int count,
+                                                             const ln_sym_desc *__restrict__ descs, int *order,
+                                                             int fill, float alpha, float beta, UmmaProblem *probs,
+                                                             int *tile_prefix, int *tile_owner, long long *pack_off,
+                                                             int *pack_prefix, char *pack_base, int terms) {
+    __shared__ float w[RANK_MAX];
+    __shared__ long long sb[PLAN_THREADS];
+    __shared__ int st[PLAN_THREADS], sp[PLAN_THREADS];
+    const int tid = threadIdx.x;
+    const bool ranked = count <= RANK_MAX;
+    if (ranked) {
+        for (int i = tid; i < count; i += PLAN_THREADS) {
+            const ln_sym_desc d = descs[i];
+            w[i] = (float)d.n * (float)d.n * (float)d.k;
+        }
+        __syncthreads();
+        for (int i = tid; i < count; i += PLAN_THREADS) {
+            const float wi = w[i];
+            int rank = 0;
+            for (int j = 0; j < count; ++j) rank += (w[j] > wi) || (w[j] == wi && j < i);
+            order[rank] = i;
+        }
+    } else {
+        for (int i = tid; i < count; i += PLAN_THREADS) order[i] = i;
+    }
+    __syncthreads();
+    __threadfence_block();
+    // each thread owns a contiguous run of ranks
+    const int per = (count + PLAN_THREADS - 1) / PLAN_THREADS;
+    const int r0 = tid * per, r1 = min(count, r0 + per);
+    long long bytes = 0;
     int tiles = 0, ptiles = 0;
-    for (int r = 0; r < count; ++r) {
+    for (int r = r0; r < r1; ++r) {
         const ln_sym_desc d = descs[order[r]];
+        if (d.n <= 0) continue;
         const int mt = (d.n + PK_ROWS - 1) / PK_ROWS;
+        const int kt = (d.k + PK_K - 1) / PK_K;
+        bytes += (long long)mt * kt * terms * PK_TILE_BYTES * (is_syr2k ? 2 : 1);
+        tiles += mt * (mt + 1) / 2;
+        ptiles += mt * kt * (is_syr2k ? 2 : 1);
+    }
+    sb[tid] = bytes;
+    st[tid] = tiles;
+    sp[tid] = ptiles;
+    __syncthreads();
+    for (int off = 1; off < PLAN_THREADS; off <<= 1) {  // inclusive Hillis-Steele scan
+        long long b2 = tid >= off ? sb[tid - off] : 0;
+        int t2 = tid >= off ? st[tid - off] : 0, p2 = tid >= off ? sp[tid - off] : 0;
+        __syncthreads();
+        sb[tid] += b2;
+        st[tid] += t2;
+        sp[tid] += p2;
+        __syncthreads();
+    }
+    long long off_b = sb[tid] - bytes;
+    int off_t = st[tid] - tiles, off_p = sp[tid] - ptiles;
+    for (int r = r0; r < r1; ++r) {
+        const ln_sym_desc d = descs[order[r]];
+        const int mt = d.n > 0 ? (d.n + PK_ROWS - 1) / PK_ROWS : 0;
         const int kt = (d.k + PK_K - 1) / PK_K;
         const long long one = (long long)mt * kt * terms * PK_TILE_BYTES;
         UmmaProblem p{};
@@ -183,10 +221,10 @@ __global__ void k_batch_layout(int is_syr2k, int count, const ln_sym_desc *__res
         p.mt = p.nt = mt;
         p.sym = 1;
         p.chunk_kt = UMMA_CHUNK_KT;
-        const char *pa = pack_base + off;
+        const char *pa = pack_base + off_b;
         const char *pb = is_syr2k ? pa + one : pa;
-        pack_off[2 * r] = off;
-        pack_off[2 * r + 1] = is_syr2k ? off + one : off;
+        pack_off[2 * r] = off_b;
+        pack_off[2 * r + 1] = is_syr2k ? off_b + one : off_b;
         if (is_syr2k) {
             p.seg[0].X = pa;
             p.seg[0].Y = pb;
@@ -207,16 +245,19 @@ __global__ void k_batch_layout(int is_syr2k, int count, const ln_sym_desc *__res
         p.epi.fill = fill;
         p.epi.sym_kind = SYM_AXPBY;
         probs[r] = p;
-        tile_prefix[r] = tiles;
-        pack_prefix[r] = ptiles;
+        tile_prefix[r] = off_t;
+        pack_prefix[r] = off_p;
         if (d.n > 0) {
-            off += one * (is_syr2k ? 2 : 1);
-            tiles += mt * (mt + 1) / 2;
-            ptiles += mt * kt * (is_syr2k ? 2 : 1);
+            for (int q = 0; q < mt * (mt + 1) / 2; ++q) tile_owner[off_t + q] = r;
+            off_b += one * (is_syr2k ? 2 : 1);
+            off_t += mt * (mt + 1) / 2;
+            off_p += mt * kt * (is_syr2k ? 2 : 1);
         }
     }
-    tile_prefix[count] = tiles;
-    pack_prefix[count] = ptiles;
+    if (tid == PLAN_THREADS - 1) {
+        tile_prefix[count] = st[tid];
+        pack_prefix[count] = sp[tid];
+    }
 }
 
 // Packs every instance's operands: a flat grid over all (rank, operand, row
@@ -298,11 +339,11 @@ ln_status pack_operands(const PackSrc *ps, int count, int terms, cudaStream_t st
 }
 
 ln_status sym_batched_plan(int is_syr2k, int count, const ln_sym_desc *d_descs, int fill, float alpha, float beta,
-                           UmmaProblem *d_probs, int *d_tile_prefix, long long *d_pack_off, int *d_pack_prefix,
-                           int *d_order, char *pack_base, int terms, cudaStream_t st) {
-    { LaunchScope ls_(FAM_PACK, st); k_batch_rank<<<(unsigned)ceil_div(count, 256), 256, 0, st>>>(count, d_descs, d_order); }
-    { LaunchScope ls_(FAM_PACK, st); k_batch_layout<<<1, 32, 0, st>>>(is_syr2k, count, d_descs, d_order, fill, alpha, beta, d_probs, d_tile_prefix,
-                                     d_pack_off, d_pack_prefix, pack_base, terms); }
+                           UmmaProblem *d_probs, int *d_tile_prefix, int *d_tile_owner, long long *d_pack_off,
+                           int *d_pack_prefix, int *d_order, char *pack_base, int terms, cudaStream_t st) {
+    LaunchScope ls_(FAM_PACK, st);
+    k_batch_plan<<<1, PLAN_THREADS, 0, st>>>(is_syr2k, count, d_descs, d_order, fill, alpha, beta, d_probs,
+                                             d_tile_prefix, d_tile_owner, d_pack_off, d_pack_prefix, pack_base, terms);
     return check_launch("batched plan");
 }
 

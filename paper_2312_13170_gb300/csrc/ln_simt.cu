@@ -159,11 +159,11 @@ __device__ void simt_tile(int M, int N, int K, const SimtOperands &op, const Epi
         const int buf = it & 1;
         const bool more = it + 1 < total;
         if (more) {
-            int seg = (it + 1) / kt;
-            c.A = op.A[seg];
-            c.B = op.B[seg];
-            c.lda = op.lda[seg];
-            c.ldb = op.ldb[seg];
+            const bool seg1 = (it + 1) >= kt;
+            c.A = seg1 ? op.A[1] : op.A[0];
+            c.B = seg1 ? op.B[1] : op.B[0];
+            c.lda = seg1 ? op.lda[1] : op.lda[0];
+            c.ldb = seg1 ? op.ldb[1] : op.ldb[0];
             c.a_vec = vec_ok(c.A, c.lda);
             c.b_vec = vec_ok(c.B, c.ldb);
             fetch<AT, BT>(c, ((it + 1) % kt) * TK, tid, ra, rb);
@@ -184,14 +184,15 @@ __device__ void simt_tile(int M, int N, int K, const SimtOperands &op, const Epi
         if (more) stash<AT, BT>(As[buf ^ 1], Bs[buf ^ 1], tid, ra, rb);
         __syncthreads();
     }
+    // per row: issue the row's eight epilogue loads, then its stores
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-        int i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
+        const int i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
+        float2 g[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            int j = j0 + (q < 4 ? tx * 4 + q : 64 + tx * 4 + (q - 4));
-            epi_store(epi, i, j, acc[r][q]);
-        }
+        for (int q = 0; q < 8; ++q) g[q] = epi_load(epi, i, j0 + (q < 4 ? tx * 4 + q : 64 + tx * 4 + (q - 4)));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) epi_apply(epi, i, j0 + (q < 4 ? tx * 4 + q : 64 + tx * 4 + (q - 4)), acc[r][q], g[q]);
     }
 }
 
@@ -204,7 +205,7 @@ __device__ __forceinline__ void tri_tile(int t, int &ti, int &tj) {
 }
 
 template <int AT, int BT>
-__global__ __launch_bounds__(256) void k_simt(int M, int N, int K, SimtOperands op, EpiParams epi, int sym) {
+__global__ __launch_bounds__(256, 2) void k_simt(int M, int N, int K, SimtOperands op, EpiParams epi, int sym) {
     int ti, tj;
     if (sym) {
         tri_tile(blockIdx.x, ti, tj);
@@ -216,7 +217,7 @@ __global__ __launch_bounds__(256) void k_simt(int M, int N, int K, SimtOperands 
 }
 
 // Batched SYRK/SYR2K: a flat grid over every instance's lower-triangle tiles.
-__global__ __launch_bounds__(256) void k_simt_sym_batched(int is_syr2k, const ln_sym_desc *__restrict__ descs,
+__global__ __launch_bounds__(256, 2) void k_simt_sym_batched(int is_syr2k, const ln_sym_desc *__restrict__ descs,
                                                           const int *__restrict__ prefix, int count, int fill,
                                                           float alpha, float beta) {
     int t = blockIdx.x;

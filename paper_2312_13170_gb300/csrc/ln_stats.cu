@@ -3,11 +3,12 @@
 //
 // The column mean and sum of squared deviations are the array reductions of
 // polybench covariance/correlation (paper Sec. VI-B, Sec. VIII). Internalized
-// form: each CTA reduces a 128-column x 128-row block with coalesced 128-bit
-// loads, accumulating in FP64 in registers, combines its 8 row groups in
-// shared memory and writes one FP64 partial per column; a second kernel adds
-// the partials in a fixed order (deterministic, no atomics). Two passes: the
-// mean first, then the squared deviations from it.
+// form: each CTA reduces a 128-column x 256-row block with coalesced 128-bit
+// loads, accumulating in registers (compensated FP32 pairs, see
+// k_col_partial), combines its 8 row groups in shared memory in FP64 and
+// writes one FP64 partial per column; a second kernel adds the partials in a
+// fixed order (deterministic, no atomics). Two passes: the mean first, then
+// the squared deviations from it.
 #include "ln_internal.h"
 
 namespace ln {
@@ -17,7 +18,7 @@ namespace {
 inline unsigned rows_grid(long long rows) { return (unsigned)(rows < 65535 ? rows : 65535); }
 
 constexpr int SC = 128;  // columns per CTA (32 threads x float4)
-constexpr int SR = 128;  // rows per CTA
+constexpr int SR = 256;  // rows per CTA
 
 __device__ __forceinline__ float4 ld4_guard(const float *row, int c, int m, bool vec) {
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -29,7 +30,26 @@ __device__ __forceinline__ float4 ld4_guard(const float *row, int c, int m, bool
     return v;
 }
 
+// s + t == a + b exactly (Knuth's error-free sum; no reassociation is allowed
+// because the library is compiled without fast-math).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &t) {
+    s = a + b;
+    const float bp = s - a;
+    t = (a - (s - bp)) + (b - bp);
+}
+
 // pass 0: partial sums of X; pass 1: partial sums of (X - mean)^2.
+// Each thread keeps its running sums as unevaluated FP32 pairs (hi + lo, hi
+// accumulating with error-free sums whose errors gather in lo). In pass 1 the
+// FP64 mean is split as mh + ml (two floats); the deviation from mh,
+// d = x - mh, is formed exactly as a pair and the thread accumulates S1 = sum d
+// and S2 = sum d^2 (squares carry their exact FMA residual). Its share of the
+// squared deviations from the FP64 mean then follows in FP64 as
+// S2 - 2 ml S1 + cnt ml^2, so ml never enters a product of small numbers.
+// The pairs are widened to FP64 for the combination across threads and
+// blocks. GB300 issues FP64 at a small fraction of its FP32 rate, so native
+// FP64 per element made this bandwidth-bound pass compute-bound; the pairs
+// keep FP64-level accuracy at FP32 speed.
 template <int PASS>
 __global__ __launch_bounds__(256) void k_col_partial(int n, int m, const float *__restrict__ X, long long ldx,
                                                      const double *__restrict__ mean, double *partials) {
@@ -38,27 +58,56 @@ __global__ __launch_bounds__(256) void k_col_partial(int n, int m, const float *
     const int c = blockIdx.x * SC + cx * 4;
     const int r0 = blockIdx.y * SR;
     const bool vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && ((ldx & 3) == 0);
-    double mu[4] = {0, 0, 0, 0};
+    float mh[4] = {0, 0, 0, 0};
+    double ml[4] = {0, 0, 0, 0};
     if (PASS == 1) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) mu[q] = (c + q < m) ? mean[c + q] : 0.0;
+        for (int q = 0; q < 4; ++q) {
+            const double mu = (c + q < m) ? mean[c + q] : 0.0;
+            mh[q] = (float)mu;
+            ml[q] = mu - (double)mh[q];
+        }
     }
-    double acc[4] = {0, 0, 0, 0};
-    for (int r = r0 + ry; r < min(n, r0 + SR); r += 8) {
+    float h1[4] = {0, 0, 0, 0}, l1[4] = {0, 0, 0, 0};  // sum x (pass 0) or sum d (pass 1)
+    float h2[4] = {0, 0, 0, 0}, l2[4] = {0, 0, 0, 0};  // sum d^2 (pass 1)
+    int cnt = 0;
+    const int r1 = min(n, r0 + SR);
+#pragma unroll 4
+    for (int r = r0 + ry; r < r1; r += 8) {
         float4 v = ld4_guard(X + (long long)r * ldx, c, m, vec);
         float x[4] = {v.x, v.y, v.z, v.w};
+        ++cnt;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
+            float s, t;
             if (PASS == 0) {
-                acc[q] += (double)x[q];
+                two_sum(h1[q], x[q], s, t);
+                h1[q] = s;
+                l1[q] += t;
             } else {
-                double d = (double)x[q] - mu[q];
-                acc[q] = fma(d, d, acc[q]);
+                float dh, dl;
+                two_sum(x[q], -mh[q], dh, dl);
+                two_sum(h1[q], dh, s, t);
+                h1[q] = s;
+                l1[q] += t + dl;
+                const float p = dh * dh;
+                const float pe = fmaf(dh, dh, -p) + (2.0f * dh + dl) * dl;
+                two_sum(h2[q], p, s, t);
+                h2[q] = s;
+                l2[q] += t + pe;
             }
         }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) red[ry][cx * 4 + q] = acc[q];
+    for (int q = 0; q < 4; ++q) {
+        const double s1 = (double)h1[q] + (double)l1[q];
+        if (PASS == 0) {
+            red[ry][cx * 4 + q] = s1;
+        } else {
+            const double s2 = (double)h2[q] + (double)l2[q];
+            red[ry][cx * 4 + q] = s2 - 2.0 * ml[q] * s1 + (double)cnt * ml[q] * ml[q];
+        }
+    }
     __syncthreads();
     if (threadIdx.x < SC) {
         int col = blockIdx.x * SC + threadIdx.x;

@@ -44,10 +44,19 @@ constexpr int MAX_NACC = 4;
 constexpr int TMEM_COLS = 512;
 constexpr int MAX_STAGES = 8;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
-constexpr int CTL_BYTES = 1024;
+constexpr int CTL_BYTES = 2048;
 constexpr int SMEM_BUDGET = 227 * 1024;
 
 enum : int { ERR_PRODUCER = 1, ERR_MMA = 2, ERR_EPILOGUE = 4, ERR_DRAIN = 8 };
+
+// One scheduled tile: the producer resolves it once (tile index -> problem,
+// row tile, column tile) and, for batched launches, copies the problem's
+// descriptor into shared memory; the MMA and epilogue roles read the slot and
+// release it (sempty) when they have finished the tile.
+struct SchedSlot {
+    int t, mi, ni, pad;
+    UmmaProblem prob;
+};
 
 struct Ctl {
     uint64_t full[MAX_STAGES];
@@ -57,9 +66,9 @@ struct Ctl {
     uint64_t sfull[SCHED];
     uint64_t sempty[SCHED];
     uint64_t drain;
-    int sched[SCHED];
     uint32_t tmem_base;
     volatile int abort;
+    SchedSlot slot[SCHED];
 };
 static_assert(sizeof(Ctl) <= CTL_BYTES, "control block too large");
 
@@ -150,6 +159,20 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
                  : "memory");
 }
 
+// 32 lanes x 16 consecutive columns: thread = lane, v[q] = column q.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     uint32_t r[32];
     asm volatile(
@@ -180,20 +203,17 @@ struct TileRef {
     int mi, ni;
 };
 
+// Tile index -> (problem, row tile, column tile). Batched launches look the
+// problem up in the tile -> instance map the planning kernel wrote.
 template <int BATCHED>
 __device__ __forceinline__ TileRef resolve(int t, const UmmaProblem *single, const UmmaProblem *probs,
-                                           const int *prefix, int nprob) {
+                                           const int *prefix, const int *owner) {
     TileRef r;
     int local = t;
     if (BATCHED) {
-        int lo = 0, hi = nprob - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (__ldg(prefix + mid) <= t) lo = mid;
-            else hi = mid - 1;
-        }
-        r.p = probs + lo;
-        local = t - __ldg(prefix + lo);
+        const int i = __ldg(owner + t);
+        r.p = probs + i;
+        local = t - __ldg(prefix + i);
     } else {
         r.p = single;
     }
@@ -204,6 +224,10 @@ __device__ __forceinline__ TileRef resolve(int t, const UmmaProblem *single, con
         r.ni = local - r.mi * r.p->nt;
     }
     return r;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 template <int P>
@@ -301,12 +325,93 @@ __device__ __forceinline__ void epi_chunk(const EpiParams &e, int row, int col0,
     for (int q = 0; q < 32; ++q) epi_store(e, row, col0 + q, v[q]);
 }
 
+// ---------------------------------------------------------------- symmetric epilogue of one 32-column chunk
+// Row `row`, columns col0..col0+31 of a lower-triangle tile. All loads the
+// chunk needs (C for alpha*acc + beta*C, rs for correlation) are issued before
+// any store, so a thread waits for one memory latency per chunk rather than
+// one per element. The lower triangle is written along the row (float4 when
+// aligned); the mirrored upper triangle is written column by column, where the
+// 32 lanes (consecutive rows) make each store one contiguous 128-byte run.
+__device__ __forceinline__ void epi_sym32(const EpiParams &e, int row, int col0, const float *v, bool diag) {
+    if (row >= e.M) return;
+    bool ok[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) ok[q] = (col0 + q < e.N) && (!diag || col0 + q <= row);
+    const bool dense = !diag && col0 + 31 < e.N;
+    float val[32];
+    if (e.sym_kind == SYM_CORR) {
+        const float ri = e.rs[row];
+        float rj[32];
+        if (dense && ((reinterpret_cast<uintptr_t>(e.rs + col0) & 15) == 0)) {
+#pragma unroll
+            for (int q = 0; q < 32; q += 4) {
+                float4 t = *reinterpret_cast<const float4 *>(e.rs + col0 + q);
+                rj[q] = t.x;
+                rj[q + 1] = t.y;
+                rj[q + 2] = t.z;
+                rj[q + 3] = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) rj[q] = ok[q] ? e.rs[col0 + q] : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 32; ++q) val[q] = (col0 + q == row) ? 1.0f : v[q] * ri * rj[q];
+    } else if (e.sym_kind == SYM_SCALE || e.beta == 0.0f) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) val[q] = e.alpha * v[q];
+    } else {
+        float c[32];
+        if (e.fill == LN_FILL_UPPER) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) c[q] = ok[q] ? e.C[(long long)(col0 + q) * e.ldc + row] : 0.0f;
+        } else {
+            const float *src = e.C + (long long)row * e.ldc + col0;
+            if (dense && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
+#pragma unroll
+                for (int q = 0; q < 32; q += 4) {
+                    float4 t = *reinterpret_cast<const float4 *>(src + q);
+                    c[q] = t.x;
+                    c[q + 1] = t.y;
+                    c[q + 2] = t.z;
+                    c[q + 3] = t.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) c[q] = ok[q] ? src[q] : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 32; ++q) val[q] = fmaf(e.beta, c[q], e.alpha * v[q]);
+    }
+    const bool write_lower = !(e.sym_kind == SYM_AXPBY && e.fill == LN_FILL_UPPER);
+    const bool write_upper = !(e.sym_kind == SYM_AXPBY && e.fill == LN_FILL_LOWER);
+    if (write_lower) {
+        float *dst = e.C + (long long)row * e.ldc + col0;
+        if (dense && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+#pragma unroll
+            for (int q = 0; q < 32; q += 4)
+                *reinterpret_cast<float4 *>(dst + q) = make_float4(val[q], val[q + 1], val[q + 2], val[q + 3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                if (ok[q]) dst[q] = val[q];
+        }
+    }
+    if (write_upper) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+            if (ok[q] && (col0 + q != row || !write_lower)) e.C[(long long)(col0 + q) * e.ldc + row] = val[q];
+    }
+}
+
 // ---------------------------------------------------------------- the kernel
 template <int P, int BN, int BATCHED>
 __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_constant__ UmmaProblem single,
                                                                   const UmmaProblem *__restrict__ probs,
-                                                                  const int *__restrict__ prefix, int nprob,
-                                                                  int total_tiles, int *queue) {
+                                                                  const int *__restrict__ prefix,
+                                                                  const int *__restrict__ owner, int total_tiles,
+                                                                  int *queue) {
     using C = Cfg<P, BN>;
     using PR = Products<P>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -362,11 +467,18 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                 if (t >= total_tiles) t = -1;
                 const int s = sidx % SCHED;
                 if (!wait_phase(ctl, &ctl->sempty[s], ((sidx / SCHED) & 1) ^ 1, ERR_PRODUCER)) break;
-                ctl->sched[s] = t;
+                SchedSlot &sl = ctl->slot[s];
+                TileRef tr{&single, 0, 0};
+                if (t >= 0) {
+                    tr = resolve<BATCHED>(t, &single, probs, prefix, owner);
+                    if (BATCHED) sl.prob = *tr.p;
+                    sl.mi = tr.mi;
+                    sl.ni = tr.ni;
+                }
+                sl.t = t;
                 mbar_arrive(&ctl->sfull[s]);
                 ++sidx;
                 if (t < 0) break;
-                const TileRef tr = resolve<BATCHED>(t, &single, probs, prefix, nprob);
                 const UmmaProblem &pb = *tr.p;
                 if (pb.inject_timeout) break;  // nothing arrives on full[]: the MMA wait runs out
                 bool ok = true;
@@ -411,12 +523,10 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
             for (;;) {
                 const int s = sidx % SCHED;
                 if (!wait_phase(ctl, &ctl->sfull[s], (sidx / SCHED) & 1, ERR_MMA)) break;
-                const int t = ctl->sched[s];
-                mbar_arrive(&ctl->sempty[s]);
+                const SchedSlot &sl = ctl->slot[s];
                 ++sidx;
-                if (t < 0) break;
-                const TileRef tr = resolve<BATCHED>(t, &single, probs, prefix, nprob);
-                const UmmaProblem &pb = *tr.p;
+                if (sl.t < 0) break;
+                const UmmaProblem &pb = BATCHED ? sl.prob : single;
                 const int ktot = pb.nseg * pb.kt;
                 const int ck = pb.chunk_kt > 0 ? pb.chunk_kt : (ktot > 0 ? ktot : 1);
                 bool ok = true;
@@ -456,6 +566,7 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                     ++acc;
                 }
                 if (!ok) break;
+                mbar_arrive(&ctl->sempty[s]);
             }
             // every MMA this thread issued has completed before TMEM is freed
             umma_commit(&ctl->drain);
@@ -471,16 +582,41 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
             const int s = sidx % SCHED;
             bool ok = wait_phase(ctl, &ctl->sfull[s], (sidx / SCHED) & 1, ERR_EPILOGUE);
             if (!__all_sync(0xffffffffu, ok)) break;
-            const int t = ctl->sched[s];
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&ctl->sempty[s]);
+            const SchedSlot &sl = ctl->slot[s];
             ++sidx;
-            if (t < 0) break;
-            const TileRef tr = resolve<BATCHED>(t, &single, probs, prefix, nprob);
-            const UmmaProblem &pb = *tr.p;
+            if (sl.t < 0) break;
+            const TileRef tr{nullptr, sl.mi, sl.ni};
+            const UmmaProblem &pb = BATCHED ? sl.prob : single;
             const int ktot = pb.nseg * pb.kt;
             const int ck = pb.chunk_kt > 0 ? pb.chunk_kt : (ktot > 0 ? ktot : 1);
             const int nch = (ktot + ck - 1) / ck;
+            {
+                // bring the values the final epilogue reads (C or D) towards L2
+                // while the tile's MMAs run
+                const EpiParams &pe = pb.epi;
+                const int prow = tr.mi * BM + quarter * 32 + lane;
+                const int pcol = tr.ni * BN + col_base;
+                if (pe.beta != 0.0f && prow < pe.M && pcol < pe.N) {
+                    if (pe.mode == EPI_GEMM || (pe.mode == EPI_SYM && pe.sym_kind == SYM_AXPBY && pe.fill != LN_FILL_UPPER)) {
+                        const float *r0 = pe.C + (long long)prow * pe.ldc + pcol;
+#pragma unroll
+                        for (int q = 0; q < 128; q += 32)
+                            if (pcol + q < pe.N) prefetch_l2(r0 + q);
+                    } else if (pe.mode == EPI_EF) {
+                        const float *r0 = pe.D + (long long)prow * pe.ld_ef + pcol;
+#pragma unroll
+                        for (int q = 0; q < 128; q += 32)
+                            if (pcol + q < pe.N) prefetch_l2(r0 + q);
+                    } else if (pe.mode == EPI_SYM && pe.sym_kind == SYM_AXPBY) {
+                        const int wrow = tr.mi * BM + quarter * 32;  // the warp's first row (< M here)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int j = pcol + lane * 4 + q;
+                            if (j < pe.N) prefetch_l2(pe.C + (long long)j * pe.ldc + wrow);
+                        }
+                    }
+                }
+            }
             // running FP32 sum of this thread's 128 outputs: each TMEM chunk is
             // added here with round-to-nearest adds
             float sum[128];
@@ -493,11 +629,11 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                 if (!ok) break;
                 tc_fence_after();
 #pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + col_base + g * 32), v);
+                for (int g = 0; g < 8; ++g) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + col_base + g * 16), v);
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) sum[g * 32 + q] += v[q];
+                    for (int q = 0; q < 16; ++q) sum[g * 16 + q] += v[q];
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -519,13 +655,16 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                     for (int cc = 0; cc < 4; ++cc)
                         store_chunk<P>(tile0, rloc, (g & 1) * 4 + cc, &sum[g * 32 + cc * 8]);
                 }
-            } else if (e.mode == EPI_SYM) {
+            } else if (BN == 128 && e.mode == EPI_SYM) {  // symmetric problems always use square tiles
+                const bool diag = tr.mi == tr.ni;
 #pragma unroll
-                for (int q = 0; q < 128; ++q) epi_store(e, row, col0 + q, sum[q]);
+                for (int g = 0; g < 4; ++g) epi_sym32(e, row, col0 + g * 32, &sum[g * 32], diag);
             } else {
 #pragma unroll
                 for (int g = 0; g < 4; ++g) epi_chunk(e, row, col0 + g * 32, &sum[g * 32]);
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->sempty[s]);
         }
     }
 
@@ -539,7 +678,7 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
 }
 
 template <int P, int BN, int BATCHED>
-ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int *prefix, int nprob, int total,
+ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int *prefix, const int *owner, int total,
                  int *queue, cudaStream_t st) {
     using C = Cfg<P, BN>;
     auto kern = k_umma<P, BN, BATCHED>;
@@ -556,26 +695,26 @@ ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int 
     UmmaProblem dummy{};
     {
         LaunchScope ls_(FAM_UMMA, st);
-        kern<<<grid, C::NTHREADS, C::SMEM, st>>>(single ? *single : dummy, probs, prefix, nprob, total, queue);
+        kern<<<grid, C::NTHREADS, C::SMEM, st>>>(single ? *single : dummy, probs, prefix, owner, total, queue);
     }
     return check_launch("tcgen05 contraction");
 }
 
 template <int BATCHED>
 ln_status dispatch(int terms, int bn, const UmmaProblem *single, const UmmaProblem *probs, const int *prefix,
-                   int nprob, int total, int *queue, cudaStream_t st) {
+                   const int *owner, int total, int *queue, cudaStream_t st) {
     if (bn == 256) {
         switch (terms) {
-            case 1: return launch<1, 256, BATCHED>(single, probs, prefix, nprob, total, queue, st);
-            case 2: return launch<2, 256, BATCHED>(single, probs, prefix, nprob, total, queue, st);
+            case 1: return launch<1, 256, BATCHED>(single, probs, prefix, owner, total, queue, st);
+            case 2: return launch<2, 256, BATCHED>(single, probs, prefix, owner, total, queue, st);
             default: break;
         }
         return fail(LN_ERR_INVALID_VALUE, "no 256-wide tile for %d split terms", terms);
     }
     switch (terms) {
-        case 1: return launch<1, 128, BATCHED>(single, probs, prefix, nprob, total, queue, st);
-        case 2: return launch<2, 128, BATCHED>(single, probs, prefix, nprob, total, queue, st);
-        case 3: return launch<3, 128, BATCHED>(single, probs, prefix, nprob, total, queue, st);
+        case 1: return launch<1, 128, BATCHED>(single, probs, prefix, owner, total, queue, st);
+        case 2: return launch<2, 128, BATCHED>(single, probs, prefix, owner, total, queue, st);
+        case 3: return launch<3, 128, BATCHED>(single, probs, prefix, owner, total, queue, st);
         default: return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
     }
 }
@@ -588,14 +727,14 @@ ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st) {
     long long tiles = p.sym ? (long long)p.mt * (p.mt + 1) / 2 : (long long)p.mt * p.nt;
     if (tiles == 0) return LN_SUCCESS;
     if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many output tiles");
-    return dispatch<0>(terms, umma_tile_n(terms, p.sym), &p, nullptr, nullptr, 1, (int)tiles, nullptr, st);
+    return dispatch<0>(terms, umma_tile_n(terms, p.sym), &p, nullptr, nullptr, nullptr, (int)tiles, nullptr, st);
 }
 
-ln_status umma_contract_batched(const UmmaProblem *d_probs, const int *d_tile_prefix, int nprob, int total_tiles,
-                                int *d_queue, int terms, cudaStream_t st) {
+ln_status umma_contract_batched(const UmmaProblem *d_probs, const int *d_tile_prefix, const int *d_tile_owner,
+                                int total_tiles, int *d_queue, int terms, cudaStream_t st) {
     if (total_tiles == 0) return LN_SUCCESS;
     LN_CUDA_TRY(cudaMemsetAsync(d_queue, 0, sizeof(int), st));
-    return dispatch<1>(terms, 128, nullptr, d_probs, d_tile_prefix, nprob, total_tiles, d_queue, st);
+    return dispatch<1>(terms, 128, nullptr, d_probs, d_tile_prefix, d_tile_owner, total_tiles, d_queue, st);
 }
 
 ln_status umma_read_error(int *value) {
