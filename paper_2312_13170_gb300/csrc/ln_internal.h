@@ -186,6 +186,8 @@ bool inject_timeout_requested();
 // must hold 128 * (width / 128) * nt rows (zero padded).
 int umma_tile_n(int terms, int sym);
 ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st);
+ln_status umma_contract_sym(const UmmaProblem &p, int terms, cudaStream_t st);  // ln_umma_sym.cu
+ln_status umma_read_error_sym(int *value);
 // d_tile_owner[t] = the problem (in d_probs order) that tile t belongs to.
 ln_status umma_contract_batched(const UmmaProblem *d_probs, const int *d_tile_prefix, const int *d_tile_owner,
                                 int total_tiles, int *d_queue, int terms, cudaStream_t st);

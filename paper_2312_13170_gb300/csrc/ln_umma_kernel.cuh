@@ -28,15 +28,19 @@
 // sets the CTA's abort flag and the library's device error word, every role
 // leaves its loop, in-flight copies and MMAs are waited for (again bounded),
 // TMEM is freed and the kernel returns. ln_stream_check() reports it.
+#pragma once
+
 #include "ln_epilogue.cuh"
 #include "ln_internal.h"
 #include "ln_split.cuh"
 
 namespace ln {
 
-__device__ int g_umma_error;
-
 namespace {
+
+// Device error word of the translation unit that includes this header (each
+// tcgen05 translation unit has its own; umma_read_error reads them all).
+__device__ int g_umma_error;
 
 constexpr int BM = 128;
 constexpr int SCHED = 4;
@@ -102,12 +106,17 @@ __device__ __forceinline__ unsigned long long gtimer() {
 }
 
 // Bounded wait for the phase of `b` with the given parity. With honor_abort,
-// returns false as soon as another role has aborted.
-__device__ bool wait_phase(Ctl *ctl, uint64_t *b, uint32_t parity, int who, bool honor_abort = true) {
+// returns false as soon as another role has aborted. A waiter that may wait
+// long (epilogue, producer) passes sleep_ns > 0: after a few polls it sleeps
+// between polls, so it does not take issue slots from the MMA-issuing thread
+// that shares its SM sub-partition; the MMA thread polls without sleeping.
+__device__ bool wait_phase(Ctl *ctl, uint64_t *b, uint32_t parity, int who, bool honor_abort = true,
+                           unsigned sleep_ns = 0) {
     if (mbar_try_wait(b, parity)) return true;
     const unsigned long long t0 = gtimer();
     for (uint32_t n = 1;; ++n) {
         if (mbar_try_wait(b, parity)) return true;
+        if (sleep_ns && n > 4) __nanosleep(sleep_ns);
         if ((n & 31) == 0) {
             if (honor_abort && ctl->abort) return false;
             if (gtimer() - t0 > WAIT_NS) {
@@ -159,34 +168,23 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-// 32 lanes x 16 consecutive columns: thread = lane, v[q] = column q.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// 32 lanes x 16 consecutive columns, without the wait: r is valid only after
+// tmem_wait() and tmem_after_wait(r).
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Ties registers written by tcgen05.ld to a point after tmem_wait(): the empty
+// volatile statements cannot move above the wait, and every later use reads
+// the value they "produce".
+__device__ __forceinline__ void tmem_after_wait(uint32_t (&r)[16]) {
 #pragma unroll
-    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+    for (int q = 0; q < 16; ++q) asm volatile("" : "+r"(r[q]));
 }
 
 // ---------------------------------------------------------------- tile scheduling
@@ -264,9 +262,12 @@ struct Cfg {
     static constexpr int A_BYTES = P * PK_TILE_BYTES;
     static constexpr int B_BYTES = P * HALVES * PK_TILE_BYTES;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-    static constexpr int STAGES_RAW = (SMEM_BUDGET - 2 * CTL_BYTES) / STAGE_BYTES;
+    static constexpr int SCRATCH_BYTES = NEPI * 32 * 32 * 4;  // one 32 x 32 FP32 block per epilogue warp
+    // 1 KiB of slack lets the kernel align the control block and stages to 1 KiB
+    static constexpr int STAGES_RAW = (SMEM_BUDGET - 1024 - CTL_BYTES - SCRATCH_BYTES) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_RAW > MAX_STAGES ? MAX_STAGES : STAGES_RAW;
-    static constexpr int SMEM = 2 * CTL_BYTES + STAGES * STAGE_BYTES;
+    static constexpr int SMEM = 1024 + CTL_BYTES + STAGES * STAGE_BYTES + SCRATCH_BYTES;
+    static constexpr int NLD = BN == 128 ? 4 : 2;  // tcgen05.ld (x16) in flight per wait
     static_assert(NACC <= MAX_NACC && STAGES >= 2, "tile configuration does not fit");
 };
 
@@ -405,8 +406,83 @@ __device__ __forceinline__ void epi_sym32(const EpiParams &e, int row, int col0,
     }
 }
 
+// Epilogue kinds, a template parameter so that each instantiation carries only
+// the store code it needs.
+enum : int { EK_PACK = 0, EK_EF = 1, EK_GEMM = 2, EK_SYM = 3 };
+
+// ---------------------------------------------------------------- warp-cooperative 32 x 32 block epilogue
+// The accumulator arrives with one output row per lane (TMEM lane = row). Row-
+// major global accesses from that layout send 32 separate requests per
+// instruction, so stores would be limited by the memory request rate. The warp
+// therefore stages its 32 x 32 block in shared memory (16-byte chunks
+// XOR-swizzled by row, conflict-free) and reads it back so that lanes
+// 8r'..8r'+7 hold one row's 32 consecutive values: with aligned data every
+// LDG.128 / STG.128 covers four whole 128-byte row segments. Mirrored
+// (transposed) stores of symmetric outputs are contiguous across lanes in the
+// row-per-lane layout and are written from it. Ragged edges, diagonal blocks of
+// symmetric outputs (only i >= j is produced) and unaligned data are handled
+// element by element within the same scheme.
+__device__ __forceinline__ bool aligned16(const void *p, long long ld) {
+    return ((reinterpret_cast<uintptr_t>(p) & 15) == 0) && ((ld & 3) == 0);
+}
+
+template <int EK>
+__device__ __forceinline__ bool block_epilogue(const EpiParams &e, float *sc, int wrow0, int c0, const float *v,
+                                               int lane) {
+    if (wrow0 + 31 >= e.M || c0 + 31 >= e.N) return false;
+    if (EK == EK_EF) {
+        if (!aligned16(e.E, e.ld_ef) || !aligned16(e.F, e.ld_ef) || (e.beta != 0.0f && !aligned16(e.D, e.ld_ef)))
+            return false;
+    } else if (!aligned16(e.C, e.ldc)) {
+        return false;
+    }
+    // stage: lane = row, 8 chunks of 4 values, chunk k of row r at (k ^ (r & 7))
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        *reinterpret_cast<float4 *>(sc + lane * 32 + ((k ^ (lane & 7)) << 2)) =
+            make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    __syncwarp();
+    const int ch = lane & 7;  // this lane's 16-byte chunk of a row
+    const int col = c0 + ch * 4;
+    const bool need_in = (EK == EK_GEMM || EK == EK_EF) && e.beta != 0.0f;
+    const float *src = EK == EK_EF ? e.D : e.C;
+    const long long lds = EK == EK_EF ? e.ld_ef : e.ldc;
+    // two halves of 16 rows: per half, all loads first, then the stores
+#pragma unroll
+    for (int h0 = 0; h0 < 8; h0 += 4) {
+        float4 x[4], in[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int r = (h0 + h) * 4 + (lane >> 3);
+            x[h] = *reinterpret_cast<const float4 *>(sc + r * 32 + ((ch ^ (r & 7)) << 2));
+            if (need_in) in[h] = *reinterpret_cast<const float4 *>(src + (long long)(wrow0 + r) * lds + col);
+        }
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int row = wrow0 + (h0 + h) * 4 + (lane >> 3);
+            const float4 o = x[h];
+            float4 f = make_float4(e.alpha * o.x, e.alpha * o.y, e.alpha * o.z, e.alpha * o.w);
+            if (need_in) {
+                f.x = fmaf(e.beta, in[h].x, f.x);
+                f.y = fmaf(e.beta, in[h].y, f.y);
+                f.z = fmaf(e.beta, in[h].z, f.z);
+                f.w = fmaf(e.beta, in[h].w, f.w);
+            }
+            if (EK == EK_EF) {
+                const long long off = (long long)row * e.ld_ef + col;
+                *reinterpret_cast<float4 *>(e.E + off) = o;
+                *reinterpret_cast<float4 *>(e.F + off) = f;
+            } else {
+                *reinterpret_cast<float4 *>(e.C + (long long)row * e.ldc + col) = f;
+            }
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
 // ---------------------------------------------------------------- the kernel
-template <int P, int BN, int BATCHED>
+template <int P, int BN, int BATCHED, int EK>
 __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_constant__ UmmaProblem single,
                                                                   const UmmaProblem *__restrict__ probs,
                                                                   const int *__restrict__ prefix,
@@ -420,6 +496,7 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
     const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
     Ctl *ctl = reinterpret_cast<Ctl *>(smem_raw + pad);
     const uint32_t stage0 = raw + pad + CTL_BYTES;
+    float *const scratch = reinterpret_cast<float *>(smem_raw + pad + CTL_BYTES + C::STAGES * C::STAGE_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -466,12 +543,12 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                 }
                 if (t >= total_tiles) t = -1;
                 const int s = sidx % SCHED;
-                if (!wait_phase(ctl, &ctl->sempty[s], ((sidx / SCHED) & 1) ^ 1, ERR_PRODUCER)) break;
+                if (!wait_phase(ctl, &ctl->sempty[s], ((sidx / SCHED) & 1) ^ 1, ERR_PRODUCER, true, 64)) break;
                 SchedSlot &sl = ctl->slot[s];
                 TileRef tr{&single, 0, 0};
                 if (t >= 0) {
                     tr = resolve<BATCHED>(t, &single, probs, prefix, owner);
-                    if (BATCHED) sl.prob = *tr.p;
+                    sl.prob = *tr.p;  // roles read the problem from shared memory, not from registers
                     sl.mi = tr.mi;
                     sl.ni = tr.ni;
                 }
@@ -486,7 +563,7 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                     const char *xb = pb.seg[sg].X + (size_t)tr.mi * pb.x_kt * C::A_BYTES;
                     for (int kt = 0; kt < pb.kt; ++kt) {
                         const int st = it % C::STAGES;
-                        if (!wait_phase(ctl, &ctl->empty[st], ((it / C::STAGES) & 1) ^ 1, ERR_PRODUCER)) {
+                        if (!wait_phase(ctl, &ctl->empty[st], ((it / C::STAGES) & 1) ^ 1, ERR_PRODUCER, true, 32)) {
                             ok = false;
                             break;
                         }
@@ -514,7 +591,7 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
             }
             // wait for this CTA's copies still in flight
             for (int j = (it > C::STAGES ? it - C::STAGES : 0); j < it; ++j)
-                wait_phase(ctl, &ctl->full[j % C::STAGES], (j / C::STAGES) & 1, ERR_DRAIN, false);
+                wait_phase(ctl, &ctl->full[j % C::STAGES], (j / C::STAGES) & 1, ERR_DRAIN, false, 256);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
@@ -526,7 +603,7 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                 const SchedSlot &sl = ctl->slot[s];
                 ++sidx;
                 if (sl.t < 0) break;
-                const UmmaProblem &pb = BATCHED ? sl.prob : single;
+                const UmmaProblem &pb = sl.prob;
                 const int ktot = pb.nseg * pb.kt;
                 const int ck = pb.chunk_kt > 0 ? pb.chunk_kt : (ktot > 0 ? ktot : 1);
                 bool ok = true;
@@ -570,7 +647,7 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
             }
             // every MMA this thread issued has completed before TMEM is freed
             umma_commit(&ctl->drain);
-            wait_phase(ctl, &ctl->drain, 0, ERR_DRAIN, false);
+            wait_phase(ctl, &ctl->drain, 0, ERR_DRAIN, false, 256);
         }
     } else {
         // ------------------------------------------------------------ epilogue warps
@@ -580,13 +657,13 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
         int sidx = 0, acc = 0;
         for (;;) {
             const int s = sidx % SCHED;
-            bool ok = wait_phase(ctl, &ctl->sfull[s], (sidx / SCHED) & 1, ERR_EPILOGUE);
+            bool ok = wait_phase(ctl, &ctl->sfull[s], (sidx / SCHED) & 1, ERR_EPILOGUE, true, 128);
             if (!__all_sync(0xffffffffu, ok)) break;
             const SchedSlot &sl = ctl->slot[s];
             ++sidx;
             if (sl.t < 0) break;
             const TileRef tr{nullptr, sl.mi, sl.ni};
-            const UmmaProblem &pb = BATCHED ? sl.prob : single;
+            const UmmaProblem &pb = sl.prob;
             const int ktot = pb.nseg * pb.kt;
             const int ck = pb.chunk_kt > 0 ? pb.chunk_kt : (ktot > 0 ? ktot : 1);
             const int nch = (ktot + ck - 1) / ck;
@@ -596,7 +673,7 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                 const EpiParams &pe = pb.epi;
                 const int prow = tr.mi * BM + quarter * 32 + lane;
                 const int pcol = tr.ni * BN + col_base;
-                if (pe.beta != 0.0f && prow < pe.M && pcol < pe.N) {
+                if (EK != EK_PACK && pe.beta != 0.0f && prow < pe.M && pcol < pe.N) {
                     if (pe.mode == EPI_GEMM || (pe.mode == EPI_SYM && pe.sym_kind == SYM_AXPBY && pe.fill != LN_FILL_UPPER)) {
                         const float *r0 = pe.C + (long long)prow * pe.ldc + pcol;
 #pragma unroll
@@ -624,16 +701,25 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
             for (int q = 0; q < 128; ++q) sum[q] = 0.0f;
             for (int c = 0; c < nch && ok; ++c) {
                 const int b = acc % C::NACC;
-                ok = wait_phase(ctl, &ctl->tfull[b], (acc / C::NACC) & 1, ERR_EPILOGUE);
+                ok = wait_phase(ctl, &ctl->tfull[b], (acc / C::NACC) & 1, ERR_EPILOGUE, true, 128);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 tc_fence_after();
 #pragma unroll
-                for (int g = 0; g < 8; ++g) {
-                    float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + col_base + g * 16), v);
+                for (int g0 = 0; g0 < 8; g0 += C::NLD) {
+                    uint32_t r[C::NLD][16];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) sum[g * 16 + q] += v[q];
+                    for (int j = 0; j < C::NLD; ++j)
+                        tmem_ld16_async(tmem + ((uint32_t)(quarter * 32) << 16) +
+                                            (uint32_t)(b * BN + col_base + (g0 + j) * 16),
+                                        r[j]);
+                    tmem_wait();
+#pragma unroll
+                    for (int j = 0; j < C::NLD; ++j) {
+                        tmem_after_wait(r[j]);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) sum[(g0 + j) * 16 + q] += __uint_as_float(r[j][q]);
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -642,10 +728,9 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
             }
             if (!ok) break;
             const int rloc = quarter * 32 + lane;
-            const int row = tr.mi * BM + rloc;
             const int col0 = tr.ni * BN + col_base;
             const EpiParams &e = pb.epi;
-            if (e.mode == EPI_PACK) {
+            if constexpr (EK == EK_PACK) {
                 // row rloc of M tile mi; column j of the result is k = j of the packed operand
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
@@ -655,13 +740,19 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                     for (int cc = 0; cc < 4; ++cc)
                         store_chunk<P>(tile0, rloc, (g & 1) * 4 + cc, &sum[g * 32 + cc * 8]);
                 }
-            } else if (BN == 128 && e.mode == EPI_SYM) {  // symmetric problems always use square tiles
-                const bool diag = tr.mi == tr.ni;
-#pragma unroll
-                for (int g = 0; g < 4; ++g) epi_sym32(e, row, col0 + g * 32, &sum[g * 32], diag);
             } else {
+                float *sc = scratch + (warp - 2) * 1024;
+                const int wrow0 = tr.mi * BM + quarter * 32;
+                const bool diag = EK == EK_SYM && tr.mi == tr.ni;
 #pragma unroll
-                for (int g = 0; g < 4; ++g) epi_chunk(e, row, col0 + g * 32, &sum[g * 32]);
+                for (int g = 0; g < 4; ++g) {
+                    if constexpr (EK == EK_SYM) {
+                        epi_sym32(e, wrow0 + lane, col0 + g * 32, &sum[g * 32], diag);
+                    } else {
+                        if (!block_epilogue<EK>(e, sc, wrow0, col0 + g * 32, &sum[g * 32], lane))
+                            epi_chunk(e, wrow0 + lane, col0 + g * 32, &sum[g * 32]);
+                    }
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->sempty[s]);
@@ -677,11 +768,11 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
     }
 }
 
-template <int P, int BN, int BATCHED>
+template <int P, int BN, int BATCHED, int EK>
 ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int *prefix, const int *owner, int total,
                  int *queue, cudaStream_t st) {
     using C = Cfg<P, BN>;
-    auto kern = k_umma<P, BN, BATCHED>;
+    auto kern = k_umma<P, BN, BATCHED, EK>;
     // the shared-memory opt-in is set once per device (so nothing but launches
     // happens while a caller captures a graph)
     static bool attr_set[64] = {false};
@@ -700,49 +791,6 @@ ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int 
     return check_launch("tcgen05 contraction");
 }
 
-template <int BATCHED>
-ln_status dispatch(int terms, int bn, const UmmaProblem *single, const UmmaProblem *probs, const int *prefix,
-                   const int *owner, int total, int *queue, cudaStream_t st) {
-    if (bn == 256) {
-        switch (terms) {
-            case 1: return launch<1, 256, BATCHED>(single, probs, prefix, owner, total, queue, st);
-            case 2: return launch<2, 256, BATCHED>(single, probs, prefix, owner, total, queue, st);
-            default: break;
-        }
-        return fail(LN_ERR_INVALID_VALUE, "no 256-wide tile for %d split terms", terms);
-    }
-    switch (terms) {
-        case 1: return launch<1, 128, BATCHED>(single, probs, prefix, owner, total, queue, st);
-        case 2: return launch<2, 128, BATCHED>(single, probs, prefix, owner, total, queue, st);
-        case 3: return launch<3, 128, BATCHED>(single, probs, prefix, owner, total, queue, st);
-        default: return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
-    }
-}
-
 }  // namespace
-
-int umma_tile_n(int terms, int sym) { return (!sym && terms <= 2) ? 256 : 128; }
-
-ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st) {
-    long long tiles = p.sym ? (long long)p.mt * (p.mt + 1) / 2 : (long long)p.mt * p.nt;
-    if (tiles == 0) return LN_SUCCESS;
-    if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many output tiles");
-    return dispatch<0>(terms, umma_tile_n(terms, p.sym), &p, nullptr, nullptr, nullptr, (int)tiles, nullptr, st);
-}
-
-ln_status umma_contract_batched(const UmmaProblem *d_probs, const int *d_tile_prefix, const int *d_tile_owner,
-                                int total_tiles, int *d_queue, int terms, cudaStream_t st) {
-    if (total_tiles == 0) return LN_SUCCESS;
-    LN_CUDA_TRY(cudaMemsetAsync(d_queue, 0, sizeof(int), st));
-    return dispatch<1>(terms, 128, nullptr, d_probs, d_tile_prefix, d_tile_owner, total_tiles, d_queue, st);
-}
-
-ln_status umma_read_error(int *value) {
-    int v = 0, zero = 0;
-    LN_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_umma_error, sizeof(int)));
-    if (v) LN_CUDA_TRY(cudaMemcpyToSymbol(g_umma_error, &zero, sizeof(int)));
-    *value = v;
-    return LN_SUCCESS;
-}
 
 }  // namespace ln

@@ -1,0 +1,41 @@
+// Instantiations of the tcgen05 contraction kernel (ln_umma_kernel.cuh) for
+// symmetric problems (covariance, correlation, SYRK/SYR2K): lower-triangle
+// square tiles with mirrored stores, single and batched (device tile queue).
+#include "ln_umma_kernel.cuh"
+
+namespace ln {
+
+ln_status umma_contract_sym(const UmmaProblem &p, int terms, cudaStream_t st) {
+    const long long tiles = (long long)p.mt * (p.mt + 1) / 2;
+    if (tiles == 0) return LN_SUCCESS;
+    if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many output tiles");
+    const int total = (int)tiles;
+    switch (terms) {
+        case 1: return launch<1, 128, 0, EK_SYM>(&p, nullptr, nullptr, nullptr, total, nullptr, st);
+        case 2: return launch<2, 128, 0, EK_SYM>(&p, nullptr, nullptr, nullptr, total, nullptr, st);
+        case 3: return launch<3, 128, 0, EK_SYM>(&p, nullptr, nullptr, nullptr, total, nullptr, st);
+        default: return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
+    }
+}
+
+ln_status umma_contract_batched(const UmmaProblem *d_probs, const int *d_tile_prefix, const int *d_tile_owner,
+                                int total_tiles, int *d_queue, int terms, cudaStream_t st) {
+    if (total_tiles == 0) return LN_SUCCESS;
+    LN_CUDA_TRY(cudaMemsetAsync(d_queue, 0, sizeof(int), st));
+    switch (terms) {
+        case 1: return launch<1, 128, 1, EK_SYM>(nullptr, d_probs, d_tile_prefix, d_tile_owner, total_tiles, d_queue, st);
+        case 2: return launch<2, 128, 1, EK_SYM>(nullptr, d_probs, d_tile_prefix, d_tile_owner, total_tiles, d_queue, st);
+        case 3: return launch<3, 128, 1, EK_SYM>(nullptr, d_probs, d_tile_prefix, d_tile_owner, total_tiles, d_queue, st);
+        default: return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
+    }
+}
+
+ln_status umma_read_error_sym(int *value) {
+    int v = 0, zero = 0;
+    LN_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_umma_error, sizeof(int)));
+    if (v) LN_CUDA_TRY(cudaMemcpyToSymbol(g_umma_error, &zero, sizeof(int)));
+    *value = v;
+    return LN_SUCCESS;
+}
+
+}  // namespace ln
