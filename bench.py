@@ -76,6 +76,27 @@ def parse():
     return ap.parse_args()
 
 
+UMMA_SOURCES = ["ln_umma_kernel.cuh", "ln_umma_general.cu", "ln_umma_sym.cu", "ln_split.cuh", "ln_epilogue.cuh",
+                "ln_internal.h"]
+
+
+def umma_traffic():
+    """DRAM bytes per launch of the tcgen05 contraction from the committed ncu
+    summary, or None when the kernel's sources changed since that capture."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_umma_traffic.json")) as f:
+            d = json.load(f)
+        h = hashlib.sha256()
+        for name in d["sources"]:
+            with open(os.path.join(ROOT, "paper_2312_13170_gb300", "csrc", name), "rb") as g:
+                h.update(g.read())
+        return float(d["dram_bytes_per_launch_mean"]) if h.hexdigest() == d["sources_sha256"] else None
+    except Exception:
+        return None
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -313,7 +334,8 @@ def run_own(args):
                        "form": "internalized", "precision": "fp32"},
         "speedup_vs_plain": ms_plain / ms,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": umma_traffic(),
+                     "traffic_unit": "DRAM bytes per launch (ncu, profiles/k_umma_traffic.json)",
                      "kernel": "k_umma<2,0> (tcgen05 3xBF16 contraction)",
                      "peak_note": f"{peak_src} bf16 burst {bf16_peak} TFLOP/s / {PRODUCTS} products",
                      "launches": umma_n, "ms_per_launch": (umma_ms / umma_n) if umma_n else None,
