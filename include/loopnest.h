@@ -122,6 +122,22 @@ ln_status ln_timing_enable(int on);
 ln_status ln_timing_read(const char *family, double *total_ms /*host*/, int *launches /*host*/);
 
 /*
+ * Tuning knobs of the tensor-core engine, process-wide (the autotuner in the
+ * Python package picks them per problem class). Keys:
+ *   "chunk_kt" 1 or 2 (default 2): k tiles of 64 accumulated in tensor memory
+ *              before the partial sum is added to an FP32 running sum; 1 is
+ *              more accurate, 2 faster;
+ *   "tile_n"   128 or 256 (default 256): output tile width of general
+ *              (non-symmetric) contractions with one or two split terms.
+ * A knob changes the workspace size of later calls: set it before the
+ * *_workspace_size query of a call, not between the query and the call.
+ * Unknown keys or values give LN_ERR_INVALID_VALUE. Not for use while kernels
+ * of this library are being enqueued from other host threads.
+ */
+ln_status ln_set_tuning(const char *key, int value);
+ln_status ln_get_tuning(const char *key, int *value /*host*/);
+
+/*
  * GEMM, polybench form (paper Sec. VI-C, Listings 5-6; Sec. VIII "GEMM"):
  *   C[i][j] = alpha * sum_k A[i][k] * B[k][j] + beta * C[i][j]
  * A is M x K (lda), B is K x N (ldb), C is M x N (ldc), in place.

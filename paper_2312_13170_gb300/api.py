@@ -57,6 +57,8 @@ _SIGS = {
     "ln_launch_count": (ctypes.c_longlong, []),
     "ln_timing_enable": (_I, [_I]),
     "ln_timing_read": (_I, [ctypes.c_char_p, _P, _P]),
+    "ln_set_tuning": (_I, [ctypes.c_char_p, _I]),
+    "ln_get_tuning": (_I, [ctypes.c_char_p, _P]),
     "ln_gemm_workspace_size": (_I, [_I, _I, _I, _I, _I, _P]),
     "ln_gemm": (_I, [_I, _I, _I, _F, _P, _I, _P, _I, _F, _P, _I, _P, _SZ, _I, _I, _P]),
     "ln_gemm_chain_workspace_size": (_I, [_I, _I, _I, _I, _I, _I, _P]),
@@ -141,6 +143,14 @@ def _ws_query(fn, *args):
     return int(n.value)
 
 
+def _autotune(op, shape, prec):
+    if os.environ.get("LN_AUTOTUNE", "off").lower() in ("cached", "search"):
+        from . import autotune
+
+        autotune.apply(op, shape, prec if isinstance(prec, str) else
+                       {v: k for k, v in PRECS.items()}.get(prec, "fp32"))
+
+
 def _workspace(nbytes, device):
     if nbytes == 0:
         return None, 0
@@ -165,6 +175,17 @@ def timing_read(family: str):
     return float(ms.value), int(n.value)
 
 
+def set_tuning(key: str, value: int) -> None:
+    """Set a tensor-core engine knob ("chunk_kt", "tile_n"); see loopnest.h."""
+    _check(lib().ln_set_tuning(key.encode(), int(value)), "ln_set_tuning")
+
+
+def get_tuning(key: str) -> int:
+    v = ctypes.c_int(0)
+    _check(lib().ln_get_tuning(key.encode(), ctypes.byref(v)), "ln_get_tuning")
+    return int(v.value)
+
+
 def stream_check(stream=None):
     """Synchronise the stream and raise if a kernel gave up a bounded wait."""
     _check(lib().ln_stream_check(_stream(stream)), "ln_stream_check")
@@ -179,6 +200,7 @@ def gemm(A, B, C, alpha=1.0, beta=0.0, form="internalized", prec="3xbf16", strea
     if K2 != K or tuple(C.shape) != (M, N):
         raise ValueError("shape mismatch")
     fm, pr = _enum(FORMS, form, "form"), _enum(PRECS, prec, "precision")
+    _autotune("gemm", (M, N, K), prec)
     ws, nb = _workspace(_ws_query("ln_gemm_workspace_size", M, N, K, fm, pr), A.device)
     _check(lib().ln_gemm(M, N, K, alpha, _ptr(A), _ld(A), _ptr(B), _ld(B), beta, _ptr(C), _ld(C), _ptr(ws), nb,
                          fm, pr, _stream(stream)), "ln_gemm")
@@ -205,6 +227,7 @@ def gemm_chain(A, B, C, D=None, alpha=1.0, beta=0.0, form="internalized", prec="
         F = torch.empty((ni, nl), dtype=torch.float32, device=A.device)
     else:
         E, F = out
+    _autotune("gemm_chain", (ni, nj, nk, nl), prec)
     ws, nb = _workspace(_ws_query("ln_gemm_chain_workspace_size", ni, nj, nk, nl, fm, pr), A.device)
     _check(lib().ln_gemm_chain(ni, nj, nk, nl, alpha, _ptr(A), _ptr(B), _ptr(C), beta, _ptr(D), _ptr(E), _ptr(F),
                                _ptr(ws), nb, fm, pr, _stream(stream)), "ln_gemm_chain")
@@ -229,6 +252,7 @@ def _covlike(fn, X, form, prec, stream, out):
     n, m = X.shape
     fm, pr = _enum(FORMS, form, "form"), _enum(PRECS, prec, "precision")
     out = torch.empty((m, m), dtype=torch.float32, device=X.device) if out is None else out
+    _autotune("covariance" if fn == "ln_covariance" else "correlation", (n, m), prec)
     ws, nb = _workspace(_ws_query("ln_covariance_workspace_size", n, m, fm, pr), X.device)
     _check(getattr(lib(), fn)(n, m, _ptr(X), _ld(X), _ptr(out), _ld(out), _ptr(ws), nb, fm, pr, _stream(stream)), fn)
     return out
@@ -247,6 +271,7 @@ def syrk(A, C, alpha=1.0, beta=0.0, fill="full", form="internalized", prec="3xbf
     _f32(A, "A"), _f32(C, "C")
     n, k = A.shape
     fm, pr, fl = _enum(FORMS, form, "form"), _enum(PRECS, prec, "precision"), _enum(FILLS, fill, "fill")
+    _autotune("syrk", (n, k), prec)
     ws, nb = _workspace(_ws_query("ln_syrk_workspace_size", n, k, fm, pr), A.device)
     _check(lib().ln_syrk(fl, n, k, alpha, _ptr(A), _ld(A), beta, _ptr(C), _ld(C), _ptr(ws), nb, fm, pr,
                          _stream(stream)), "ln_syrk")
@@ -258,6 +283,7 @@ def syr2k(A, B, C, alpha=1.0, beta=0.0, fill="full", form="internalized", prec="
     _f32(A, "A"), _f32(B, "B"), _f32(C, "C")
     n, k = A.shape
     fm, pr, fl = _enum(FORMS, form, "form"), _enum(PRECS, prec, "precision"), _enum(FILLS, fill, "fill")
+    _autotune("syr2k", (n, k), prec)
     ws, nb = _workspace(_ws_query("ln_syr2k_workspace_size", n, k, fm, pr), A.device)
     _check(lib().ln_syr2k(fl, n, k, alpha, _ptr(A), _ld(A), _ptr(B), _ld(B), beta, _ptr(C), _ld(C), _ptr(ws), nb, fm,
                           pr, _stream(stream)), "ln_syr2k")

@@ -63,6 +63,15 @@ LaunchScope::~LaunchScope() {
     if (slot >= 0) cudaEventRecord(g_timing.pending[f][slot].second, st);
 }
 
+// ------------------------------------------------------------------ tuning knobs
+namespace {
+std::atomic<int> g_chunk_kt{2};
+std::atomic<int> g_tile_n{256};
+}  // namespace
+
+int tune_chunk_kt() { return g_chunk_kt.load(std::memory_order_relaxed); }
+int tune_tile_n() { return g_tile_n.load(std::memory_order_relaxed); }
+
 bool inject_timeout_requested() {
     const char *v = getenv("LN_FAULT_INJECT");
     return v && strcmp(v, "timeout") == 0;
@@ -219,7 +228,7 @@ ln_status run_contract(int M, int N, int K, Operand a, Operand b, const EpiParam
     pb.mt = cp.mt;
     pb.nt = cp.nt;
     pb.sym = 0;
-    pb.chunk_kt = UMMA_CHUNK_KT;
+    pb.chunk_kt = tune_chunk_kt();
     pb.inject_timeout = inject_timeout_requested();
     pb.epi = epi;
     return umma_contract(pb, P, st);
@@ -346,7 +355,7 @@ ln_status run_cov(bool corr, int n, int m, const float *X, int ldx, float *out, 
     pb.x_kt = pb.y_kt = p.kt;
     pb.mt = pb.nt = p.mt;
     pb.sym = 1;
-    pb.chunk_kt = UMMA_CHUNK_KT;
+    pb.chunk_kt = tune_chunk_kt();
     pb.epi = e;
     return umma_contract(pb, P, st);
 }
@@ -429,7 +438,7 @@ ln_status run_sym(bool two, ln_fill fill, int n, int k, float alpha, const float
     pb.x_kt = pb.y_kt = p.kt;
     pb.mt = pb.nt = p.mt;
     pb.sym = 1;
-    pb.chunk_kt = UMMA_CHUNK_KT;
+    pb.chunk_kt = tune_chunk_kt();
     pb.epi = e;
     return umma_contract(pb, P, st);
 }
@@ -683,6 +692,31 @@ int ln_version(void) { return 100; }
 
 long long ln_launch_count(void) { return g_launches.load(); }
 
+ln_status ln_set_tuning(const char *key, int value) {
+    clear_error();
+    if (!key) return fail(LN_ERR_INVALID_VALUE, "NULL key");
+    if (strcmp(key, "chunk_kt") == 0) {
+        if (value != 1 && value != 2) return fail(LN_ERR_INVALID_VALUE, "chunk_kt must be 1 or 2 (got %d)", value);
+        g_chunk_kt.store(value);
+        return LN_SUCCESS;
+    }
+    if (strcmp(key, "tile_n") == 0) {
+        if (value != 128 && value != 256) return fail(LN_ERR_INVALID_VALUE, "tile_n must be 128 or 256 (got %d)", value);
+        g_tile_n.store(value);
+        return LN_SUCCESS;
+    }
+    return fail(LN_ERR_INVALID_VALUE, "unknown tuning key '%s'", key);
+}
+
+ln_status ln_get_tuning(const char *key, int *value) {
+    clear_error();
+    if (!key || !value) return fail(LN_ERR_INVALID_VALUE, "NULL argument");
+    if (strcmp(key, "chunk_kt") == 0) *value = g_chunk_kt.load();
+    else if (strcmp(key, "tile_n") == 0) *value = g_tile_n.load();
+    else return fail(LN_ERR_INVALID_VALUE, "unknown tuning key '%s'", key);
+    return LN_SUCCESS;
+}
+
 ln_status ln_timing_enable(int on) {
     clear_error();
     g_timing.on = on != 0;
@@ -822,7 +856,7 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
     g1.x_kt = g1.y_kt = p.g1.kt;
     g1.mt = p.g1.mt;
     g1.nt = p.g1.nt;
-    g1.chunk_kt = UMMA_CHUNK_KT;
+    g1.chunk_kt = tune_chunk_kt();
     g1.inject_timeout = inject_timeout_requested();
     g1.epi.mode = EPI_PACK;
     g1.epi.M = ni;
@@ -838,7 +872,7 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
     g2.y_kt = p.g2.kt;
     g2.mt = p.g2.mt;
     g2.nt = p.g2.nt;
-    g2.chunk_kt = UMMA_CHUNK_KT;
+    g2.chunk_kt = tune_chunk_kt();
     g2.inject_timeout = g1.inject_timeout;
     g2.epi = ef;
     return umma_contract(g2, P, st);

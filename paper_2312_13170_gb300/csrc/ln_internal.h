@@ -158,8 +158,12 @@ size_t corr_bwd_partials_bytes(int n, int m);
 ln_status pack_operand(const PackSrc &p, int terms, cudaStream_t st);
 // Packs up to four operands in one launch.
 ln_status pack_operands(const PackSrc *ps, int count, int terms, cudaStream_t st);
-// k tiles per TMEM accumulation chunk of the tcgen05 engine
-constexpr int UMMA_CHUNK_KT = 2;
+// Process-wide tuning knobs (ln_set_tuning): k tiles per TMEM accumulation
+// chunk of the tcgen05 engine (1 or 2; default 2) and the output tile width of
+// general tcgen05 contractions (128 or 256; default 256, three-term splits
+// always 128).
+int tune_chunk_kt();
+int tune_tile_n();
 
 // ln_umma.cu: tcgen05 contraction over packed operands
 struct UmmaSeg {

@@ -158,7 +158,8 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_batch_plan(int is_syr2k, int c
                                                              const ln_sym_desc *__restrict__ descs, int *order,
                                                              int fill, float alpha, float beta, UmmaProblem *probs,
                                                              int *tile_prefix, int *tile_owner, long long *pack_off,
-                                                             int *pack_prefix, char *pack_base, int terms) {
+                                                             int *pack_prefix, char *pack_base, int terms,
+                                                             int chunk_kt_for_kernel) {
     __shared__ float w[RANK_MAX];
     __shared__ long long sb[PLAN_THREADS];
     __shared__ int st[PLAN_THREADS], sp[PLAN_THREADS];
@@ -220,7 +221,7 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_batch_plan(int is_syr2k, int c
         p.x_kt = p.y_kt = kt;
         p.mt = p.nt = mt;
         p.sym = 1;
-        p.chunk_kt = UMMA_CHUNK_KT;
+        p.chunk_kt = chunk_kt_for_kernel;
         const char *pa = pack_base + off_b;
         const char *pb = is_syr2k ? pa + one : pa;
         pack_off[2 * r] = off_b;
@@ -343,7 +344,8 @@ ln_status sym_batched_plan(int is_syr2k, int count, const ln_sym_desc *d_descs, 
                            int *d_pack_prefix, int *d_order, char *pack_base, int terms, cudaStream_t st) {
     LaunchScope ls_(FAM_PACK, st);
     k_batch_plan<<<1, PLAN_THREADS, 0, st>>>(is_syr2k, count, d_descs, d_order, fill, alpha, beta, d_probs,
-                                             d_tile_prefix, d_tile_owner, d_pack_off, d_pack_prefix, pack_base, terms);
+                                             d_tile_prefix, d_tile_owner, d_pack_off, d_pack_prefix, pack_base, terms,
+                                             tune_chunk_kt());
     return check_launch("batched plan");
 }
 

@@ -27,7 +27,7 @@ int epi_kind(const EpiParams &e) {
 
 }  // namespace
 
-int umma_tile_n(int terms, int sym) { return (!sym && terms <= 2) ? 256 : 128; }
+int umma_tile_n(int terms, int sym) { return (!sym && terms <= 2) ? tune_tile_n() : 128; }
 
 ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st) {
     long long tiles = p.sym ? (long long)p.mt * (p.mt + 1) / 2 : (long long)p.mt * p.nt;
@@ -40,9 +40,10 @@ ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st) {
     }
     if (p.sym) return fail(LN_ERR_INVALID_VALUE, "symmetric problem needs the symmetric epilogue");
     const int total = (int)tiles;
+    const bool wide = umma_tile_n(terms, 0) == 256;
     switch (terms) {
-        case 1: return launch_single<1, 256>(ek, p, total, st);
-        case 2: return launch_single<2, 256>(ek, p, total, st);
+        case 1: return wide ? launch_single<1, 256>(ek, p, total, st) : launch_single<1, 128>(ek, p, total, st);
+        case 2: return wide ? launch_single<2, 256>(ek, p, total, st) : launch_single<2, 128>(ek, p, total, st);
         case 3: return launch_single<3, 128>(ek, p, total, st);
         default: return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
     }
