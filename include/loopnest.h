@@ -114,8 +114,10 @@ ln_status ln_stream_check(void *stream);
  * milliseconds and the number of launches of one family since the last read
  * (families: "umma" = tcgen05 contraction, "pack" = split-and-pack,
  * "simt" = FP32 tiled contraction, "plain" = one-thread-per-output kernels,
- * "stats" = column statistics and element-wise helpers). Enabling and reading
- * must not happen during CUDA graph capture. Not thread-safe.
+ * "stats" = column statistics and element-wise helpers). Launches captured
+ * into a CUDA graph get external event-record nodes, so their times are those
+ * of the latest replay of the graph (read after replaying each captured graph
+ * once). Enabling and reading must not happen during capture. Not thread-safe.
  */
 long long ln_launch_count(void);
 ln_status ln_timing_enable(int on);

@@ -44,6 +44,16 @@ std::atomic<long long> g_launches{0};
 const char *const kFamilies[FAM_COUNT] = {"umma", "pack", "simt", "plain", "stats"};
 }  // namespace
 
+// Inside stream capture a plain event record is only a dependency marker; an
+// external record becomes a graph node that timestamps every replay.
+void record_event(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, st);
+}
+
 LaunchScope::LaunchScope(Family fam, cudaStream_t s) : slot(-1), st(s), f(fam) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!g_timing.on) return;
@@ -54,13 +64,13 @@ LaunchScope::LaunchScope(Family fam, cudaStream_t s) : slot(-1), st(s), f(fam) {
     } else if (cudaEventCreate(&ev.first) != cudaSuccess || cudaEventCreate(&ev.second) != cudaSuccess) {
         return;
     }
-    cudaEventRecord(ev.first, st);
+    record_event(ev.first, st);
     g_timing.pending[f].push_back(ev);
     slot = (int)g_timing.pending[f].size() - 1;
 }
 
 LaunchScope::~LaunchScope() {
-    if (slot >= 0) cudaEventRecord(g_timing.pending[f][slot].second, st);
+    if (slot >= 0) record_event(g_timing.pending[f][slot].second, st);
 }
 
 // ------------------------------------------------------------------ tuning knobs
@@ -848,7 +858,11 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
     PackSrc ps[3] = {{A, nk, 0, ni, nk, nullptr, nullptr, p.pa, p.g1.mt, p.g1.kt},
                      {B, nj, 1, nj, nk, nullptr, nullptr, p.pb, p.g1.yrt, p.g1.kt},
                      {C, nl, 1, nl, nj, nullptr, nullptr, p.pc, p.g2.yrt, p.g2.kt}};
-    LN_TRY(pack_operands(ps, 3, P, st));
+    // C is packed by the first contraction's spare CTAs when it has fewer
+    // output tiles than SMs, else here with A and B
+    PackMulti side;
+    const bool try_side = umma_tile_n(P, 0) == 256 && make_pack_multi(ps + 2, 1, side) && pack_stream_eligible(side);
+    LN_TRY(pack_operands(ps, try_side ? 2 : 3, P, st));
     UmmaProblem g1{};
     g1.seg[0] = {p.pa, p.pb};
     g1.nseg = 1;
@@ -863,7 +877,9 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
     g1.epi.N = nj;
     g1.epi.pack = p.pt;
     g1.epi.pack_kt = p.ktT;
-    LN_TRY(umma_contract(g1, P, st));
+    bool side_done = false;
+    LN_TRY(umma_contract(g1, P, st, try_side ? &side : nullptr, &side_done));
+    if (try_side && !side_done) LN_TRY(pack_operands(ps + 2, 1, P, st));
     UmmaProblem g2{};
     g2.seg[0] = {p.pt, p.pc};
     g2.nseg = 1;

@@ -112,6 +112,14 @@ struct PackSrc {
     int rt, kt;      // tile counts of the destination (>= ceil(rows/128), ceil(K/64))
 };
 
+// Up to four operands packed by one launch: a flat tile index space, operand i
+// owning tiles [prefix[i], prefix[i+1]).
+struct PackMulti {
+    PackSrc op[4];
+    int prefix[5];
+    int count;
+};
+
 // ------------------------------------------------------------------ launchers (one per .cu)
 // ln_plain.cu
 ln_status plain_gemm(int M, int N, int K, const float *A, long long sai, long long sak, const float *B,
@@ -158,6 +166,12 @@ size_t corr_bwd_partials_bytes(int n, int m);
 ln_status pack_operand(const PackSrc &p, int terms, cudaStream_t st);
 // Packs up to four operands in one launch.
 ln_status pack_operands(const PackSrc *ps, int count, int terms, cudaStream_t st);
+// Fills m for pack_operands' operands; false if count is out of range or the
+// tile count overflows.
+bool make_pack_multi(const PackSrc *ps, int count, PackMulti &m);
+// True if the bulk-copy pack stream can read every operand of m (16-byte
+// aligned rows of a whole number of 16-byte units).
+bool pack_stream_eligible(const PackMulti &m);
 // Process-wide tuning knobs (ln_set_tuning): k tiles per TMEM accumulation
 // chunk of the tcgen05 engine (1 or 2; default 2) and the output tile width of
 // general tcgen05 contractions (128 or 256; default 256, three-term splits
@@ -189,7 +203,11 @@ bool inject_timeout_requested();
 // `nt` of a problem counts tiles of this width, and the packed N-side operand
 // must hold 128 * (width / 128) * nt rows (zero padded).
 int umma_tile_n(int terms, int sym);
-ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st);
+// With `side`, a contraction with the packing epilogue may also pack that
+// operand on SMs without an output tile; *side_done says whether it did (if
+// not, the caller packs it).
+ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st, const PackMulti *side = nullptr,
+                        bool *side_done = nullptr);
 ln_status umma_contract_sym(const UmmaProblem &p, int terms, cudaStream_t st);  // ln_umma_sym.cu
 ln_status umma_read_error_sym(int *value);
 // d_tile_owner[t] = the problem (in d_probs order) that tile t belongs to.

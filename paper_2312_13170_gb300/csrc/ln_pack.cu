@@ -9,6 +9,7 @@
 // (hi + lo = the FP64 mean), so the centred value is correct to about one
 // FP32 rounding even when the mean is large compared to the spread.
 #include "ln_internal.h"
+#include "ln_pack_stream.cuh"
 #include "ln_split.cuh"
 
 namespace ln {
@@ -126,12 +127,6 @@ __global__ __launch_bounds__(256) void k_pack(PackSrc p) {
     pack_tile<TRANS, P>(p, blockIdx.x, blockIdx.y, s);
 }
 
-struct PackMulti {
-    PackSrc op[4];
-    int prefix[5];
-    int count;
-};
-
 // Several operands in one launch: a flat grid over all their tiles.
 template <int P>
 __global__ __launch_bounds__(256) void k_pack_multi(const __grid_constant__ PackMulti m) {
@@ -143,6 +138,16 @@ __global__ __launch_bounds__(256) void k_pack_multi(const __grid_constant__ Pack
     const int local = t - m.prefix[i];
     if (p.trans) pack_tile<1, P>(p, local % p.kt, local / p.kt, s);
     else pack_tile<0, P>(p, local % p.kt, local / p.kt, s);
+}
+
+// Persistent bulk-copy pack stream (ln_pack_stream.cuh), one CTA per SM.
+constexpr int PS_KERNEL_THREADS = 512;
+
+template <int P>
+__global__ __launch_bounds__(PS_KERNEL_THREADS, 1) void k_pack_stream(const __grid_constant__ PackMulti m, int ns,
+                                                                       int nout) {
+    extern __shared__ __align__(128) unsigned char ps_smem[];
+    pack_stream<P, PS_KERNEL_THREADS>(m, blockIdx.x, gridDim.x, ps_smem, ns, nout);
 }
 
 // Batched layout, one CTA of 1024 threads: (1) rank instances by decreasing
@@ -300,6 +305,10 @@ __global__ __launch_bounds__(256) void k_pack_batched(int is_syr2k, int count, c
 
 ln_status pack_operand(const PackSrc &p, int terms, cudaStream_t st) {
     if (p.rt <= 0 || p.kt <= 0) return LN_SUCCESS;
+    {
+        PackMulti m;
+        if (make_pack_multi(&p, 1, m) && pack_stream_eligible(m)) return pack_operands(&p, 1, terms, st);
+    }
     if (p.rt > 65535) return fail(LN_ERR_INVALID_VALUE, "operand too tall to pack (%d row tiles)", p.rt);
     dim3 grid((unsigned)p.kt, (unsigned)p.rt);
     LaunchScope ls_(FAM_PACK, st);
@@ -316,19 +325,77 @@ ln_status pack_operand(const PackSrc &p, int terms, cudaStream_t st) {
     return check_launch("split-and-pack");
 }
 
-ln_status pack_operands(const PackSrc *ps, int count, int terms, cudaStream_t st) {
-    if (count < 1 || count > 4) return fail(LN_ERR_INVALID_VALUE, "pack_operands: bad operand count %d", count);
-    PackMulti m{};
+bool make_pack_multi(const PackSrc *ps, int count, PackMulti &m) {
+    if (count < 1 || count > 4) return false;
+    m = PackMulti{};
     m.count = count;
     long long tiles = 0;
     for (int i = 0; i < count; ++i) {
         m.op[i] = ps[i];
         m.prefix[i] = (int)tiles;
         tiles += (long long)ps[i].rt * ps[i].kt;
+        if (tiles > 0x7fffffffLL) return false;
     }
     m.prefix[count] = (int)tiles;
+    return true;
+}
+
+bool pack_stream_eligible(const PackMulti &m) {
+    for (int i = 0; i < m.count; ++i) {
+        const PackSrc &p = m.op[i];
+        if (m.prefix[i + 1] == m.prefix[i]) continue;
+        if ((reinterpret_cast<uintptr_t>(p.S) & 15) || (p.ld & 3)) return false;
+        if (p.trans ? (p.rows & 3) : (p.K & 3)) return false;
+        if (reinterpret_cast<uintptr_t>(p.dst) & 15) return false;
+    }
+    return true;
+}
+
+namespace {
+
+// 4 input stages and 3 output buffers where they fit in 227 KiB (1 and 2
+// terms), else 3 and 2
+constexpr int stream_stages(int terms) { return terms >= 3 ? 3 : PS_MAX_STAGES; }
+constexpr int stream_outs(int terms) { return terms >= 3 ? 2 : 3; }
+static_assert(pack_stream_smem(stream_stages(2), stream_outs(2), 2) <= 227 * 1024, "pack stream smem");
+static_assert(pack_stream_smem(stream_stages(3), stream_outs(3), 3) <= 227 * 1024, "pack stream smem");
+
+template <int P>
+ln_status launch_pack_stream(const PackMulti &m, cudaStream_t st) {
+    const int ns = stream_stages(P), nout = stream_outs(P);
+    const int bytes = pack_stream_smem(ns, nout, P);
+    // the shared-memory opt-in is set once per device (so nothing but launches
+    // happens while a caller captures a graph)
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    LN_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        LN_CUDA_TRY(cudaFuncSetAttribute(k_pack_stream<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    const int tiles = m.prefix[m.count];
+    const int grid = std::min(tiles, sm_count());
+    LaunchScope ls_(FAM_PACK, st);
+    k_pack_stream<P><<<grid, PS_KERNEL_THREADS, bytes, st>>>(m, ns, nout);
+    return check_launch("split-and-pack stream");
+}
+
+}  // namespace
+
+ln_status pack_operands(const PackSrc *ps, int count, int terms, cudaStream_t st) {
+    if (count < 1 || count > 4) return fail(LN_ERR_INVALID_VALUE, "pack_operands: bad operand count %d", count);
+    PackMulti m;
+    if (!make_pack_multi(ps, count, m)) return fail(LN_ERR_INVALID_VALUE, "too many tiles to pack");
+    const int tiles = m.prefix[count];
     if (tiles == 0) return LN_SUCCESS;
-    if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many tiles to pack");
+    if (pack_stream_eligible(m)) {
+        switch (terms) {
+            case 1: return launch_pack_stream<1>(m, st);
+            case 2: return launch_pack_stream<2>(m, st);
+            case 3: return launch_pack_stream<3>(m, st);
+            default: return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
+        }
+    }
     LaunchScope ls_(FAM_PACK, st);
     switch (terms) {
         case 1: k_pack_multi<1><<<(unsigned)tiles, 256, 0, st>>>(m); break;

@@ -13,6 +13,9 @@
 
 namespace ln {
 
+// One cvt.rn.bf16x2.f32 rounds a pair (first value in the low half); a BF16
+// value widened to FP32 is its 16 bits shifted to the top, so hi is recovered
+// exactly with one shift or mask.
 template <int P>
 __device__ __forceinline__ void split8(const float *v, uint4 (&out)[P]) {
     uint32_t w[P][4];
@@ -21,10 +24,13 @@ __device__ __forceinline__ void split8(const float *v, uint4 (&out)[P]) {
         float x0 = v[q], x1 = v[q + 1];
 #pragma unroll
         for (int t = 0; t < P; ++t) {
-            __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-            w[t][q / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-            x0 = x0 - __bfloat162float(h0);
-            x1 = x1 - __bfloat162float(h1);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+            const uint32_t u = *reinterpret_cast<const uint32_t *>(&h);
+            w[t][q / 2] = u;
+            if (t + 1 < P) {
+                x0 -= __uint_as_float(u << 16);
+                x1 -= __uint_as_float(u & 0xffff0000u);
+            }
         }
     }
 #pragma unroll

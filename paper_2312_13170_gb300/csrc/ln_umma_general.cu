@@ -8,9 +8,11 @@ namespace ln {
 namespace {
 
 template <int P, int BN>
-ln_status launch_single(int ek, const UmmaProblem &p, int total, cudaStream_t st) {
+ln_status launch_single(int ek, const UmmaProblem &p, int total, cudaStream_t st, const PackMulti *side,
+                        bool *side_done) {
     switch (ek) {
-        case EK_PACK: return launch<P, BN, 0, EK_PACK>(&p, nullptr, nullptr, nullptr, total, nullptr, st);
+        case EK_PACK:
+            return launch<P, BN, 0, EK_PACK>(&p, nullptr, nullptr, nullptr, total, nullptr, st, side, side_done);
         case EK_EF: return launch<P, BN, 0, EK_EF>(&p, nullptr, nullptr, nullptr, total, nullptr, st);
         default: return launch<P, BN, 0, EK_GEMM>(&p, nullptr, nullptr, nullptr, total, nullptr, st);
     }
@@ -29,7 +31,8 @@ int epi_kind(const EpiParams &e) {
 
 int umma_tile_n(int terms, int sym) { return (!sym && terms <= 2) ? tune_tile_n() : 128; }
 
-ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st) {
+ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st, const PackMulti *side, bool *side_done) {
+    if (side_done) *side_done = false;
     long long tiles = p.sym ? (long long)p.mt * (p.mt + 1) / 2 : (long long)p.mt * p.nt;
     if (tiles == 0) return LN_SUCCESS;
     if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many output tiles");
@@ -42,9 +45,13 @@ ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st) {
     const int total = (int)tiles;
     const bool wide = umma_tile_n(terms, 0) == 256;
     switch (terms) {
-        case 1: return wide ? launch_single<1, 256>(ek, p, total, st) : launch_single<1, 128>(ek, p, total, st);
-        case 2: return wide ? launch_single<2, 256>(ek, p, total, st) : launch_single<2, 128>(ek, p, total, st);
-        case 3: return launch_single<3, 128>(ek, p, total, st);
+        case 1:
+            return wide ? launch_single<1, 256>(ek, p, total, st, side, side_done)
+                        : launch_single<1, 128>(ek, p, total, st, side, side_done);
+        case 2:
+            return wide ? launch_single<2, 256>(ek, p, total, st, side, side_done)
+                        : launch_single<2, 128>(ek, p, total, st, side, side_done);
+        case 3: return launch_single<3, 128>(ek, p, total, st, side, side_done);
         default: return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
     }
 }

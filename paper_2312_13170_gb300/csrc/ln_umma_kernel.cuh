@@ -30,8 +30,10 @@
 // TMEM is freed and the kernel returns. ln_stream_check() reports it.
 #pragma once
 
+#include "ln_async.cuh"
 #include "ln_epilogue.cuh"
 #include "ln_internal.h"
+#include "ln_pack_stream.cuh"
 #include "ln_split.cuh"
 
 namespace ln {
@@ -77,33 +79,7 @@ struct Ctl {
 static_assert(sizeof(Ctl) <= CTL_BYTES, "control block too large");
 
 // ---------------------------------------------------------------- PTX wrappers
-__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(saddr(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
+// (mbarrier, bulk-copy and timer wrappers are in ln_async.cuh)
 
 // Bounded wait for the phase of `b` with the given parity. With honor_abort,
 // returns false as soon as another role has aborted. A waiter that may wait
@@ -126,13 +102,6 @@ __device__ bool wait_phase(Ctl *ctl, uint64_t *b, uint32_t parity, int who, bool
             }
         }
     }
-}
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(saddr(bar))
-        : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -269,6 +238,12 @@ struct Cfg {
     static constexpr int SMEM = 1024 + CTL_BYTES + STAGES * STAGE_BYTES + SCRATCH_BYTES;
     static constexpr int NLD = BN == 128 ? 4 : 2;  // tcgen05.ld (x16) in flight per wait
     static_assert(NACC <= MAX_NACC && STAGES >= 2, "tile configuration does not fit");
+    // input stages of the pack stream that spare CTAs run in this shared memory
+    static constexpr int SIDE_NOUT = SMEM - 1024 - 3 * P * PK_TILE_BYTES >= 4 * PS_IN_BYTES ? 3 : 2;
+    static constexpr int SIDE_NS_RAW = (SMEM - 1024 - SIDE_NOUT * P * PK_TILE_BYTES) / PS_IN_BYTES;
+    static constexpr int SIDE_NS = SIDE_NS_RAW > PS_MAX_STAGES ? PS_MAX_STAGES : SIDE_NS_RAW;
+    // spare CTAs can pack the next contraction's operand: wide packing-epilogue kernels
+    static constexpr bool SIDE_OK = BN == 256 && NTHREADS >= 256 && SIDE_NS >= 2;
 };
 
 // ---------------------------------------------------------------- epilogue of one 32 x 32 chunk
@@ -482,18 +457,31 @@ __device__ __forceinline__ bool block_epilogue(const EpiParams &e, float *sc, in
 }
 
 // ---------------------------------------------------------------- the kernel
+// Grid: tile_ctas CTAs take output tiles (static stride tile_ctas, or the
+// queue); CTAs from tile_ctas on (only launched for single problems with the
+// packing epilogue, see Cfg::SIDE_OK) run the pack stream over `side`, the
+// operand of the next contraction, on SMs that have no output tile.
 template <int P, int BN, int BATCHED, int EK>
 __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_constant__ UmmaProblem single,
                                                                   const UmmaProblem *__restrict__ probs,
                                                                   const int *__restrict__ prefix,
                                                                   const int *__restrict__ owner, int total_tiles,
-                                                                  int *queue) {
+                                                                  int *queue, const __grid_constant__ PackMulti side,
+                                                                  int tile_ctas) {
     using C = Cfg<P, BN>;
     using PR = Products<P>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment of the stage area is required by the 128-byte swizzle.
     const uint32_t raw = saddr(smem_raw);
     const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
+    if constexpr (EK == EK_PACK && !BATCHED && C::SIDE_OK) {
+        if ((int)blockIdx.x >= tile_ctas) {
+            if (threadIdx.x < 256)
+                pack_stream<P, 256>(side, (int)blockIdx.x - tile_ctas, (int)gridDim.x - tile_ctas, smem_raw + pad,
+                                    C::SIDE_NS, C::SIDE_NOUT);
+            return;
+        }
+    }
     Ctl *ctl = reinterpret_cast<Ctl *>(smem_raw + pad);
     const uint32_t stage0 = raw + pad + CTL_BYTES;
     float *const scratch = reinterpret_cast<float *>(smem_raw + pad + CTL_BYTES + C::STAGES * C::STAGE_BYTES);
@@ -539,7 +527,7 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                 if (queue) t = atomicAdd(queue, 1);
                 else {
                     t = next;
-                    next += gridDim.x;
+                    next += tile_ctas;
                 }
                 if (t >= total_tiles) t = -1;
                 const int s = sidx % SCHED;
@@ -768,9 +756,12 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
     }
 }
 
+// With `side` (single problems, packing epilogue, Cfg::SIDE_OK), CTAs beyond
+// the tile CTAs pack that operand when enough SMs are free to finish it within
+// the contraction's own time; *side_done reports whether they were launched.
 template <int P, int BN, int BATCHED, int EK>
 ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int *prefix, const int *owner, int total,
-                 int *queue, cudaStream_t st) {
+                 int *queue, cudaStream_t st, const PackMulti *side = nullptr, bool *side_done = nullptr) {
     using C = Cfg<P, BN>;
     auto kern = k_umma<P, BN, BATCHED, EK>;
     // the shared-memory opt-in is set once per device (so nothing but launches
@@ -782,13 +773,32 @@ ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int 
         LN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    const int grid = total < sm_count() ? total : sm_count();
+    const int sms = sm_count();
+    const int tile_ctas = total < sms ? total : sms;
+    int side_ctas = 0;
+    PackMulti none{};
+    if (side_done) *side_done = false;
+    if constexpr (EK == EK_PACK && !BATCHED && C::SIDE_OK) {
+        if (side && single && side->prefix[side->count] > 0 && pack_stream_eligible(*side)) {
+            // time model: a 128 x BN x 64 MMA step per product at the SM's share of
+            // the BF16 peak (~0.33 us at BN = 256) against ~60 GB/s of split
+            // traffic (32 KiB in, 32 KiB out per pack tile) for each spare SM
+            const double mma_us = ceil_div(total, tile_ctas) * (double)single->kt * Products<P>::n * 0.33 * (BN / 256.0);
+            const int free_sms = sms - tile_ctas;
+            const double pack_us =
+                free_sms > 0 ? side->prefix[side->count] * 65536.0 / (free_sms * 60e3) : 1e30;
+            if (pack_us <= 0.8 * mma_us) side_ctas = free_sms;
+        }
+    }
     UmmaProblem dummy{};
     {
         LaunchScope ls_(FAM_UMMA, st);
-        kern<<<grid, C::NTHREADS, C::SMEM, st>>>(single ? *single : dummy, probs, prefix, owner, total, queue);
+        kern<<<tile_ctas + side_ctas, C::NTHREADS, C::SMEM, st>>>(single ? *single : dummy, probs, prefix, owner,
+                                                                  total, queue, side_ctas ? *side : none, tile_ctas);
     }
-    return check_launch("tcgen05 contraction");
+    const ln_status ls = check_launch("tcgen05 contraction");
+    if (side_done) *side_done = ls == LN_SUCCESS && side_ctas > 0;
+    return ls;
 }
 
 }  // namespace
