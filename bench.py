@@ -79,6 +79,7 @@ def parse():
 
 
 UMMA_SOURCES = ["ln_umma_kernel.cuh", "ln_umma_general.cu", "ln_umma_sym.cu", "ln_split.cuh", "ln_epilogue.cuh",
+                "ln_async.cuh", "ln_pack_stream.cuh",
                 "ln_internal.h"]
 
 
@@ -418,14 +419,37 @@ def run_suite(args):
     def peak_of(prec):
         return fp32_peak if prec == "fp32" else bf16_peak / {"bf16": 1, "3xbf16": 3, "6xbf16": 6}[prec]
 
-    def time_it(fn, n=reps):
+    def time_it(fn, n=reps, graph=True):
+        """Median and mean device time of fn over n repetitions, L2 flushed
+        before each. With graph (the default, as in the main benchmark) every
+        repetition replays its own CUDA graph of fn, so host launch gaps are
+        not timed; fn must then be capturable."""
         fn()
         torch.cuda.synchronize()
+        if graph:
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):  # warm-up off the default stream (autograd capture)
+                fn()
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.synchronize()
+            graphs, pool = [], None
+            for _ in range(n):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, pool=pool):
+                    fn()
+                pool = g.pool()
+                graphs.append(g)
+            for g in graphs:
+                g.replay()
+            torch.cuda.synchronize()
+            run = iter([g.replay for g in graphs])
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
         for a, b in evs:
+            f = next(run) if graph else fn
             flush.zero_()
             a.record()
-            fn()
+            f()
             b.record()
         torch.cuda.synchronize()
         t = sorted(a.elapsed_time(b) for a, b in evs)
@@ -434,6 +458,7 @@ def run_suite(args):
     def emit(work, op, form, prec, flops, nbytes, ms, err, cpu):
         roof_ms = max(flops / (peak_of(prec) * 1e12), nbytes / (hbm * 1e9)) * 1e3
         line = {"suite": True, "workload": work, "op": op, "form": form, "precision": prec,
+                "launch": "one CUDA graph replay per timed step, L2 flushed before each",
                 "ms_median": ms[0], "ms_mean": ms[1], "gflops": flops / (ms[0] / 1e3) / 1e9,
                 "roofline_ms": roof_ms, "roofline_frac": roof_ms / ms[0],
                 "bound": "tensor" if (prec != "fp32" and flops / peak_of(prec) / 1e12 > nbytes / hbm / 1e9)
@@ -590,7 +615,7 @@ def run_batched(only, modes, api, inputs, oracle, cores, time_it, emit, reps):
             torch.cuda.current_stream().wait_stream(s)
             with torch.cuda.graph(g):
                 batch.run()
-            ms = time_it(g.replay, n=2 if form == "plain" else reps)
+            ms = time_it(g.replay, n=2 if form == "plain" else reps, graph=False)
             emit("512 uneven instances, n,k log-uniform [32,1536], CUDA graph", op, form, prec, fl, by, ms, err, cpu)
 
 

@@ -130,7 +130,13 @@ ln_status ln_timing_read(const char *family, double *total_ms /*host*/, int *lau
  *              before the partial sum is added to an FP32 running sum; 1 is
  *              more accurate, 2 faster;
  *   "tile_n"   128 or 256 (default 256): output tile width of general
- *              (non-symmetric) contractions with one or two split terms.
+ *              (non-symmetric) contractions with one or two split terms;
+ *   "pack_threads" 512 or 1024 (default 512): threads per CTA of the
+ *              split-and-pack stream;
+ *   "split_k"  0 or 1 (default 0): split the K range of tensor-core
+ *              contractions whose output tiles fill less than half the GPU
+ *              (slices exchange FP32 partial sums through the workspace; the
+ *              last slice of a tile to finish adds them in slice order).
  * A knob changes the workspace size of later calls: set it before the
  * *_workspace_size query of a call, not between the query and the call.
  * Unknown keys or values give LN_ERR_INVALID_VALUE. Not for use while kernels
@@ -203,7 +209,8 @@ ln_status ln_correlation(int nsamples, int nfeat, const float *X, int ldx, float
  * statistics and per-block partial sums) is one fixed 8 MiB device array in
  * the library, held on every GPU that loads the library until the process
  * exits. Sizes whose scratch exceeds 8 MiB -- about
- * 40*nfeat + 8*nfeat*ceil(nsamples/256) bytes -- give LN_ERR_INVALID_VALUE
+ * 40*nfeat + 8*nfeat*ceil(nsamples/r) bytes, r the rows per reduction block
+ * (256, 128 or 64, smaller for narrow inputs) -- give LN_ERR_INVALID_VALUE
  * with a message; nothing is launched then. The first call on each device
  * looks up the array's device address (cudaGetSymbolAddress) and must come
  * before any CUDA graph capture on that device. All calls share the array, so

@@ -176,7 +176,7 @@ def timing_read(family: str):
 
 
 def set_tuning(key: str, value: int) -> None:
-    """Set a tensor-core engine knob ("chunk_kt", "tile_n"); see loopnest.h."""
+    """Set an engine knob ("chunk_kt", "tile_n", "pack_threads"); see loopnest.h."""
     _check(lib().ln_set_tuning(key.encode(), int(value)), "ln_set_tuning")
 
 

@@ -77,10 +77,14 @@ LaunchScope::~LaunchScope() {
 namespace {
 std::atomic<int> g_chunk_kt{2};
 std::atomic<int> g_tile_n{256};
+std::atomic<int> g_pack_threads{512};
+std::atomic<int> g_split_k{0};
 }  // namespace
 
 int tune_chunk_kt() { return g_chunk_kt.load(std::memory_order_relaxed); }
 int tune_tile_n() { return g_tile_n.load(std::memory_order_relaxed); }
+int tune_pack_threads() { return g_pack_threads.load(std::memory_order_relaxed); }
+int tune_split_k() { return g_split_k.load(std::memory_order_relaxed); }
 
 bool inject_timeout_requested() {
     const char *v = getenv("LN_FAULT_INJECT");
@@ -116,6 +120,52 @@ struct Ws {
         return p;
     }
 };
+
+// Split-K workspace shared by contractions that run one after another in
+// stream order (sized for the largest of them).
+struct SplitArea {
+    float *part = nullptr;
+    int *cnt = nullptr;
+};
+
+// Split-K of one tcgen05 contraction (umma_ksplit): slices and their workspace.
+struct SplitPlan {
+    int ksplit = 1;
+    float *part = nullptr;
+    int *cnt = nullptr;
+};
+
+void plan_split(Ws &w, long long tiles, int ktot, int bn, SplitPlan &sp) {
+    sp.ksplit = umma_ksplit(tiles, ktot);
+    if (sp.ksplit > 1) {
+        sp.part = w.take<float>(umma_split_part_bytes(tiles, sp.ksplit, bn));
+        sp.cnt = w.take<int>(umma_split_cnt_bytes(tiles, bn));
+    }
+}
+
+// dims: (M, N, K) of general contractions
+void plan_split_area(Ws &w, const int (*dims)[3], int nd, int P, SplitArea &a) {
+    const int bn = umma_tile_n(P, 0);
+    size_t pbytes = 0, cbytes = 0;
+    for (int i = 0; i < nd; ++i) {
+        const long long tiles = ceil_div(dims[i][0], PK_ROWS) * ceil_div(dims[i][1], bn);
+        const int ks = umma_ksplit(tiles, (int)ceil_div(dims[i][2], PK_K));
+        if (ks > 1) {
+            pbytes = std::max(pbytes, umma_split_part_bytes(tiles, ks, bn));
+            cbytes = std::max(cbytes, umma_split_cnt_bytes(tiles, bn));
+        }
+    }
+    if (pbytes) {
+        a.part = w.take<float>(pbytes);
+        a.cnt = w.take<int>(cbytes);
+    }
+}
+
+void apply_split(UmmaProblem &pb, const SplitPlan &sp) {
+    pb.ksplit = sp.ksplit;
+    pb.kpart = sp.part;
+    pb.kcnt = sp.cnt;
+}
 
 // ------------------------------------------------------------------ validation helpers
 struct Span {
@@ -184,6 +234,7 @@ struct Operand {
 struct ContractPlan {
     char *px = nullptr, *py = nullptr;
     int mt = 0, nt = 0, kt = 0, yrt = 0;
+    SplitPlan split;
 };
 
 void contract_geometry(int M, int N, int K, int P, ContractPlan &cp) {
@@ -204,6 +255,7 @@ void plan_contract(Ws &w, int M, int N, int K, ln_form form, ln_precision prec, 
     contract_geometry(M, N, K, P, cp);
     cp.px = w.take<char>(packed_bytes(cp.mt, cp.kt, P));
     cp.py = w.take<char>(packed_bytes(cp.yrt, cp.kt, P));
+    plan_split(w, (long long)cp.mt * cp.nt, cp.kt, umma_tile_n(P, 0), cp.split);
 }
 
 ln_status run_contract(int M, int N, int K, Operand a, Operand b, const EpiParams &epi, ln_form form,
@@ -240,6 +292,7 @@ ln_status run_contract(int M, int N, int K, Operand a, Operand b, const EpiParam
     pb.sym = 0;
     pb.chunk_kt = tune_chunk_kt();
     pb.inject_timeout = inject_timeout_requested();
+    apply_split(pb, cp.split);
     pb.epi = epi;
     return umma_contract(pb, P, st);
 }
@@ -271,6 +324,7 @@ struct ChainPlan {
     char *pa = nullptr, *pb = nullptr, *pt = nullptr, *pc = nullptr;
     ContractPlan g1, g2;
     int ktT = 0;
+    SplitPlan s1, s2;
 };
 
 void plan_chain(Ws &w, int ni, int nj, int nk, int nl, ln_form form, ln_precision prec, ChainPlan &p) {
@@ -286,6 +340,8 @@ void plan_chain(Ws &w, int ni, int nj, int nk, int nl, ln_form form, ln_precisio
     p.pb = w.take<char>(packed_bytes(p.g1.yrt, p.g1.kt, P));
     p.pt = w.take<char>(packed_bytes(p.g1.mt, p.ktT, P));
     p.pc = w.take<char>(packed_bytes(p.g2.yrt, p.g2.kt, P));
+    plan_split(w, (long long)p.g1.mt * p.g1.nt, p.g1.kt, umma_tile_n(P, 0), p.s1);
+    plan_split(w, (long long)p.g2.mt * p.g2.nt, p.g2.kt, umma_tile_n(P, 0), p.s2);
 }
 
 // ------------------------------------------------------------------ covariance / correlation
@@ -294,6 +350,7 @@ struct CovPlan {
     float *hi = nullptr, *lo = nullptr, *rs = nullptr;
     char *pack = nullptr;
     int mt = 0, kt = 0;
+    SplitPlan split;
 };
 
 void plan_cov(Ws &w, int n, int m, ln_form form, ln_precision prec, CovPlan &p) {
@@ -307,6 +364,7 @@ void plan_cov(Ws &w, int n, int m, ln_form form, ln_precision prec, CovPlan &p) 
         p.mt = (int)ceil_div(m, PK_ROWS);
         p.kt = (int)ceil_div(n, PK_K);
         p.pack = w.take<char>(packed_bytes(p.mt, p.kt, prec_terms(prec)));
+        plan_split(w, (long long)p.mt * (p.mt + 1) / 2, p.kt, 128, p.split);
     }
 }
 
@@ -366,6 +424,7 @@ ln_status run_cov(bool corr, int n, int m, const float *X, int ldx, float *out, 
     pb.mt = pb.nt = p.mt;
     pb.sym = 1;
     pb.chunk_kt = tune_chunk_kt();
+    apply_split(pb, p.split);
     pb.epi = e;
     return umma_contract(pb, P, st);
 }
@@ -374,6 +433,7 @@ ln_status run_cov(bool corr, int n, int m, const float *X, int ldx, float *out, 
 struct SymPlan {
     char *pa = nullptr, *pb = nullptr;
     int mt = 0, kt = 0;
+    SplitPlan split;
 };
 
 void plan_sym(Ws &w, bool two, int n, int k, ln_form form, ln_precision prec, SymPlan &p) {
@@ -382,6 +442,7 @@ void plan_sym(Ws &w, bool two, int n, int k, ln_form form, ln_precision prec, Sy
     p.kt = (int)ceil_div(k, PK_K);
     p.pa = w.take<char>(packed_bytes(p.mt, p.kt, prec_terms(prec)));
     if (two) p.pb = w.take<char>(packed_bytes(p.mt, p.kt, prec_terms(prec)));
+    plan_split(w, (long long)p.mt * (p.mt + 1) / 2, (two ? 2 : 1) * p.kt, 128, p.split);
 }
 
 ln_status run_sym(bool two, ln_fill fill, int n, int k, float alpha, const float *A, int lda, const float *B, int ldb,
@@ -449,6 +510,7 @@ ln_status run_sym(bool two, ln_fill fill, int n, int k, float alpha, const float
     pb.mt = pb.nt = p.mt;
     pb.sym = 1;
     pb.chunk_kt = tune_chunk_kt();
+    apply_split(pb, p.split);
     pb.epi = e;
     return umma_contract(pb, P, st);
 }
@@ -567,6 +629,7 @@ ln_status run_batch(bool two, ln_fill fill, int count, const ln_sym_desc *h, con
 struct ChainBwdPlan {
     float *BC = nullptr, *GCt = nullptr, *T = nullptr;
     ContractPlan c;  // sized for the largest of the contractions, reused in stream order
+    SplitArea split;
 };
 
 void plan_chain_bwd(Ws &w, int ni, int nj, int nk, int nl, ln_form form, ln_precision prec, ChainBwdPlan &p) {
@@ -584,17 +647,23 @@ void plan_chain_bwd(Ws &w, int ni, int nj, int nk, int nl, ln_form form, ln_prec
             best = std::max(best, contract_pack_bytes(g, P));
         }
         p.c.px = w.take<char>(best);
+        plan_split_area(w, dims, 6, P, p.split);
     }
 }
 
 ln_status contract_into(int M, int N, int K, Operand a, Operand b, const EpiParams &e, ln_form form, ln_precision prec,
-                        char *pack_area, cudaStream_t st) {
+                        char *pack_area, const SplitArea &split, cudaStream_t st) {
     ContractPlan cp;
     if (form == LN_FORM_INTERNALIZED && tensor_prec(prec)) {
         const int P = prec_terms(prec);
         contract_geometry(M, N, K, P, cp);
         cp.px = pack_area;
         cp.py = pack_area + align_up(packed_bytes(cp.mt, cp.kt, P), 256);
+        cp.split.ksplit = umma_ksplit((long long)cp.mt * cp.nt, cp.kt);
+        if (cp.split.ksplit > 1) {  // the area was planned for these dimensions
+            cp.split.part = split.part;
+            cp.split.cnt = split.cnt;
+        }
     }
     return run_contract(M, N, K, a, b, e, form, prec, cp, st);
 }
@@ -604,6 +673,7 @@ struct CovBwdPlan {
     float *hi = nullptr, *lo = nullptr, *rs = nullptr;
     float *Z = nullptr, *Ws_ = nullptr, *dZ = nullptr;
     char *pack = nullptr;
+    SplitArea split;
 };
 
 void plan_cov_bwd(Ws &w, bool corr, int n, int m, ln_form form, ln_precision prec, CovBwdPlan &p) {
@@ -621,6 +691,8 @@ void plan_cov_bwd(Ws &w, bool corr, int n, int m, ln_form form, ln_precision pre
         ContractPlan g;
         contract_geometry(n, m, m, P, g);
         p.pack = w.take<char>(contract_pack_bytes(g, P));
+        const int dims[1][3] = {{n, m, m}};
+        plan_split_area(w, dims, 1, P, p.split);
     }
 }
 
@@ -668,8 +740,8 @@ ln_status run_cov_bwd(bool corr, int n, int m, const float *X, int ldx, const fl
     LN_TRY(center_matrix(n, m, X, ldx, p.hi, p.lo, corr ? p.rs : nullptr, p.Z, m, st));
     LN_TRY(symmetrize_weights(m, W, ldw, corr ? 1.0f : (float)(1.0 / (double)(n - 1)), corr ? 1 : 0, p.Ws_, st));
     Operand z{p.Z, m, 0}, wsop{p.Ws_, m, 0};
-    if (!corr) return contract_into(n, m, m, z, wsop, epi_store(n, m, 1.0f, dX, lddx), form, prec, p.pack, st);
-    LN_TRY(contract_into(n, m, m, z, wsop, epi_store(n, m, 1.0f, p.dZ, m), form, prec, p.pack, st));
+    if (!corr) return contract_into(n, m, m, z, wsop, epi_store(n, m, 1.0f, dX, lddx), form, prec, p.pack, p.split, st);
+    LN_TRY(contract_into(n, m, m, z, wsop, epi_store(n, m, 1.0f, p.dZ, m), form, prec, p.pack, p.split, st));
     return corr_bwd_finish(n, m, p.Z, m, p.dZ, m, p.rs, dX, lddx, p.partials, st);
 }
 
@@ -715,6 +787,17 @@ ln_status ln_set_tuning(const char *key, int value) {
         g_tile_n.store(value);
         return LN_SUCCESS;
     }
+    if (strcmp(key, "split_k") == 0) {
+        if (value != 0 && value != 1) return fail(LN_ERR_INVALID_VALUE, "split_k must be 0 or 1 (got %d)", value);
+        g_split_k.store(value);
+        return LN_SUCCESS;
+    }
+    if (strcmp(key, "pack_threads") == 0) {
+        if (value != 512 && value != 1024)
+            return fail(LN_ERR_INVALID_VALUE, "pack_threads must be 512 or 1024 (got %d)", value);
+        g_pack_threads.store(value);
+        return LN_SUCCESS;
+    }
     return fail(LN_ERR_INVALID_VALUE, "unknown tuning key '%s'", key);
 }
 
@@ -723,6 +806,8 @@ ln_status ln_get_tuning(const char *key, int *value) {
     if (!key || !value) return fail(LN_ERR_INVALID_VALUE, "NULL argument");
     if (strcmp(key, "chunk_kt") == 0) *value = g_chunk_kt.load();
     else if (strcmp(key, "tile_n") == 0) *value = g_tile_n.load();
+    else if (strcmp(key, "pack_threads") == 0) *value = g_pack_threads.load();
+    else if (strcmp(key, "split_k") == 0) *value = g_split_k.load();
     else return fail(LN_ERR_INVALID_VALUE, "unknown tuning key '%s'", key);
     return LN_SUCCESS;
 }
@@ -877,6 +962,7 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
     g1.epi.N = nj;
     g1.epi.pack = p.pt;
     g1.epi.pack_kt = p.ktT;
+    apply_split(g1, p.s1);
     bool side_done = false;
     LN_TRY(umma_contract(g1, P, st, try_side ? &side : nullptr, &side_done));
     if (try_side && !side_done) LN_TRY(pack_operands(ps + 2, 1, P, st));
@@ -890,6 +976,7 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
     g2.nt = p.g2.nt;
     g2.chunk_kt = tune_chunk_kt();
     g2.inject_timeout = g1.inject_timeout;
+    apply_split(g2, p.s2);
     g2.epi = ef;
     return umma_contract(g2, P, st);
 }
@@ -1058,14 +1145,14 @@ ln_status ln_gemm_chain_bwd(int ni, int nj, int nk, int nl, const float *A, cons
     cudaStream_t st = S(stream);
     char *pk = p.c.px;
     // BC = B C (nk x nl); dA = G BC^T
-    LN_TRY(contract_into(nk, nl, nj, {B, nj, 0}, {C, nl, 0}, epi_store(nk, nl, 1.0f, p.BC, nl), form, prec, pk, st));
-    LN_TRY(contract_into(ni, nk, nl, {G, nl, 0}, {p.BC, nl, 1}, epi_store(ni, nk, 1.0f, dA, nk), form, prec, pk, st));
+    LN_TRY(contract_into(nk, nl, nj, {B, nj, 0}, {C, nl, 0}, epi_store(nk, nl, 1.0f, p.BC, nl), form, prec, pk, p.split, st));
+    LN_TRY(contract_into(ni, nk, nl, {G, nl, 0}, {p.BC, nl, 1}, epi_store(ni, nk, 1.0f, dA, nk), form, prec, pk, p.split, st));
     // GCt = G C^T (ni x nj); dB = A^T GCt
-    LN_TRY(contract_into(ni, nj, nl, {G, nl, 0}, {C, nl, 1}, epi_store(ni, nj, 1.0f, p.GCt, nj), form, prec, pk, st));
-    LN_TRY(contract_into(nk, nj, ni, {A, nk, 1}, {p.GCt, nj, 0}, epi_store(nk, nj, 1.0f, dB, nj), form, prec, pk, st));
+    LN_TRY(contract_into(ni, nj, nl, {G, nl, 0}, {C, nl, 1}, epi_store(ni, nj, 1.0f, p.GCt, nj), form, prec, pk, p.split, st));
+    LN_TRY(contract_into(nk, nj, ni, {A, nk, 1}, {p.GCt, nj, 0}, epi_store(nk, nj, 1.0f, dB, nj), form, prec, pk, p.split, st));
     // T = A B (ni x nj); dC = T^T G
-    LN_TRY(contract_into(ni, nj, nk, {A, nk, 0}, {B, nj, 0}, epi_store(ni, nj, 1.0f, p.T, nj), form, prec, pk, st));
-    return contract_into(nj, nl, ni, {p.T, nj, 1}, {G, nl, 0}, epi_store(nj, nl, 1.0f, dC, nl), form, prec, pk, st);
+    LN_TRY(contract_into(ni, nj, nk, {A, nk, 0}, {B, nj, 0}, epi_store(ni, nj, 1.0f, p.T, nj), form, prec, pk, p.split, st));
+    return contract_into(nj, nl, ni, {p.T, nj, 1}, {G, nl, 0}, epi_store(nj, nl, 1.0f, dC, nl), form, prec, pk, p.split, st);
 }
 
 ln_status ln_covariance_bwd_workspace_size(int nsamples, int nfeat, ln_form form, ln_precision prec, size_t *bytes) {

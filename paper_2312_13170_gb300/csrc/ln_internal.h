@@ -178,6 +178,8 @@ bool pack_stream_eligible(const PackMulti &m);
 // always 128).
 int tune_chunk_kt();
 int tune_tile_n();
+int tune_pack_threads();  // threads per CTA of the split-and-pack stream (512 or 1024)
+int tune_split_k();       // 1: split the K range of contractions with few output tiles
 
 // ln_umma.cu: tcgen05 contraction over packed operands
 struct UmmaSeg {
@@ -194,6 +196,15 @@ struct UmmaProblem {
     int chunk_kt;    // k tiles accumulated in TMEM before the partial sum is added (in FP32
                      // registers) to the running sum; <= 0 means the whole reduction
     int inject_timeout;  // test hook: the producer issues no copy, so a bounded wait runs out
+    // split-K (single problems only; <= 1 means none): work item t is output tile
+    // t / ksplit, k slice t % ksplit (a contiguous range of the nseg * kt k tiles).
+    // Every slice's epilogue warp stores its FP32 partial sums to kpart
+    // ([tile][slice][epilogue warp][4096]) and counts its arrival in kcnt
+    // ([tile][epilogue warp], zero at launch); the last to arrive adds the slices
+    // in slice order and runs the epilogue.
+    int ksplit;
+    float *kpart;
+    int *kcnt;
     EpiParams epi;
 };
 // True when LN_FAULT_INJECT=timeout is set in the environment (read per call).
@@ -203,6 +214,16 @@ bool inject_timeout_requested();
 // `nt` of a problem counts tiles of this width, and the packed N-side operand
 // must hold 128 * (width / 128) * nt rows (zero padded).
 int umma_tile_n(int terms, int sym);
+// Split-K slices for a single problem with `tiles` output tiles and `ktot`
+// k tiles (segments x k tiles): enough to fill the SMs, at least four k tiles
+// each, none empty; 1 when the tiles already fill the GPU or the "split_k"
+// knob is off (its default: the slices' FP32 partials, a burst of fresh
+// writes through L2, cost more than the idle SMs save on GB300).
+int umma_ksplit(long long tiles, int ktot);
+// Workspace of a split: partial sums and arrival counters (bytes, each
+// 256-aligned in the plan).
+size_t umma_split_part_bytes(long long tiles, int ksplit, int bn);
+size_t umma_split_cnt_bytes(long long tiles, int bn);
 // With `side`, a contraction with the packing epilogue may also pack that
 // operand on SMs without an output tile; *side_done says whether it did (if
 // not, the caller packs it).

@@ -73,7 +73,8 @@ extern "C" ln_status ln_covariance_noalloc(int nsamples, int nfeat, const float 
     if (L.total > NOALLOC_SCRATCH_BYTES)
         return fail(LN_ERR_INVALID_VALUE,
                     "ln_covariance_noalloc needs %zu bytes of scratch for %d x %d, more than its fixed %zu bytes "
-                    "(about 40*nfeat + 8*nfeat*ceil(nsamples/256) bytes are needed); use ln_covariance with a workspace",
+                    "(about 40*nfeat + 8*nfeat*ceil(nsamples/r) bytes, r = 64 to 256 rows per reduction block); "
+                    "use ln_covariance with a workspace",
                     L.total, nsamples, nfeat, NOALLOC_SCRATCH_BYTES);
     int dev = 0;
     LN_CUDA_TRY(cudaGetDevice(&dev));

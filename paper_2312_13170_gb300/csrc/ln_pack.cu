@@ -141,13 +141,10 @@ __global__ __launch_bounds__(256) void k_pack_multi(const __grid_constant__ Pack
 }
 
 // Persistent bulk-copy pack stream (ln_pack_stream.cuh), one CTA per SM.
-constexpr int PS_KERNEL_THREADS = 512;
-
-template <int P>
-__global__ __launch_bounds__(PS_KERNEL_THREADS, 1) void k_pack_stream(const __grid_constant__ PackMulti m, int ns,
-                                                                       int nout) {
+template <int P, int NT>
+__global__ __launch_bounds__(NT, 1) void k_pack_stream(const __grid_constant__ PackMulti m, int ns, int nout) {
     extern __shared__ __align__(128) unsigned char ps_smem[];
-    pack_stream<P, PS_KERNEL_THREADS>(m, blockIdx.x, gridDim.x, ps_smem, ns, nout);
+    pack_stream<P, NT>(m, blockIdx.x, gridDim.x, ps_smem, ns, nout);
 }
 
 // Batched layout, one CTA of 1024 threads: (1) rank instances by decreasing
@@ -360,7 +357,7 @@ constexpr int stream_outs(int terms) { return terms >= 3 ? 2 : 3; }
 static_assert(pack_stream_smem(stream_stages(2), stream_outs(2), 2) <= 227 * 1024, "pack stream smem");
 static_assert(pack_stream_smem(stream_stages(3), stream_outs(3), 3) <= 227 * 1024, "pack stream smem");
 
-template <int P>
+template <int P, int NT>
 ln_status launch_pack_stream(const PackMulti &m, cudaStream_t st) {
     const int ns = stream_stages(P), nout = stream_outs(P);
     const int bytes = pack_stream_smem(ns, nout, P);
@@ -370,14 +367,19 @@ ln_status launch_pack_stream(const PackMulti &m, cudaStream_t st) {
     int dev = 0;
     LN_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        LN_CUDA_TRY(cudaFuncSetAttribute(k_pack_stream<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        LN_CUDA_TRY(cudaFuncSetAttribute(k_pack_stream<P, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     const int tiles = m.prefix[m.count];
     const int grid = std::min(tiles, sm_count());
     LaunchScope ls_(FAM_PACK, st);
-    k_pack_stream<P><<<grid, PS_KERNEL_THREADS, bytes, st>>>(m, ns, nout);
+    k_pack_stream<P, NT><<<grid, NT, bytes, st>>>(m, ns, nout);
     return check_launch("split-and-pack stream");
+}
+
+template <int P>
+ln_status launch_pack_stream(const PackMulti &m, cudaStream_t st) {
+    return tune_pack_threads() == 1024 ? launch_pack_stream<P, 1024>(m, st) : launch_pack_stream<P, 512>(m, st);
 }
 
 }  // namespace

@@ -18,7 +18,17 @@ namespace {
 inline unsigned rows_grid(long long rows) { return (unsigned)(rows < 65535 ? rows : 65535); }
 
 constexpr int SC = 128;  // columns per CTA (32 threads x float4)
-constexpr int SR = 256;  // rows per CTA
+constexpr int EW_ROWS = 32;  // rows per CTA of the element-wise kernels
+
+// Rows per CTA of the column reductions: the largest of 256, 128, 64 that
+// still gives about four CTAs per SM of a 152-SM GPU (a fixed target, so that
+// workspace sizes do not depend on the device).
+int stats_rows(int n, int m) {
+    const long long colb = ceil_div(m, SC);
+    for (int sr = 256; sr > 64; sr >>= 1)
+        if (colb * ceil_div(n, sr) >= 608) return sr;
+    return 64;
+}
 
 __device__ __forceinline__ float4 ld4_guard(const float *row, int c, int m, bool vec) {
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -52,11 +62,11 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &t) {
 // keep FP64-level accuracy at FP32 speed.
 template <int PASS>
 __global__ __launch_bounds__(256) void k_col_partial(int n, int m, const float *__restrict__ X, long long ldx,
-                                                     const double *__restrict__ mean, double *partials) {
+                                                     const double *__restrict__ mean, double *partials, int sr) {
     __shared__ double red[8][SC];
     const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
     const int c = blockIdx.x * SC + cx * 4;
-    const int r0 = blockIdx.y * SR;
+    const int r0 = blockIdx.y * sr;
     const bool vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && ((ldx & 3) == 0);
     float mh[4] = {0, 0, 0, 0};
     double ml[4] = {0, 0, 0, 0};
@@ -71,7 +81,7 @@ __global__ __launch_bounds__(256) void k_col_partial(int n, int m, const float *
     float h1[4] = {0, 0, 0, 0}, l1[4] = {0, 0, 0, 0};  // sum x (pass 0) or sum d (pass 1)
     float h2[4] = {0, 0, 0, 0}, l2[4] = {0, 0, 0, 0};  // sum d^2 (pass 1)
     int cnt = 0;
-    const int r1 = min(n, r0 + SR);
+    const int r1 = min(n, r0 + sr);
 #pragma unroll 4
     for (int r = r0 + ry; r < r1; r += 8) {
         float4 v = ld4_guard(X + (long long)r * ldx, c, m, vec);
@@ -169,99 +179,185 @@ __global__ void k_sym_scale(int n, int fill, float beta, float *C, long long ldc
     }
 }
 
-__global__ void k_center(int n, int m, const float *__restrict__ X, long long ldx, const float *__restrict__ hi,
-                         const float *__restrict__ lo, const float *__restrict__ rs, float *Y, long long ldy) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
-    for (int r = blockIdx.y; r < n; r += gridDim.y) {
-        float v = (X[(long long)r * ldx + j] - hi[j]) - lo[j];
-        if (rs) v *= rs[j];
-        Y[(long long)r * ldy + j] = v;
+// Element-wise kernels: a CTA of 64 x 4 threads covers 256 columns x EW_ROWS
+// rows, each thread 4 consecutive columns (one 16-byte access when the rows
+// are 16-byte aligned) of every fourth row.
+__device__ __forceinline__ void ld4(const float *row, int c, int m, bool vec, float (&v)[4]) {
+    if (vec && c + 3 < m) {
+        const float4 x = __ldg(reinterpret_cast<const float4 *>(row + c));
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+        return;
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = (c + q < m) ? __ldg(row + c + q) : 0.0f;
+}
+__device__ __forceinline__ void st4(float *row, int c, int m, bool vec, const float (&v)[4]) {
+    if (vec && c + 3 < m) {
+        *reinterpret_cast<float4 *>(row + c) = make_float4(v[0], v[1], v[2], v[3]);
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (c + q < m) row[c + q] = v[q];
 }
 
-__global__ void k_symw(int m, const float *__restrict__ W, long long ldw, float scale, int zero_diag, float *Ws) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
-    for (int i = blockIdx.y; i < m; i += gridDim.y) {
-        float v = scale * (W[(long long)i * ldw + j] + W[(long long)j * ldw + i]);
-        if (zero_diag && i == j) v = 0.0f;
-        Ws[(long long)i * m + j] = v;
+// Y = (X - (hi + lo)) * rs, column-wise offsets and scales (rs optional)
+__global__ __launch_bounds__(256) void k_center(int n, int m, const float *__restrict__ X, long long ldx,
+                                                const float *__restrict__ hi, const float *__restrict__ lo,
+                                                const float *__restrict__ rs, float *Y, long long ldy, int vec) {
+    const int c = (blockIdx.x * 64 + threadIdx.x) * 4;
+    if (c >= m) return;
+    float h[4], l[4], sc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const bool in = c + q < m;
+        h[q] = in ? hi[c + q] : 0.0f;
+        l[q] = in ? lo[c + q] : 0.0f;
+        sc[q] = (in && rs) ? rs[c + q] : 1.0f;
     }
-}
-
-// Partial column sums of Z .* dZ (PASS 0) or of dX (PASS 1) over 128-row chunks.
-template <int PASS>
-__global__ __launch_bounds__(256) void k_pair_partial(int n, int m, const float *__restrict__ Z, long long ldz,
-                                                      const float *__restrict__ dZ, long long lddz,
-                                                      double *partials) {
-    __shared__ double red[8][SC];
-    const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
-    const int r0 = blockIdx.y * SR;
-    double acc[4] = {0, 0, 0, 0};
-    for (int r = r0 + ry; r < min(n, r0 + SR); r += 8) {
+    const int r0 = blockIdx.y * EW_ROWS, r1 = min(n, r0 + EW_ROWS);
+    for (int r = r0 + threadIdx.y; r < r1; r += 4) {
+        float v[4];
+        ld4(X + (long long)r * ldx, c, m, vec != 0, v);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            int c = blockIdx.x * SC + cx * 4 + q;
-            if (c < m) {
-                float a = Z[(long long)r * ldz + c];
-                acc[q] += (PASS == 0) ? (double)a * (double)dZ[(long long)r * lddz + c] : (double)a;
-            }
+            v[q] = (v[q] - h[q]) - l[q];
+            if (rs) v[q] *= sc[q];
+        }
+        st4(Y + (long long)r * ldy, c, m, vec != 0, v);
+    }
+}
+
+// Ws = scale * (W + W^T) (diagonal zeroed on request), through a 32 x 32
+// shared-memory tile so that both W reads are coalesced.
+__global__ __launch_bounds__(256) void k_symw(int m, const float *__restrict__ W, long long ldw, float scale,
+                                              int zero_diag, float *Ws) {
+    __shared__ float t[32][33];
+    const int bi = blockIdx.y * 32, bj = blockIdx.x * 32, tx = threadIdx.x, ty = threadIdx.y;
+    for (int k = ty; k < 32; k += 8) {  // t[k][tx] = W[bj + k][bi + tx]
+        const int r = bj + k, c = bi + tx;
+        t[k][tx] = (r < m && c < m) ? W[(long long)r * ldw + c] : 0.0f;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int i = bi + k, j = bj + tx;
+        if (i < m && j < m) {
+            float v = scale * (W[(long long)i * ldw + j] + t[tx][k]);  // W[j][i] = t[j - bj][i - bi]
+            if (zero_diag && i == j) v = 0.0f;
+            Ws[(long long)i * m + j] = v;
+        }
+    }
+}
+
+// Per-column partial sums over a chunk of rows, for the correlation adjoint:
+// S0 = sum Z.*dZ, S1 = sum dZ, S2 = sum Z, each kept per thread as a
+// compensated FP32 pair (products carry their exact FMA residual) and
+// combined across the CTA in FP64. partials = [3][nchunks][m].
+__global__ __launch_bounds__(256) void k_corr_cols(int n, int m, const float *__restrict__ Z, long long ldz,
+                                                   const float *__restrict__ dZ, long long lddz, double *partials,
+                                                   int sr, int nch) {
+    __shared__ double red[3][8][SC];
+    const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
+    const int c = blockIdx.x * SC + cx * 4;
+    const int r0 = blockIdx.y * sr, r1 = min(n, r0 + sr);
+    const bool vz = ((reinterpret_cast<uintptr_t>(Z) & 15) == 0) && ((ldz & 3) == 0);
+    const bool vd = ((reinterpret_cast<uintptr_t>(dZ) & 15) == 0) && ((lddz & 3) == 0);
+    float h[3][4] = {}, l[3][4] = {};
+#pragma unroll 2
+    for (int r = r0 + ry; r < r1; r += 8) {
+        float z[4], g[4];
+        ld4(Z + (long long)r * ldz, c, m, vz, z);
+        ld4(dZ + (long long)r * lddz, c, m, vd, g);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float s, t;
+            const float p = z[q] * g[q], pe = fmaf(z[q], g[q], -p);
+            two_sum(h[0][q], p, s, t);
+            h[0][q] = s;
+            l[0][q] += t + pe;
+            two_sum(h[1][q], g[q], s, t);
+            h[1][q] = s;
+            l[1][q] += t;
+            two_sum(h[2][q], z[q], s, t);
+            h[2][q] = s;
+            l[2][q] += t;
         }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) red[ry][cx * 4 + q] = acc[q];
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) red[k][ry][cx * 4 + q] = (double)h[k][q] + (double)l[k][q];
     __syncthreads();
     if (threadIdx.x < SC) {
-        int col = blockIdx.x * SC + threadIdx.x;
-        double s = 0.0;
+        const int col = blockIdx.x * SC + threadIdx.x;
+        if (col < m) {
 #pragma unroll
-        for (int g = 0; g < 8; ++g) s += red[g][threadIdx.x];
-        if (col < m) partials[(long long)blockIdx.y * m + col] = s;
+            for (int k = 0; k < 3; ++k) {
+                double s = 0.0;
+#pragma unroll
+                for (int gi = 0; gi < 8; ++gi) s += red[k][gi][threadIdx.x];
+                partials[((long long)k * nch + blockIdx.y) * m + col] = s;
+            }
+        }
     }
 }
 
-__global__ void k_sum_partials(int m, int nchunks, const double *__restrict__ partials, double *out) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+// d_j = sum_r Z dZ and the column mean of dXc = (dZ - Z d) rs, which is
+// rs_j (sum dZ - d_j sum Z) / n (the adjoint of the centring subtracts it).
+__global__ void k_corr_cols_final(int n, int m, int nch, const double *__restrict__ partials,
+                                  const float *__restrict__ rs, float *d, float *cmean) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m) return;
-    double s = 0.0;
-    for (int ch = 0; ch < nchunks; ++ch) s += partials[(long long)ch * m + j];
-    out[j] = s;
-}
-
-// dX = (dZ - Z * dot) * rs   (the adjoint of the column normalisation)
-__global__ void k_corr_dxc(int n, int m, const float *__restrict__ Z, long long ldz, const float *__restrict__ dZ,
-                           long long lddz, const double *__restrict__ dot, const float *__restrict__ rs, float *dX,
-                           long long lddx) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
-    const float d = (float)dot[j], s = rs[j];
-    for (int r = blockIdx.y; r < n; r += gridDim.y) {
-        float z = Z[(long long)r * ldz + j];
-        float g = dZ[(long long)r * lddz + j];
-        dX[(long long)r * lddx + j] = (g - z * d) * s;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int ch = 0; ch < nch; ++ch) {
+        s0 += partials[(long long)ch * m + j];
+        s1 += partials[((long long)nch + ch) * m + j];
+        s2 += partials[(2LL * nch + ch) * m + j];
     }
+    d[j] = (float)s0;
+    cmean[j] = (float)((double)rs[j] * (s1 - s0 * s2) / (double)n);
 }
 
-// dX -= colsum / n   (the adjoint of the centring)
-__global__ void k_sub_colmean(int n, int m, const double *__restrict__ colsum, float *dX, long long lddx) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
-    const float c = (float)(colsum[j] / (double)n);
-    for (int r = blockIdx.y; r < n; r += gridDim.y) dX[(long long)r * lddx + j] -= c;
+// dX = (dZ - Z * d) * rs - cmean
+__global__ __launch_bounds__(256) void k_corr_dx(int n, int m, const float *__restrict__ Z, long long ldz,
+                                                 const float *__restrict__ dZ, long long lddz,
+                                                 const float *__restrict__ d, const float *__restrict__ rs,
+                                                 const float *__restrict__ cmean, float *dX, long long lddx, int vec) {
+    const int c = (blockIdx.x * 64 + threadIdx.x) * 4;
+    if (c >= m) return;
+    float dd[4], sc[4], cm[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const bool in = c + q < m;
+        dd[q] = in ? d[c + q] : 0.0f;
+        sc[q] = in ? rs[c + q] : 0.0f;
+        cm[q] = in ? cmean[c + q] : 0.0f;
+    }
+    const int r0 = blockIdx.y * EW_ROWS, r1 = min(n, r0 + EW_ROWS);
+    for (int r = r0 + threadIdx.y; r < r1; r += 4) {
+        float z[4], g[4];
+        ld4(Z + (long long)r * ldz, c, m, vec != 0, z);
+        ld4(dZ + (long long)r * lddz, c, m, vec != 0, g);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) g[q] = fmaf(-z[q], dd[q], g[q]) * sc[q] - cm[q];
+        st4(dX + (long long)r * lddx, c, m, vec != 0, g);
+    }
 }
 
 }  // namespace
 
-size_t col_stats_partials_bytes(int n, int m) { return sizeof(double) * (size_t)ceil_div(n, SR) * (size_t)m; }
+size_t col_stats_partials_bytes(int n, int m) {
+    return sizeof(double) * (size_t)ceil_div(n, stats_rows(n, m)) * (size_t)m;
+}
 
 ln_status col_stats(int n, int m, const float *X, long long ldx, double *mean, double *ss, float *off_hi,
                     float *off_lo, float *rs, double *partials, cudaStream_t st) {
-    const int nch = (int)ceil_div(n, SR);
+    const int sr = stats_rows(n, m);
+    const int nch = (int)ceil_div(n, sr);
     dim3 grid((unsigned)ceil_div(m, SC), (unsigned)nch);
-    { LaunchScope ls_(FAM_STATS, st); k_col_partial<0><<<grid, 256, 0, st>>>(n, m, X, ldx, nullptr, partials); }
+    { LaunchScope ls_(FAM_STATS, st); k_col_partial<0><<<grid, 256, 0, st>>>(n, m, X, ldx, nullptr, partials, sr); }
     { LaunchScope ls_(FAM_STATS, st); k_col_final<0><<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(n, m, nch, partials, mean); }
-    { LaunchScope ls_(FAM_STATS, st); k_col_partial<1><<<grid, 256, 0, st>>>(n, m, X, ldx, mean, partials); }
+    { LaunchScope ls_(FAM_STATS, st); k_col_partial<1><<<grid, 256, 0, st>>>(n, m, X, ldx, mean, partials, sr); }
     { LaunchScope ls_(FAM_STATS, st); k_col_final<1><<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(n, m, nch, partials, ss); }
     if (off_hi || rs) {
         LaunchScope ls_(FAM_STATS, st);
@@ -288,35 +384,58 @@ ln_status sym_fill_zero_k(int n, int fill, float beta, float *C, long long ldc, 
     return check_launch("symmetric scale");
 }
 
+namespace {
+bool rows16(const void *p, long long ld) { return ((reinterpret_cast<uintptr_t>(p) & 15) == 0) && ((ld & 3) == 0); }
+dim3 ew_grid(int n, int m) { return dim3((unsigned)ceil_div(m, 256), (unsigned)ceil_div(n, EW_ROWS)); }
+}  // namespace
+
 ln_status center_matrix(int n, int m, const float *X, long long ldx, const float *off_hi, const float *off_lo,
                         const float *rs, float *Y, long long ldy, cudaStream_t st) {
-    { LaunchScope ls_(FAM_STATS, st); k_center<<<dim3((unsigned)ceil_div(m, 256), rows_grid(n)), 256, 0, st>>>(n, m, X, ldx, off_hi, off_lo, rs, Y, ldy); }
+    if (n == 0 || m == 0) return LN_SUCCESS;
+    if (ceil_div(n, EW_ROWS) > 65535) return fail(LN_ERR_INVALID_VALUE, "too many rows to centre (%d)", n);
+    const int vec = rows16(X, ldx) && rows16(Y, ldy);
+    {
+        LaunchScope ls_(FAM_STATS, st);
+        k_center<<<ew_grid(n, m), dim3(64, 4), 0, st>>>(n, m, X, ldx, off_hi, off_lo, rs, Y, ldy, vec);
+    }
     return check_launch("centre");
 }
 
 ln_status symmetrize_weights(int m, const float *W, long long ldw, float scale, int zero_diag, float *Ws,
                              cudaStream_t st) {
-    { LaunchScope ls_(FAM_STATS, st); k_symw<<<dim3((unsigned)ceil_div(m, 256), rows_grid(m)), 256, 0, st>>>(m, W, ldw, scale, zero_diag, Ws); }
+    if (m == 0) return LN_SUCCESS;
+    if (ceil_div(m, 32) > 65535) return fail(LN_ERR_INVALID_VALUE, "weights too large to symmetrise (%d)", m);
+    const unsigned g = (unsigned)ceil_div(m, 32);
+    { LaunchScope ls_(FAM_STATS, st); k_symw<<<dim3(g, g), dim3(32, 8), 0, st>>>(m, W, ldw, scale, zero_diag, Ws); }
     return check_launch("symmetrise weights");
 }
 
 size_t corr_bwd_partials_bytes(int n, int m) {
-    return sizeof(double) * ((size_t)ceil_div(n, SR) * (size_t)m + 2 * (size_t)m);
+    return sizeof(double) * (3 * (size_t)ceil_div(n, stats_rows(n, m)) * (size_t)m + (size_t)m);
 }
 
 ln_status corr_bwd_finish(int n, int m, const float *Z, long long ldz, const float *dZ, long long lddz,
                           const float *rs, float *dX, long long lddx, double *partials, cudaStream_t st) {
-    const int nch = (int)ceil_div(n, SR);
-    double *dot = partials + (size_t)nch * m;
-    double *colsum = dot + m;
-    dim3 grid((unsigned)ceil_div(m, SC), (unsigned)nch);
-    dim3 g2((unsigned)ceil_div(m, 256), rows_grid(n));
-    { LaunchScope ls_(FAM_STATS, st); k_pair_partial<0><<<grid, 256, 0, st>>>(n, m, Z, ldz, dZ, lddz, partials); }
-    { LaunchScope ls_(FAM_STATS, st); k_sum_partials<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(m, nch, partials, dot); }
-    { LaunchScope ls_(FAM_STATS, st); k_corr_dxc<<<g2, 256, 0, st>>>(n, m, Z, ldz, dZ, lddz, dot, rs, dX, lddx); }
-    { LaunchScope ls_(FAM_STATS, st); k_pair_partial<1><<<grid, 256, 0, st>>>(n, m, dX, lddx, nullptr, 0, partials); }
-    { LaunchScope ls_(FAM_STATS, st); k_sum_partials<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(m, nch, partials, colsum); }
-    { LaunchScope ls_(FAM_STATS, st); k_sub_colmean<<<g2, 256, 0, st>>>(n, m, colsum, dX, lddx); }
+    if (n == 0 || m == 0) return LN_SUCCESS;
+    if (ceil_div(n, EW_ROWS) > 65535) return fail(LN_ERR_INVALID_VALUE, "too many rows (%d)", n);
+    const int sr = stats_rows(n, m);
+    const int nch = (int)ceil_div(n, sr);
+    float *d = reinterpret_cast<float *>(partials + 3 * (size_t)nch * m);
+    float *cmean = d + m;
+    const int vec = rows16(Z, ldz) && rows16(dZ, lddz) && rows16(dX, lddx);
+    {
+        LaunchScope ls_(FAM_STATS, st);
+        k_corr_cols<<<dim3((unsigned)ceil_div(m, SC), (unsigned)nch), 256, 0, st>>>(n, m, Z, ldz, dZ, lddz, partials,
+                                                                                 sr, nch);
+    }
+    {
+        LaunchScope ls_(FAM_STATS, st);
+        k_corr_cols_final<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(n, m, nch, partials, rs, d, cmean);
+    }
+    {
+        LaunchScope ls_(FAM_STATS, st);
+        k_corr_dx<<<ew_grid(n, m), dim3(64, 4), 0, st>>>(n, m, Z, ldz, dZ, lddz, d, rs, cmean, dX, lddx, vec);
+    }
     return check_launch("correlation adjoint");
 }
 

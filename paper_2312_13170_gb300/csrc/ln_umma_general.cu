@@ -31,6 +31,23 @@ int epi_kind(const EpiParams &e) {
 
 int umma_tile_n(int terms, int sym) { return (!sym && terms <= 2) ? tune_tile_n() : 128; }
 
+int umma_ksplit(long long tiles, int ktot) {
+    const int sms = sm_count();
+    if (!tune_split_k() || tiles <= 0 || ktot < 8 || 2 * tiles > sms) return 1;
+    long long ks = sms / tiles;  // slices per tile that the SMs hold at once
+    if (ks > ktot / 4) ks = ktot / 4;
+    if (ks > 16) ks = 16;
+    if (ks < 2) return 1;
+    const int per = (int)((ktot + ks - 1) / ks);
+    return (ktot + per - 1) / per;  // no empty slice
+}
+
+size_t umma_split_part_bytes(long long tiles, int ksplit, int bn) {
+    return ksplit > 1 ? (size_t)tiles * ksplit * (bn / 32) * 4096 * sizeof(float) : 0;
+}
+
+size_t umma_split_cnt_bytes(long long tiles, int bn) { return (size_t)tiles * (bn / 32) * sizeof(int); }
+
 ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st, const PackMulti *side, bool *side_done) {
     if (side_done) *side_done = false;
     long long tiles = p.sym ? (long long)p.mt * (p.mt + 1) / 2 : (long long)p.mt * p.nt;
@@ -42,6 +59,12 @@ ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st, const 
         return umma_contract_sym(p, terms, st);
     }
     if (p.sym) return fail(LN_ERR_INVALID_VALUE, "symmetric problem needs the symmetric epilogue");
+    if (p.ksplit > 1) {
+        if (!p.kpart || !p.kcnt) return fail(LN_ERR_INVALID_VALUE, "split-K without its workspace");
+        tiles *= p.ksplit;
+        LN_CUDA_TRY(cudaMemsetAsync(p.kcnt, 0, umma_split_cnt_bytes(tiles / p.ksplit, umma_tile_n(terms, 0)), st));
+    }
+    if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many work items");
     const int total = (int)tiles;
     const bool wide = umma_tile_n(terms, 0) == 256;
     switch (terms) {

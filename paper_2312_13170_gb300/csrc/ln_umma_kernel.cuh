@@ -14,9 +14,11 @@
 // epilogue of one tile overlaps the MMAs of the next.
 //
 // Warp roles: warp 0 issues bulk copies, warp 1 allocates TMEM and issues
-// MMAs (one lane each), BN/32 epilogue warps read the accumulator back with
-// tcgen05.ld (each warp owns the 32 TMEM lanes = output rows its warp index
-// may access, and 128 of the tile's columns) and run the shared epilogue.
+// MMAs (one lane each), BN/32 epilogue warps from warp EPI0 on read the
+// accumulator back with tcgen05.ld (each warp owns the 32 TMEM lanes = output
+// rows its warp index may access, and 128 of the tile's columns) and run the
+// shared epilogue. With BN = 256 the epilogue is two whole warpgroups that
+// take registers from warpgroup 0 with setmaxnreg.
 //
 // Accumulation precision: the tensor core's FP32 accumulation into TMEM loses
 // accuracy in proportion to the number of accumulation steps, so every
@@ -60,9 +62,22 @@ enum : int { ERR_PRODUCER = 1, ERR_MMA = 2, ERR_EPILOGUE = 4, ERR_DRAIN = 8 };
 // descriptor into shared memory; the MMA and epilogue roles read the slot and
 // release it (sempty) when they have finished the tile.
 struct SchedSlot {
-    int t, mi, ni, pad;
+    int t, mi, ni, ks;  // work item, row tile, column tile, k slice
     UmmaProblem prob;
 };
+
+// k tiles [qa, qb) of slice ks of a problem's nseg * kt flattened k range
+__device__ __forceinline__ void slice_range(const UmmaProblem &p, int ks, int &qa, int &qb) {
+    const int ktot = p.nseg * p.kt;
+    if (p.ksplit <= 1) {
+        qa = 0;
+        qb = ktot;
+        return;
+    }
+    const int per = (ktot + p.ksplit - 1) / p.ksplit;
+    qa = ks * per;
+    qb = qa + per < ktot ? qa + per : ktot;
+}
 
 struct Ctl {
     uint64_t full[MAX_STAGES];
@@ -225,7 +240,17 @@ struct Products<3> {  // the six products of order >= 2^-16
 template <int P, int BN>
 struct Cfg {
     static constexpr int NEPI = BN / 32;  // epilogue warps: 4 per 128 columns
-    static constexpr int NTHREADS = 64 + 32 * NEPI;
+    // first epilogue warp: BN = 256 gives the epilogue two whole warpgroups
+    // (warpgroup 0 = producer, MMA issuer and two idle warps), so that
+    // setmaxnreg can move registers from warpgroup 0 to the epilogue, whose
+    // 128 running sums per thread do not fit in the 168 registers a thread of
+    // a 12-warp CTA gets at launch
+    static constexpr int EPI0 = BN == 256 ? 4 : 2;
+    static constexpr int NTHREADS = 32 * (EPI0 + NEPI);
+    static constexpr bool REG_SPLIT = BN == 256;
+    static constexpr int REG_LAUNCH = ((65536 / NTHREADS) & ~7) > 255 ? 255 : ((65536 / NTHREADS) & ~7);
+    static constexpr int REG_LO = 64;
+    static constexpr int REG_HI = ((REG_LAUNCH * NTHREADS - 128 * REG_LO) / (32 * NEPI)) & ~7;
     static constexpr int NACC = TMEM_COLS / BN;
     static constexpr int HALVES = BN / 128;
     static constexpr int A_BYTES = P * PK_TILE_BYTES;
@@ -238,6 +263,9 @@ struct Cfg {
     static constexpr int SMEM = 1024 + CTL_BYTES + STAGES * STAGE_BYTES + SCRATCH_BYTES;
     static constexpr int NLD = BN == 128 ? 4 : 2;  // tcgen05.ld (x16) in flight per wait
     static_assert(NACC <= MAX_NACC && STAGES >= 2, "tile configuration does not fit");
+    static_assert(!REG_SPLIT || (128 * REG_LO + 32 * NEPI * REG_HI <= REG_LAUNCH * NTHREADS && REG_HI <= 256 &&
+                                 NTHREADS == 128 + 32 * NEPI),
+                  "register split exceeds the launch allocation");
     // input stages of the pack stream that spare CTAs run in this shared memory
     static constexpr int SIDE_NOUT = SMEM - 1024 - 3 * P * PK_TILE_BYTES >= 4 * PS_IN_BYTES ? 3 : 2;
     static constexpr int SIDE_NS_RAW = (SMEM - 1024 - SIDE_NOUT * P * PK_TILE_BYTES) / PS_IN_BYTES;
@@ -516,7 +544,11 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = ctl->tmem_base;
-
+    // Each warpgroup changes its register count at the top of its own branch
+    // (the role code is then allocated under that count); the host checked that
+    // the launch allocation covers the split.
+    if (warp < C::EPI0) {
+    if constexpr (C::REG_SPLIT) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(C::REG_LO));
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
@@ -534,11 +566,13 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                 if (!wait_phase(ctl, &ctl->sempty[s], ((sidx / SCHED) & 1) ^ 1, ERR_PRODUCER, true, 64)) break;
                 SchedSlot &sl = ctl->slot[s];
                 TileRef tr{&single, 0, 0};
+                const int ksplit = (!BATCHED && single.ksplit > 1) ? single.ksplit : 1;
                 if (t >= 0) {
-                    tr = resolve<BATCHED>(t, &single, probs, prefix, owner);
+                    tr = resolve<BATCHED>(t / ksplit, &single, probs, prefix, owner);
                     sl.prob = *tr.p;  // roles read the problem from shared memory, not from registers
                     sl.mi = tr.mi;
                     sl.ni = tr.ni;
+                    sl.ks = t - (t / ksplit) * ksplit;
                 }
                 sl.t = t;
                 mbar_arrive(&ctl->sfull[s]);
@@ -547,9 +581,12 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                 const UmmaProblem &pb = *tr.p;
                 if (pb.inject_timeout) break;  // nothing arrives on full[]: the MMA wait runs out
                 bool ok = true;
-                for (int sg = 0; sg < pb.nseg && ok; ++sg) {
-                    const char *xb = pb.seg[sg].X + (size_t)tr.mi * pb.x_kt * C::A_BYTES;
-                    for (int kt = 0; kt < pb.kt; ++kt) {
+                int qa, qb;
+                slice_range(pb, sl.ks, qa, qb);
+                {
+                    for (int q = qa; q < qb; ++q) {
+                        const int sg = q / pb.kt, kt = q - sg * pb.kt;
+                        const char *xb = pb.seg[sg].X + (size_t)tr.mi * pb.x_kt * C::A_BYTES;
                         const int st = it % C::STAGES;
                         if (!wait_phase(ctl, &ctl->empty[st], ((it / C::STAGES) & 1) ^ 1, ERR_PRODUCER, true, 32)) {
                             ok = false;
@@ -592,11 +629,12 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                 ++sidx;
                 if (sl.t < 0) break;
                 const UmmaProblem &pb = sl.prob;
-                const int ktot = pb.nseg * pb.kt;
-                const int ck = pb.chunk_kt > 0 ? pb.chunk_kt : (ktot > 0 ? ktot : 1);
+                int qa, qb;
+                slice_range(pb, sl.ks, qa, qb);
+                const int ck = pb.chunk_kt > 0 ? pb.chunk_kt : (qb - qa > 0 ? qb - qa : 1);
                 bool ok = true;
                 // one TMEM accumulator buffer per chunk of ck k tiles
-                for (int q0 = 0; q0 < ktot && ok; q0 += ck) {
+                for (int q0 = qa; q0 < qb && ok; q0 += ck) {
                     const int b = acc % C::NACC;
                     if (!wait_phase(ctl, &ctl->tempty[b], ((acc / C::NACC) & 1) ^ 1, ERR_MMA)) {
                         ok = false;
@@ -604,7 +642,7 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                     }
                     tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)(b * BN);
-                    const int q1 = q0 + ck < ktot ? q0 + ck : ktot;
+                    const int q1 = q0 + ck < qb ? q0 + ck : qb;
                     for (int q = q0; q < q1; ++q) {
                         const int st = it % C::STAGES;
                         if (!wait_phase(ctl, &ctl->full[st], (it / C::STAGES) & 1, ERR_MMA)) {
@@ -637,10 +675,12 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
             umma_commit(&ctl->drain);
             wait_phase(ctl, &ctl->drain, 0, ERR_DRAIN, false, 256);
         }
+    }
     } else {
+        if constexpr (C::REG_SPLIT) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(C::REG_HI));
         // ------------------------------------------------------------ epilogue warps
-        const int quarter = warp & 3;          // TMEM lanes (= tile rows) this warp may access
-        const int half = (warp - 2) >> 2;      // which 128 of the tile's BN columns
+        const int quarter = warp & 3;             // TMEM lanes (= tile rows) this warp may access
+        const int half = (warp - C::EPI0) >> 2;  // which 128 of the tile's BN columns
         const int col_base = half * 128;
         int sidx = 0, acc = 0;
         for (;;) {
@@ -652,12 +692,15 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
             if (sl.t < 0) break;
             const TileRef tr{nullptr, sl.mi, sl.ni};
             const UmmaProblem &pb = sl.prob;
-            const int ktot = pb.nseg * pb.kt;
-            const int ck = pb.chunk_kt > 0 ? pb.chunk_kt : (ktot > 0 ? ktot : 1);
-            const int nch = (ktot + ck - 1) / ck;
+            int qa, qb;
+            slice_range(pb, sl.ks, qa, qb);
+            const int ck = pb.chunk_kt > 0 ? pb.chunk_kt : (qb - qa > 0 ? qb - qa : 1);
+            const int nch = (qb - qa + ck - 1) / ck;
             {
                 // bring the values the final epilogue reads (C or D) towards L2
-                // while the tile's MMAs run
+                // while the tile's MMAs run (prefetching the lines it only
+                // writes as well was measured slower: the extra HBM reads cost
+                // more than the write misses they avoid)
                 const EpiParams &pe = pb.epi;
                 const int prow = tr.mi * BM + quarter * 32 + lane;
                 const int pcol = tr.ni * BN + col_base;
@@ -715,10 +758,52 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                 ++acc;
             }
             if (!ok) break;
+            bool last = true;
+            if (!BATCHED && pb.ksplit > 1) {
+                // split-K hand-off: publish this slice's sums, count the arrival;
+                // the last slice to arrive adds all slices in slice order
+                const int ew = warp - C::EPI0;
+                const long long tile = sl.t / pb.ksplit;
+                float *const base = pb.kpart + (size_t)(tile * pb.ksplit) * C::NEPI * 4096 + (size_t)ew * 4096;
+                float *const mine = base + (size_t)sl.ks * C::NEPI * 4096;
+#pragma unroll
+                for (int q = 0; q < 128; q += 4)
+                    *reinterpret_cast<float4 *>(mine + q * 32 + lane * 4) =
+                        make_float4(sum[q], sum[q + 1], sum[q + 2], sum[q + 3]);
+                __threadfence();
+                __syncwarp();
+                int old = 0;
+                if (lane == 0) old = atomicAdd(pb.kcnt + tile * C::NEPI + ew, 1);
+                old = __shfl_sync(0xffffffffu, old, 0);
+                last = old == pb.ksplit - 1;
+                if (last) {
+                    // every slice, this one included, is in kpart: add them in slice order
+                    __threadfence();
+                    const float *src = base + lane * 4;
+#pragma unroll
+                    for (int q = 0; q < 128; q += 4) {
+                        float4 a = __ldcg(reinterpret_cast<const float4 *>(src + q * 32));
+                        for (int k = 1; k < pb.ksplit; ++k) {
+                            const float4 v =
+                                __ldcg(reinterpret_cast<const float4 *>(src + (size_t)k * C::NEPI * 4096 + q * 32));
+                            a.x += v.x;
+                            a.y += v.y;
+                            a.z += v.z;
+                            a.w += v.w;
+                        }
+                        sum[q] = a.x;
+                        sum[q + 1] = a.y;
+                        sum[q + 2] = a.z;
+                        sum[q + 3] = a.w;
+                    }
+                }
+            }
             const int rloc = quarter * 32 + lane;
             const int col0 = tr.ni * BN + col_base;
             const EpiParams &e = pb.epi;
-            if constexpr (EK == EK_PACK) {
+            if (!last) {
+                // another slice of this tile finishes it
+            } else if constexpr (EK == EK_PACK) {
                 // row rloc of M tile mi; column j of the result is k = j of the packed operand
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
@@ -729,7 +814,7 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                         store_chunk<P>(tile0, rloc, (g & 1) * 4 + cc, &sum[g * 32 + cc * 8]);
                 }
             } else {
-                float *sc = scratch + (warp - 2) * 1024;
+                float *sc = scratch + (warp - C::EPI0) * 1024;
                 const int wrow0 = tr.mi * BM + quarter * 32;
                 const bool diag = EK == EK_SYM && tr.mi == tr.ni;
 #pragma unroll
@@ -773,6 +858,22 @@ ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int 
         LN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
+    if constexpr (C::REG_SPLIT) {
+        // setmaxnreg.inc waits until the registers it asks for are free: launch
+        // only if the kernel really got the per-thread count the split assumes
+        static int regs[64] = {0};
+        if (dev < 0 || dev >= 64 || regs[dev] == 0) {
+            cudaFuncAttributes fa{};
+            LN_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+            if (dev >= 0 && dev < 64) regs[dev] = fa.numRegs;
+            if (fa.numRegs != C::REG_LAUNCH)
+                return fail(LN_ERR_UNSUPPORTED, "tcgen05 kernel compiled with %d registers per thread, %d expected",
+                            fa.numRegs, C::REG_LAUNCH);
+        } else if (regs[dev] != C::REG_LAUNCH) {
+            return fail(LN_ERR_UNSUPPORTED, "tcgen05 kernel compiled with %d registers per thread, %d expected",
+                        regs[dev], C::REG_LAUNCH);
+        }
+    }
     const int sms = sm_count();
     const int tile_ctas = total < sms ? total : sms;
     int side_ctas = 0;
@@ -783,7 +884,9 @@ ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int 
             // time model: a 128 x BN x 64 MMA step per product at the SM's share of
             // the BF16 peak (~0.33 us at BN = 256) against ~60 GB/s of split
             // traffic (32 KiB in, 32 KiB out per pack tile) for each spare SM
-            const double mma_us = ceil_div(total, tile_ctas) * (double)single->kt * Products<P>::n * 0.33 * (BN / 256.0);
+            const int ktot = single->nseg * single->kt;
+            const int kslice = single->ksplit > 1 ? (ktot + single->ksplit - 1) / single->ksplit : ktot;
+            const double mma_us = ceil_div(total, tile_ctas) * (double)kslice * Products<P>::n * 0.33 * (BN / 256.0);
             const int free_sms = sms - tile_ctas;
             const double pack_us =
                 free_sms > 0 ? side->prefix[side->count] * 65536.0 / (free_sms * 60e3) : 1e30;

@@ -6,8 +6,13 @@
 namespace ln {
 
 ln_status umma_contract_sym(const UmmaProblem &p, int terms, cudaStream_t st) {
-    const long long tiles = (long long)p.mt * (p.mt + 1) / 2;
+    long long tiles = (long long)p.mt * (p.mt + 1) / 2;
     if (tiles == 0) return LN_SUCCESS;
+    if (p.ksplit > 1) {
+        if (!p.kpart || !p.kcnt) return fail(LN_ERR_INVALID_VALUE, "split-K without its workspace");
+        LN_CUDA_TRY(cudaMemsetAsync(p.kcnt, 0, umma_split_cnt_bytes(tiles, 128), st));
+        tiles *= p.ksplit;
+    }
     if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many output tiles");
     const int total = (int)tiles;
     switch (terms) {

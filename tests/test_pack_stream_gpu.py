@@ -99,3 +99,69 @@ def test_chain_fullsize_side_pack_matches_separate(api):
     for E in (E1, E2):
         assert inputs.rel_fro(host(E)[rows], E_ref) <= 1e-5
     assert inputs.rel_fro(host(F1), host(F2)) <= 2e-6
+
+
+@pytest.mark.parametrize("prec", ["3xbf16", "6xbf16"])
+def test_split_k_graph_replay(api, prec):
+    """Few output tiles and a long reduction: the contraction is split along K
+    (slices hand partial sums to the last arrival through the workspace, with
+    arrival counters zeroed per call), so replaying a captured call repeats
+    the same result bit for bit."""
+    api.set_tuning("split_k", 1)
+    try:
+        _split_k_graph_replay(api, prec)
+    finally:
+        api.set_tuning("split_k", 0)
+
+
+def _split_k_graph_replay(api, prec):
+    A, B = (inputs.int_matrix(s, seed=50 + i) for i, s in enumerate([(1024, 1024), (1024, 1024)]))
+    ref = oracle.gemm(A, B)
+    At, Bt = dev(A), dev(B)
+    C = torch.empty((1024, 1024), device="cuda")
+    api.gemm(At, Bt, C, 1.0, 0.0, prec=prec)  # warm (workspace, attributes)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        api.gemm(At, Bt, C, 1.0, 0.0, prec=prec)
+    for _ in range(3):
+        C.fill_(float("nan"))
+        g.replay()
+        api.stream_check()
+        assert np.array_equal(host(C).astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("prec", ["3xbf16", "6xbf16"])
+def test_split_k_parity(api, prec):
+    """With split-K on: general, chain, symmetric and backward contractions with
+    few output tiles against the oracle (integer inputs: bit for bit)."""
+    api.set_tuning("split_k", 1)
+    try:
+        M, N, K = 300, 260, 2000
+        A, B, C = (inputs.int_matrix(s, seed=60 + i) for i, s in enumerate([(M, K), (K, N), (M, N)]))
+        Ct = dev(C)
+        api.gemm(dev(A), dev(B), Ct, 2.0, -1.0, prec=prec)
+        assert np.array_equal(host(Ct).astype(np.float64), oracle.gemm(A, B, C, 2.0, -1.0))
+        ni, nj, nk, nl = 200, 136, 1000, 92
+        A, B, Cc, D = (inputs.int_matrix(s, seed=70 + i) for i, s in enumerate([(ni, nk), (nk, nj), (nj, nl), (ni, nl)]))
+        E_ref, F_ref = oracle.gemm_chain(A, B, Cc, D, 2.0, -1.0)
+        E, F = api.gemm_chain(dev(A), dev(B), dev(Cc), dev(D), 2.0, -1.0, prec=prec)
+        assert np.array_equal(host(E).astype(np.float64), E_ref)
+        assert np.array_equal(host(F).astype(np.float64), F_ref)
+        n, k = 260, 1500
+        A, Cs = inputs.int_matrix((n, k), seed=80), inputs.int_matrix((n, n), seed=81)
+        Cs = (Cs + Cs.T).astype(np.float32)
+        Ct = dev(Cs)
+        api.syrk(dev(A), Ct, 2.0, -1.0, prec=prec)
+        assert np.array_equal(host(Ct).astype(np.float64), oracle.syrk(A, Cs, 2.0, -1.0))
+        d = inputs.backward_inputs(256, 16, 1024, seed=3)
+        t = {k: dev(d[k]) for k in ("A", "B", "C")}
+        G = dev(d["A"])
+        dA, dB, dC = api.gemm_chain_bwd(t["A"], t["B"], t["C"], G, prec=prec)
+        rA, rB, rC = oracle.gemm_chain_vjp(d["A"], d["B"], d["C"], d["A"])
+        for got, ref in ((dA, rA), (dB, rB), (dC, rC)):
+            assert inputs.rel_fro(host(got), ref) <= 1e-5
+        api.stream_check()
+    finally:
+        api.set_tuning("split_k", 0)
