@@ -52,10 +52,10 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &t) {
 // Each thread keeps its running sums as unevaluated FP32 pairs (hi + lo, hi
 // accumulating with error-free sums whose errors gather in lo). In pass 1 the
 // FP64 mean is split as mh + ml (two floats); the deviation from mh,
-// d = x - mh, is formed exactly as a pair and the thread accumulates S1 = sum d
-// and S2 = sum d^2 (squares carry their exact FMA residual). Its share of the
-// squared deviations from the FP64 mean then follows in FP64 as
-// S2 - 2 ml S1 + cnt ml^2, so ml never enters a product of small numbers.
+// d = x - mh, is formed exactly as a pair (dh, dl) and the thread accumulates
+// sum d^2 (the square of the pair, carrying its exact FMA residual). Because
+// the deviations from the mean sum to zero, sum (x - mean)^2 =
+// sum (x - mh)^2 - n ml^2; the final kernel subtracts n ml^2 once per column.
 // The pairs are widened to FP64 for the combination across threads and
 // blocks. GB300 issues FP64 at a small fraction of its FP32 rate, so native
 // FP64 per element made this bandwidth-bound pass compute-bound; the pairs
@@ -69,55 +69,36 @@ __global__ __launch_bounds__(256) void k_col_partial(int n, int m, const float *
     const int r0 = blockIdx.y * sr;
     const bool vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && ((ldx & 3) == 0);
     float mh[4] = {0, 0, 0, 0};
-    double ml[4] = {0, 0, 0, 0};
     if (PASS == 1) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const double mu = (c + q < m) ? mean[c + q] : 0.0;
-            mh[q] = (float)mu;
-            ml[q] = mu - (double)mh[q];
-        }
+        for (int q = 0; q < 4; ++q) mh[q] = (c + q < m) ? (float)mean[c + q] : 0.0f;
     }
-    float h1[4] = {0, 0, 0, 0}, l1[4] = {0, 0, 0, 0};  // sum x (pass 0) or sum d (pass 1)
-    float h2[4] = {0, 0, 0, 0}, l2[4] = {0, 0, 0, 0};  // sum d^2 (pass 1)
-    int cnt = 0;
+    float h[4] = {0, 0, 0, 0}, l[4] = {0, 0, 0, 0};  // sum x (pass 0) or sum d^2 (pass 1)
     const int r1 = min(n, r0 + sr);
-#pragma unroll 4
+#pragma unroll 8
     for (int r = r0 + ry; r < r1; r += 8) {
         float4 v = ld4_guard(X + (long long)r * ldx, c, m, vec);
         float x[4] = {v.x, v.y, v.z, v.w};
-        ++cnt;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             float s, t;
             if (PASS == 0) {
-                two_sum(h1[q], x[q], s, t);
-                h1[q] = s;
-                l1[q] += t;
+                two_sum(h[q], x[q], s, t);
+                h[q] = s;
+                l[q] += t;
             } else {
                 float dh, dl;
                 two_sum(x[q], -mh[q], dh, dl);
-                two_sum(h1[q], dh, s, t);
-                h1[q] = s;
-                l1[q] += t + dl;
                 const float p = dh * dh;
                 const float pe = fmaf(dh, dh, -p) + (2.0f * dh + dl) * dl;
-                two_sum(h2[q], p, s, t);
-                h2[q] = s;
-                l2[q] += t + pe;
+                two_sum(h[q], p, s, t);
+                h[q] = s;
+                l[q] += t + pe;
             }
         }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const double s1 = (double)h1[q] + (double)l1[q];
-        if (PASS == 0) {
-            red[ry][cx * 4 + q] = s1;
-        } else {
-            const double s2 = (double)h2[q] + (double)l2[q];
-            red[ry][cx * 4 + q] = s2 - 2.0 * ml[q] * s1 + (double)cnt * ml[q] * ml[q];
-        }
-    }
+    for (int q = 0; q < 4; ++q) red[ry][cx * 4 + q] = (double)h[q] + (double)l[q];
     __syncthreads();
     if (threadIdx.x < SC) {
         int col = blockIdx.x * SC + threadIdx.x;
@@ -128,13 +109,40 @@ __global__ __launch_bounds__(256) void k_col_partial(int n, int m, const float *
     }
 }
 
+// Sum of each column's chunk partials, 8 threads per column (strided over the
+// chunks, coalesced across columns) combined in a fixed order. PASS 0 writes
+// the mean; PASS 1 writes the sum of squared deviations and, on request, the
+// centring pair (hi + lo = mean) and 1/sqrt(ss) (0 for a zero-variance column).
 template <int PASS>
-__global__ void k_col_final(int n, int m, int nchunks, const double *__restrict__ partials, double *out) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
+__global__ __launch_bounds__(256) void k_col_final(int n, int m, int nchunks, const double *__restrict__ partials,
+                                                   const double *__restrict__ mean, double *out, float *off_hi,
+                                                   float *off_lo, float *rs) {
+    __shared__ double red[8][32];
+    const int cx = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + cx;
     double s = 0.0;
-    for (int ch = 0; ch < nchunks; ++ch) s += partials[(long long)ch * m + j];
-    out[j] = (PASS == 0) ? s / (double)n : s;
+    if (j < m)
+        for (int ch = g; ch < nchunks; ch += 8) s += partials[(long long)ch * m + j];
+    red[g][cx] = s;
+    __syncthreads();
+    if (g != 0 || j >= m) return;
+#pragma unroll
+    for (int k = 1; k < 8; ++k) s += red[k][cx];
+    if (PASS == 0) {
+        out[j] = s / (double)n;
+        return;
+    }
+    const double mu = mean[j];
+    const float h = (float)mu;
+    const double ml = mu - (double)h;
+    double q = s - (double)n * ml * ml;
+    if (q < 0.0) q = 0.0;
+    out[j] = q;
+    if (off_hi) {
+        off_hi[j] = h;
+        off_lo[j] = (float)ml;
+    }
+    if (rs) rs[j] = (q > 0.0) ? (float)(1.0 / sqrt(q)) : 0.0f;
 }
 
 __global__ void k_derive(int m, const double *__restrict__ mean, const double *__restrict__ ss, float *off_hi,
@@ -355,13 +363,16 @@ ln_status col_stats(int n, int m, const float *X, long long ldx, double *mean, d
     const int sr = stats_rows(n, m);
     const int nch = (int)ceil_div(n, sr);
     dim3 grid((unsigned)ceil_div(m, SC), (unsigned)nch);
+    const unsigned gf = (unsigned)ceil_div(m, 32);
     { LaunchScope ls_(FAM_STATS, st); k_col_partial<0><<<grid, 256, 0, st>>>(n, m, X, ldx, nullptr, partials, sr); }
-    { LaunchScope ls_(FAM_STATS, st); k_col_final<0><<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(n, m, nch, partials, mean); }
-    { LaunchScope ls_(FAM_STATS, st); k_col_partial<1><<<grid, 256, 0, st>>>(n, m, X, ldx, mean, partials, sr); }
-    { LaunchScope ls_(FAM_STATS, st); k_col_final<1><<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(n, m, nch, partials, ss); }
-    if (off_hi || rs) {
+    {
         LaunchScope ls_(FAM_STATS, st);
-        k_derive<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(m, mean, ss, off_hi, off_lo, rs);
+        k_col_final<0><<<gf, 256, 0, st>>>(n, m, nch, partials, nullptr, mean, nullptr, nullptr, nullptr);
+    }
+    { LaunchScope ls_(FAM_STATS, st); k_col_partial<1><<<grid, 256, 0, st>>>(n, m, X, ldx, mean, partials, sr); }
+    {
+        LaunchScope ls_(FAM_STATS, st);
+        k_col_final<1><<<gf, 256, 0, st>>>(n, m, nch, partials, mean, ss, off_hi, off_lo, rs);
     }
     return check_launch("column statistics");
 }
