@@ -46,7 +46,9 @@ size_t umma_split_part_bytes(long long tiles, int ksplit, int bn) {
     return ksplit > 1 ? (size_t)tiles * ksplit * (bn / 32) * 4096 * sizeof(float) : 0;
 }
 
-size_t umma_split_cnt_bytes(long long tiles, int bn) { return (size_t)tiles * (bn / 32) * sizeof(int); }
+// one counter per (tile, epilogue warp); every configuration has at most 8
+// epilogue warps (Cfg::NEPI)
+size_t umma_split_cnt_bytes(long long tiles, int) { return (size_t)tiles * 8 * sizeof(int); }
 
 ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st, const PackMulti *side, bool *side_done) {
     if (side_done) *side_done = false;

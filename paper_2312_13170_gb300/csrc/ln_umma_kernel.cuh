@@ -237,17 +237,19 @@ struct Products<3> {  // the six products of order >= 2^-16
 //  shared memory per stage: A (P x 16 KiB) + B (P x BN/128 x 16 KiB), B term q
 //  at q * BN/128 * 16 KiB with its two 128-row halves 16 KiB apart;
 //  TMEM: NACC = 512 / BN accumulator buffers of BN columns.
-template <int P, int BN>
+// EPW: columns per epilogue warp (128, or 64 for symmetric outputs, whose
+// element-wise epilogue is latency-bound and gains from twice the warps).
+template <int P, int BN, int EPW = 128>
 struct Cfg {
-    static constexpr int NEPI = BN / 32;  // epilogue warps: 4 per 128 columns
-    // first epilogue warp: BN = 256 gives the epilogue two whole warpgroups
+    static constexpr int NEPI = 4 * BN / EPW;  // epilogue warps: 4 (one per TMEM lane quarter) per EPW columns
+    // first epilogue warp: eight epilogue warps make two whole warpgroups
     // (warpgroup 0 = producer, MMA issuer and two idle warps), so that
-    // setmaxnreg can move registers from warpgroup 0 to the epilogue, whose
-    // 128 running sums per thread do not fit in the 168 registers a thread of
-    // a 12-warp CTA gets at launch
-    static constexpr int EPI0 = BN == 256 ? 4 : 2;
+    // setmaxnreg can move registers from warpgroup 0 to the epilogue, which
+    // does not fit in the 168 registers a thread of a 12-warp CTA gets at
+    // launch
+    static constexpr int EPI0 = NEPI == 8 ? 4 : 2;
     static constexpr int NTHREADS = 32 * (EPI0 + NEPI);
-    static constexpr bool REG_SPLIT = BN == 256;
+    static constexpr bool REG_SPLIT = NEPI == 8;
     static constexpr int REG_LAUNCH = ((65536 / NTHREADS) & ~7) > 255 ? 255 : ((65536 / NTHREADS) & ~7);
     static constexpr int REG_LO = 64;
     static constexpr int REG_HI = ((REG_LAUNCH * NTHREADS - 128 * REG_LO) / (32 * NEPI)) & ~7;
@@ -261,7 +263,8 @@ struct Cfg {
     static constexpr int STAGES_RAW = (SMEM_BUDGET - 1024 - CTL_BYTES - SCRATCH_BYTES) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_RAW > MAX_STAGES ? MAX_STAGES : STAGES_RAW;
     static constexpr int SMEM = 1024 + CTL_BYTES + STAGES * STAGE_BYTES + SCRATCH_BYTES;
-    static constexpr int NLD = BN == 128 ? 4 : 2;  // tcgen05.ld (x16) in flight per wait
+    static constexpr int NLD = (BN == 128 && EPW == 128) ? 4 : 2;  // tcgen05.ld (x16) in flight per wait
+    static_assert((EPW == 64 || EPW == 128) && NEPI <= 8, "epilogue width");
     static_assert(NACC <= MAX_NACC && STAGES >= 2, "tile configuration does not fit");
     static_assert(!REG_SPLIT || (128 * REG_LO + 32 * NEPI * REG_HI <= REG_LAUNCH * NTHREADS && REG_HI <= 256 &&
                                  NTHREADS == 128 + 32 * NEPI),
@@ -489,14 +492,18 @@ __device__ __forceinline__ bool block_epilogue(const EpiParams &e, float *sc, in
 // queue); CTAs from tile_ctas on (only launched for single problems with the
 // packing epilogue, see Cfg::SIDE_OK) run the pack stream over `side`, the
 // operand of the next contraction, on SMs that have no output tile.
+template <int EK>
+constexpr int epi_width() { return EK == EK_SYM ? 64 : 128; }
+
 template <int P, int BN, int BATCHED, int EK>
-__global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_constant__ UmmaProblem single,
+__global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_umma(const __grid_constant__ UmmaProblem single,
                                                                   const UmmaProblem *__restrict__ probs,
                                                                   const int *__restrict__ prefix,
                                                                   const int *__restrict__ owner, int total_tiles,
                                                                   int *queue, const __grid_constant__ PackMulti side,
                                                                   int tile_ctas) {
-    using C = Cfg<P, BN>;
+    using C = Cfg<P, BN, epi_width<EK>()>;
+    constexpr int EPW = epi_width<EK>();
     using PR = Products<P>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment of the stage area is required by the 128-byte swizzle.
@@ -680,8 +687,8 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
         if constexpr (C::REG_SPLIT) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(C::REG_HI));
         // ------------------------------------------------------------ epilogue warps
         const int quarter = warp & 3;             // TMEM lanes (= tile rows) this warp may access
-        const int half = (warp - C::EPI0) >> 2;  // which 128 of the tile's BN columns
-        const int col_base = half * 128;
+        const int half = (warp - C::EPI0) >> 2;  // which EPW of the tile's BN columns
+        const int col_base = half * EPW;
         int sidx = 0, acc = 0;
         for (;;) {
             const int s = sidx % SCHED;
@@ -708,28 +715,28 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                     if (pe.mode == EPI_GEMM || (pe.mode == EPI_SYM && pe.sym_kind == SYM_AXPBY && pe.fill != LN_FILL_UPPER)) {
                         const float *r0 = pe.C + (long long)prow * pe.ldc + pcol;
 #pragma unroll
-                        for (int q = 0; q < 128; q += 32)
+                        for (int q = 0; q < EPW; q += 32)
                             if (pcol + q < pe.N) prefetch_l2(r0 + q);
                     } else if (pe.mode == EPI_EF) {
                         const float *r0 = pe.D + (long long)prow * pe.ld_ef + pcol;
 #pragma unroll
-                        for (int q = 0; q < 128; q += 32)
+                        for (int q = 0; q < EPW; q += 32)
                             if (pcol + q < pe.N) prefetch_l2(r0 + q);
                     } else if (pe.mode == EPI_SYM && pe.sym_kind == SYM_AXPBY) {
                         const int wrow = tr.mi * BM + quarter * 32;  // the warp's first row (< M here)
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int j = pcol + lane * 4 + q;
+                        for (int q = 0; q < EPW / 32; ++q) {
+                            const int j = pcol + lane * (EPW / 32) + q;
                             if (j < pe.N) prefetch_l2(pe.C + (long long)j * pe.ldc + wrow);
                         }
                     }
                 }
             }
-            // running FP32 sum of this thread's 128 outputs: each TMEM chunk is
+            // running FP32 sum of this thread's EPW outputs: each TMEM chunk is
             // added here with round-to-nearest adds
-            float sum[128];
+            float sum[EPW];
 #pragma unroll
-            for (int q = 0; q < 128; ++q) sum[q] = 0.0f;
+            for (int q = 0; q < EPW; ++q) sum[q] = 0.0f;
             for (int c = 0; c < nch && ok; ++c) {
                 const int b = acc % C::NACC;
                 ok = wait_phase(ctl, &ctl->tfull[b], (acc / C::NACC) & 1, ERR_EPILOGUE, true, 128);
@@ -737,7 +744,7 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                 if (!ok) break;
                 tc_fence_after();
 #pragma unroll
-                for (int g0 = 0; g0 < 8; g0 += C::NLD) {
+                for (int g0 = 0; g0 < EPW / 16; g0 += C::NLD) {
                     uint32_t r[C::NLD][16];
 #pragma unroll
                     for (int j = 0; j < C::NLD; ++j)
@@ -764,10 +771,11 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                 // the last slice to arrive adds all slices in slice order
                 const int ew = warp - C::EPI0;
                 const long long tile = sl.t / pb.ksplit;
-                float *const base = pb.kpart + (size_t)(tile * pb.ksplit) * C::NEPI * 4096 + (size_t)ew * 4096;
-                float *const mine = base + (size_t)sl.ks * C::NEPI * 4096;
+                constexpr int SLAB = EPW * 32;  // one warp's partial sums
+                float *const base = pb.kpart + (size_t)(tile * pb.ksplit) * C::NEPI * SLAB + (size_t)ew * SLAB;
+                float *const mine = base + (size_t)sl.ks * C::NEPI * SLAB;
 #pragma unroll
-                for (int q = 0; q < 128; q += 4)
+                for (int q = 0; q < EPW; q += 4)
                     *reinterpret_cast<float4 *>(mine + q * 32 + lane * 4) =
                         make_float4(sum[q], sum[q + 1], sum[q + 2], sum[q + 3]);
                 __threadfence();
@@ -781,11 +789,11 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                     __threadfence();
                     const float *src = base + lane * 4;
 #pragma unroll
-                    for (int q = 0; q < 128; q += 4) {
+                    for (int q = 0; q < EPW; q += 4) {
                         float4 a = __ldcg(reinterpret_cast<const float4 *>(src + q * 32));
                         for (int k = 1; k < pb.ksplit; ++k) {
                             const float4 v =
-                                __ldcg(reinterpret_cast<const float4 *>(src + (size_t)k * C::NEPI * 4096 + q * 32));
+                                __ldcg(reinterpret_cast<const float4 *>(src + (size_t)k * C::NEPI * SLAB + q * 32));
                             a.x += v.x;
                             a.y += v.y;
                             a.z += v.z;
@@ -806,7 +814,7 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
             } else if constexpr (EK == EK_PACK) {
                 // row rloc of M tile mi; column j of the result is k = j of the packed operand
 #pragma unroll
-                for (int g = 0; g < 4; ++g) {
+                for (int g = 0; g < EPW / 32; ++g) {
                     const int kt = (col0 + g * 32) / PK_K;
                     char *tile0 = e.pack + (size_t)((long long)tr.mi * e.pack_kt + kt) * P * PK_TILE_BYTES;
 #pragma unroll
@@ -818,7 +826,7 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
                 const int wrow0 = tr.mi * BM + quarter * 32;
                 const bool diag = EK == EK_SYM && tr.mi == tr.ni;
 #pragma unroll
-                for (int g = 0; g < 4; ++g) {
+                for (int g = 0; g < EPW / 32; ++g) {
                     if constexpr (EK == EK_SYM) {
                         epi_sym32(e, wrow0 + lane, col0 + g * 32, &sum[g * 32], diag);
                     } else {
@@ -847,7 +855,7 @@ __global__ __launch_bounds__(Cfg<P, BN>::NTHREADS, 1) void k_umma(const __grid_c
 template <int P, int BN, int BATCHED, int EK>
 ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int *prefix, const int *owner, int total,
                  int *queue, cudaStream_t st, const PackMulti *side = nullptr, bool *side_done = nullptr) {
-    using C = Cfg<P, BN>;
+    using C = Cfg<P, BN, epi_width<EK>()>;
     auto kern = k_umma<P, BN, BATCHED, EK>;
     // the shared-memory opt-in is set once per device (so nothing but launches
     // happens while a caller captures a graph)
