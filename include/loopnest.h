@@ -162,6 +162,13 @@ ln_status ln_gemm(int M, int N, int K, float alpha, const float *A, int lda, con
  * (ld = columns). T lives in the workspace (FP32 for FP32 forms; as packed
  * BF16 split terms for tensor-core forms), so every form needs a workspace.
  * D may be NULL when beta == 0. E and F must not overlap each other or inputs.
+ * A, B, C, D, E and F may be device memory or host memory the GPU can reach:
+ * pinned (page-locked or registered) host buffers are read and written by the
+ * kernels through their device mapping, over the host link, without staging
+ * copies; pageable host memory is accepted only where the device reports
+ * coherent pageable access (cudaDevAttrPageableMemoryAccess), otherwise the
+ * call returns LN_ERR_INVALID_VALUE before launching anything. The workspace
+ * must be device memory.
  */
 ln_status ln_gemm_chain_workspace_size(int ni, int nj, int nk, int nl, ln_form form, ln_precision prec,
                                        size_t *bytes /*host*/);

@@ -125,9 +125,11 @@ def _enum(table, v, what):
         raise ValueError(f"unknown {what} {v!r}; expected one of {sorted(table)}") from None
 
 
-def _f32(t, name):
-    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda:
-        raise TypeError(f"{name} must be a float32 CUDA tensor")
+def _f32(t, name, host_ok=False):
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32:
+        raise TypeError(f"{name} must be a float32 tensor")
+    if not t.is_cuda and not (host_ok and t.is_pinned()):
+        raise TypeError(f"{name} must be a CUDA tensor" + (" or a pinned host tensor" if host_ok else ""))
     if t.dim() != 2 or t.stride(1) != 1:
         raise ValueError(f"{name} must be a 2-D row-major tensor (unit column stride)")
     return t
@@ -208,9 +210,13 @@ def gemm(A, B, C, alpha=1.0, beta=0.0, form="internalized", prec="3xbf16", strea
 
 
 def gemm_chain(A, B, C, D=None, alpha=1.0, beta=0.0, form="internalized", prec="3xbf16", stream=None, out=None):
-    """E = (A@B)@C, F = alpha*E + beta*D. Returns (E, F)."""
+    """E = (A@B)@C, F = alpha*E + beta*D. Returns (E, F).
+
+    Operands and outputs may be pinned host tensors: the kernels then read and
+    write them in host memory directly (no staging copies); new outputs follow
+    A's placement. The workspace is always on the current GPU."""
     for t, nme in ((A, "A"), (B, "B"), (C, "C")):
-        _f32(t, nme)
+        _f32(t, nme, host_ok=True)
         if not t.is_contiguous():
             raise ValueError(f"{nme} must be contiguous")
     ni, nk = A.shape
@@ -218,17 +224,20 @@ def gemm_chain(A, B, C, D=None, alpha=1.0, beta=0.0, form="internalized", prec="
     if B.shape[0] != nk or C.shape[0] != nj:
         raise ValueError("shape mismatch")
     if D is not None:
-        _f32(D, "D")
+        _f32(D, "D", host_ok=True)
         if tuple(D.shape) != (ni, nl) or not D.is_contiguous():
             raise ValueError("D must be contiguous ni x nl")
     fm, pr = _enum(FORMS, form, "form"), _enum(PRECS, prec, "precision")
     if out is None:
-        E = torch.empty((ni, nl), dtype=torch.float32, device=A.device)
-        F = torch.empty((ni, nl), dtype=torch.float32, device=A.device)
+        pin = not A.is_cuda
+        E = torch.empty((ni, nl), dtype=torch.float32, device=A.device, pin_memory=pin)
+        F = torch.empty((ni, nl), dtype=torch.float32, device=A.device, pin_memory=pin)
     else:
         E, F = out
+        _f32(E, "E", host_ok=True), _f32(F, "F", host_ok=True)
+    dev = A.device if A.is_cuda else torch.device("cuda", torch.cuda.current_device())
     _autotune("gemm_chain", (ni, nj, nk, nl), prec)
-    ws, nb = _workspace(_ws_query("ln_gemm_chain_workspace_size", ni, nj, nk, nl, fm, pr), A.device)
+    ws, nb = _workspace(_ws_query("ln_gemm_chain_workspace_size", ni, nj, nk, nl, fm, pr), dev)
     _check(lib().ln_gemm_chain(ni, nj, nk, nl, alpha, _ptr(A), _ptr(B), _ptr(C), beta, _ptr(D), _ptr(E), _ptr(F),
                                _ptr(ws), nb, fm, pr, _stream(stream)), "ln_gemm_chain")
     return E, F

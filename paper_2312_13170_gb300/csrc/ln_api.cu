@@ -167,6 +167,40 @@ void apply_split(UmmaProblem &pb, const SplitPlan &sp) {
     pb.kcnt = sp.cnt;
 }
 
+// ------------------------------------------------------------------ host-resident operands
+// The address kernels use for `p`: device and managed memory as is; pinned
+// (page-locked or registered) host memory through its device mapping (read
+// and written by the kernels over the host link, no staging copy); pageable
+// host memory only where the GPU reports coherent pageable access (e.g.
+// NVLink-C2C systems), else LN_ERR_INVALID_VALUE before anything is launched.
+template <class T>
+ln_status device_view(T *p, T **out, const char *name) {
+    *out = p;
+    if (!p) return LN_SUCCESS;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LN_ERR_INVALID_VALUE, "%s: not a pointer this process can use", name);
+    }
+    switch (a.type) {
+        case cudaMemoryTypeDevice:
+        case cudaMemoryTypeManaged: return LN_SUCCESS;
+        case cudaMemoryTypeHost:
+            if (!a.devicePointer) return fail(LN_ERR_INVALID_VALUE, "%s: pinned host buffer without a device mapping", name);
+            *out = static_cast<T *>(a.devicePointer);
+            return LN_SUCCESS;
+        default: {
+            int dev = 0, pageable = 0;
+            LN_CUDA_TRY(cudaGetDevice(&dev));
+            LN_CUDA_TRY(cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev));
+            if (!pageable)
+                return fail(LN_ERR_INVALID_VALUE, "%s: pageable host memory is not accessible from this GPU (pin it)",
+                            name);
+            return LN_SUCCESS;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ validation helpers
 struct Span {
     const void *p;
@@ -915,6 +949,13 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
     if (overlap(se, sf)) return fail(LN_ERR_ALIASING, "E overlaps F");
     for (const Span &s : ins)
         if (overlap(se, s) || overlap(sf, s)) return fail(LN_ERR_ALIASING, "E or F overlaps an input");
+    // operands may live in host memory the GPU can reach (see device_view)
+    LN_TRY(device_view(A, &A, "A"));
+    LN_TRY(device_view(B, &B, "B"));
+    LN_TRY(device_view(C, &C, "C"));
+    LN_TRY(device_view(D, &D, "D"));
+    LN_TRY(device_view(E, &E, "E"));
+    LN_TRY(device_view(F, &F, "F"));
     cudaStream_t st = S(stream);
     EpiParams ef{};
     ef.mode = EPI_EF;

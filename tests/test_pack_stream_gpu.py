@@ -165,3 +165,23 @@ def test_split_k_parity(api, prec):
         api.stream_check()
     finally:
         api.set_tuning("split_k", 0)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "3xbf16"])
+def test_chain_host_resident_operands(api, prec):
+    """Pinned host operands and outputs: the kernels read A..D and write E, F in
+    host memory directly; the result equals the device-resident call bit for
+    bit, and pageable host tensors are refused by the binding."""
+    form = "internalized"
+    d = inputs.chain_inputs(520, 264, 300, 392, seed=9)
+    host = {k: torch.from_numpy(d[k]).pin_memory() for k in "ABCD"}
+    devt = {k: v.cuda() for k, v in host.items()}
+    E, F = api.gemm_chain(devt["A"], devt["B"], devt["C"], devt["D"], d["alpha"], d["beta"], form=form, prec=prec)
+    hE = torch.empty(E.shape).pin_memory()
+    hF = torch.empty(E.shape).pin_memory()
+    api.gemm_chain(host["A"], host["B"], host["C"], host["D"], d["alpha"], d["beta"], form=form, prec=prec,
+                   out=(hE, hF))
+    api.stream_check()
+    assert torch.equal(hE, E.cpu()) and torch.equal(hF, F.cpu())
+    with pytest.raises(TypeError):
+        api.gemm_chain(torch.from_numpy(d["A"]), host["B"], host["C"], host["D"], 1.0, 1.0, prec=prec)
