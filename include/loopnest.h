@@ -129,8 +129,10 @@ ln_status ln_timing_read(const char *family, double *total_ms /*host*/, int *lau
  *   "chunk_kt" 1 or 2 (default 2): k tiles of 64 accumulated in tensor memory
  *              before the partial sum is added to an FP32 running sum; 1 is
  *              more accurate, 2 faster;
- *   "tile_n"   128 or 256 (default 256): output tile width of general
- *              (non-symmetric) contractions with one or two split terms;
+ *   "tile_n"   0, 128 or 256 (default 0 = automatic: 256, or 128 when
+ *              256-wide tiles would fill at most half the SMs): output tile
+ *              width of general (non-symmetric) contractions with one or two
+ *              split terms;
  *   "pack_threads" 512 or 1024 (default 512): threads per CTA of the
  *              split-and-pack stream;
  *   "split_k"  0 or 1 (default 0): split the K range of tensor-core

@@ -9,7 +9,7 @@ JSON file keyed by GPU. The Python binding applies a cached choice before each
 call (``LN_AUTOTUNE=cached``) and may search on a miss (``LN_AUTOTUNE=search``);
 ``LN_AUTOTUNE=off`` (the default) leaves the library's defaults in place.
 
-Knobs (see ``ln_set_tuning`` in include/loopnest.h): ``tile_n`` in {128, 256}
+Knobs (see ``ln_set_tuning`` in include/loopnest.h): ``tile_n`` in {0 (automatic), 128, 256}
 for general contractions, ``chunk_kt`` in {1, 2} (k tiles accumulated in
 tensor memory before promotion to FP32 registers). Only configurations that
 keep the library's accuracy gate are offered.
@@ -23,15 +23,19 @@ import math
 import os
 import threading
 
+# tile_n 0 is the library's automatic width (256, or 128 for problems whose
+# 256-wide tiles would fill at most half the SMs)
 CANDIDATES = {
-    "gemm": [{"tile_n": 256, "chunk_kt": 2}, {"tile_n": 128, "chunk_kt": 2}, {"tile_n": 256, "chunk_kt": 1}],
-    "gemm_chain": [{"tile_n": 256, "chunk_kt": 2}, {"tile_n": 128, "chunk_kt": 2}, {"tile_n": 256, "chunk_kt": 1}],
-    "covariance": [{"tile_n": 256, "chunk_kt": 2}, {"tile_n": 256, "chunk_kt": 1}],
-    "correlation": [{"tile_n": 256, "chunk_kt": 2}, {"tile_n": 256, "chunk_kt": 1}],
-    "syrk": [{"tile_n": 256, "chunk_kt": 2}, {"tile_n": 256, "chunk_kt": 1}],
-    "syr2k": [{"tile_n": 256, "chunk_kt": 2}, {"tile_n": 256, "chunk_kt": 1}],
+    "gemm": [{"tile_n": 0, "chunk_kt": 2}, {"tile_n": 256, "chunk_kt": 2}, {"tile_n": 128, "chunk_kt": 2},
+             {"tile_n": 0, "chunk_kt": 1}],
+    "gemm_chain": [{"tile_n": 0, "chunk_kt": 2}, {"tile_n": 256, "chunk_kt": 2}, {"tile_n": 128, "chunk_kt": 2},
+                   {"tile_n": 0, "chunk_kt": 1}],
+    "covariance": [{"tile_n": 0, "chunk_kt": 2}, {"tile_n": 0, "chunk_kt": 1}],
+    "correlation": [{"tile_n": 0, "chunk_kt": 2}, {"tile_n": 0, "chunk_kt": 1}],
+    "syrk": [{"tile_n": 0, "chunk_kt": 2}, {"tile_n": 0, "chunk_kt": 1}],
+    "syr2k": [{"tile_n": 0, "chunk_kt": 2}, {"tile_n": 0, "chunk_kt": 1}],
 }
-DEFAULT = {"tile_n": 256, "chunk_kt": 2}
+DEFAULT = {"tile_n": 0, "chunk_kt": 2}
 _lock = threading.Lock()
 _cache = None
 _state = threading.local()  # set while a search runs, so its own calls are not re-tuned

@@ -76,7 +76,7 @@ LaunchScope::~LaunchScope() {
 // ------------------------------------------------------------------ tuning knobs
 namespace {
 std::atomic<int> g_chunk_kt{2};
-std::atomic<int> g_tile_n{256};
+std::atomic<int> g_tile_n{0};
 std::atomic<int> g_pack_threads{512};
 std::atomic<int> g_split_k{0};
 }  // namespace
@@ -145,9 +145,9 @@ void plan_split(Ws &w, long long tiles, int ktot, int bn, SplitPlan &sp) {
 
 // dims: (M, N, K) of general contractions
 void plan_split_area(Ws &w, const int (*dims)[3], int nd, int P, SplitArea &a) {
-    const int bn = umma_tile_n(P, 0);
     size_t pbytes = 0, cbytes = 0;
     for (int i = 0; i < nd; ++i) {
+        const int bn = umma_tile_n(P, 0, dims[i][0], dims[i][1]);
         const long long tiles = ceil_div(dims[i][0], PK_ROWS) * ceil_div(dims[i][1], bn);
         const int ks = umma_ksplit(tiles, (int)ceil_div(dims[i][2], PK_K));
         if (ks > 1) {
@@ -267,12 +267,13 @@ struct Operand {
 // packed N-side operand holds yrt = nt * width/128 row tiles (zero padded).
 struct ContractPlan {
     char *px = nullptr, *py = nullptr;
-    int mt = 0, nt = 0, kt = 0, yrt = 0;
+    int mt = 0, nt = 0, kt = 0, yrt = 0, bn = 256;
     SplitPlan split;
 };
 
 void contract_geometry(int M, int N, int K, int P, ContractPlan &cp) {
-    const int bn = umma_tile_n(P, 0);
+    const int bn = umma_tile_n(P, 0, M, N);
+    cp.bn = bn;
     cp.mt = (int)ceil_div(M, PK_ROWS);
     cp.nt = (int)ceil_div(N, bn);
     cp.kt = (int)ceil_div(K, PK_K);
@@ -289,7 +290,7 @@ void plan_contract(Ws &w, int M, int N, int K, ln_form form, ln_precision prec, 
     contract_geometry(M, N, K, P, cp);
     cp.px = w.take<char>(packed_bytes(cp.mt, cp.kt, P));
     cp.py = w.take<char>(packed_bytes(cp.yrt, cp.kt, P));
-    plan_split(w, (long long)cp.mt * cp.nt, cp.kt, umma_tile_n(P, 0), cp.split);
+    plan_split(w, (long long)cp.mt * cp.nt, cp.kt, cp.bn, cp.split);
 }
 
 ln_status run_contract(int M, int N, int K, Operand a, Operand b, const EpiParams &epi, ln_form form,
@@ -327,6 +328,7 @@ ln_status run_contract(int M, int N, int K, Operand a, Operand b, const EpiParam
     pb.chunk_kt = tune_chunk_kt();
     pb.inject_timeout = inject_timeout_requested();
     apply_split(pb, cp.split);
+    pb.bn = cp.bn;
     pb.epi = epi;
     return umma_contract(pb, P, st);
 }
@@ -374,8 +376,8 @@ void plan_chain(Ws &w, int ni, int nj, int nk, int nl, ln_form form, ln_precisio
     p.pb = w.take<char>(packed_bytes(p.g1.yrt, p.g1.kt, P));
     p.pt = w.take<char>(packed_bytes(p.g1.mt, p.ktT, P));
     p.pc = w.take<char>(packed_bytes(p.g2.yrt, p.g2.kt, P));
-    plan_split(w, (long long)p.g1.mt * p.g1.nt, p.g1.kt, umma_tile_n(P, 0), p.s1);
-    plan_split(w, (long long)p.g2.mt * p.g2.nt, p.g2.kt, umma_tile_n(P, 0), p.s2);
+    plan_split(w, (long long)p.g1.mt * p.g1.nt, p.g1.kt, p.g1.bn, p.s1);
+    plan_split(w, (long long)p.g2.mt * p.g2.nt, p.g2.kt, p.g2.bn, p.s2);
 }
 
 // ------------------------------------------------------------------ covariance / correlation
@@ -817,7 +819,8 @@ ln_status ln_set_tuning(const char *key, int value) {
         return LN_SUCCESS;
     }
     if (strcmp(key, "tile_n") == 0) {
-        if (value != 128 && value != 256) return fail(LN_ERR_INVALID_VALUE, "tile_n must be 128 or 256 (got %d)", value);
+        if (value != 0 && value != 128 && value != 256)
+            return fail(LN_ERR_INVALID_VALUE, "tile_n must be 0 (automatic), 128 or 256 (got %d)", value);
         g_tile_n.store(value);
         return LN_SUCCESS;
     }
@@ -987,7 +990,7 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
     // C is packed by the first contraction's spare CTAs when it has fewer
     // output tiles than SMs, else here with A and B
     PackMulti side;
-    const bool try_side = umma_tile_n(P, 0) == 256 && make_pack_multi(ps + 2, 1, side) && pack_stream_eligible(side);
+    const bool try_side = p.g1.bn == 256 && make_pack_multi(ps + 2, 1, side) && pack_stream_eligible(side);
     LN_TRY(pack_operands(ps, try_side ? 2 : 3, P, st));
     UmmaProblem g1{};
     g1.seg[0] = {p.pa, p.pb};
@@ -1004,6 +1007,7 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
     g1.epi.pack = p.pt;
     g1.epi.pack_kt = p.ktT;
     apply_split(g1, p.s1);
+    g1.bn = p.g1.bn;
     bool side_done = false;
     LN_TRY(umma_contract(g1, P, st, try_side ? &side : nullptr, &side_done));
     if (try_side && !side_done) LN_TRY(pack_operands(ps + 2, 1, P, st));
@@ -1018,6 +1022,7 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
     g2.chunk_kt = tune_chunk_kt();
     g2.inject_timeout = g1.inject_timeout;
     apply_split(g2, p.s2);
+    g2.bn = p.g2.bn;
     g2.epi = ef;
     return umma_contract(g2, P, st);
 }

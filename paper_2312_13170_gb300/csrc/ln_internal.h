@@ -205,15 +205,18 @@ struct UmmaProblem {
     int ksplit;
     float *kpart;
     int *kcnt;
+    int bn;  // output tile width chosen at planning (umma_tile_n); 0: derive from epi.M, epi.N
     EpiParams epi;
 };
 // True when LN_FAULT_INJECT=timeout is set in the environment (read per call).
 bool inject_timeout_requested();
-// Output tile width the engine uses: 256 for general contractions with one or
-// two split terms, else 128. Symmetric problems always use square 128 tiles.
-// `nt` of a problem counts tiles of this width, and the packed N-side operand
-// must hold 128 * (width / 128) * nt rows (zero padded).
-int umma_tile_n(int terms, int sym);
+// Output tile width the engine uses for an M x N output: symmetric problems
+// and three split terms use square 128 tiles; otherwise the "tile_n" knob if
+// set (128 or 256), else 256 unless 256-wide tiles would fill at most half the
+// SMs (then 128: twice the tiles, half the reduction per tile). `nt` of a
+// problem counts tiles of this width, and the packed N-side operand must hold
+// 128 * (width / 128) * nt rows (zero padded).
+int umma_tile_n(int terms, int sym, long long M, long long N);
 // Split-K slices for a single problem with `tiles` output tiles and `ktot`
 // k tiles (segments x k tiles): enough to fill the SMs, at least four k tiles
 // each, none empty; 1 when the tiles already fill the GPU or the "split_k"

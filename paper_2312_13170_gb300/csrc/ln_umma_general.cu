@@ -29,7 +29,13 @@ int epi_kind(const EpiParams &e) {
 
 }  // namespace
 
-int umma_tile_n(int terms, int sym) { return (!sym && terms <= 2) ? tune_tile_n() : 128; }
+int umma_tile_n(int terms, int sym, long long M, long long N) {
+    if (sym || terms > 2) return 128;
+    const int knob = tune_tile_n();
+    if (knob == 128 || knob == 256) return knob;
+    const long long wide_tiles = ceil_div(M, 128) * ceil_div(N, 256);
+    return 2 * wide_tiles <= sm_count() ? 128 : 256;
+}
 
 int umma_ksplit(long long tiles, int ktot) {
     const int sms = sm_count();
@@ -64,11 +70,14 @@ ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st, const 
     if (p.ksplit > 1) {
         if (!p.kpart || !p.kcnt) return fail(LN_ERR_INVALID_VALUE, "split-K without its workspace");
         tiles *= p.ksplit;
-        LN_CUDA_TRY(cudaMemsetAsync(p.kcnt, 0, umma_split_cnt_bytes(tiles / p.ksplit, umma_tile_n(terms, 0)), st));
+        LN_CUDA_TRY(cudaMemsetAsync(p.kcnt, 0, umma_split_cnt_bytes(tiles / p.ksplit, 0), st));
     }
     if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many work items");
     const int total = (int)tiles;
-    const bool wide = umma_tile_n(terms, 0) == 256;
+    const int bn = p.bn > 0 ? p.bn : umma_tile_n(terms, 0, p.epi.M, p.epi.N);
+    if (bn != 128 && bn != 256) return fail(LN_ERR_INVALID_VALUE, "tile width %d", bn);
+    if (terms > 2 && bn != 128) return fail(LN_ERR_INVALID_VALUE, "three split terms need 128-wide tiles");
+    const bool wide = bn == 256;
     switch (terms) {
         case 1:
             return wide ? launch_single<1, 256>(ek, p, total, st, side, side_done)

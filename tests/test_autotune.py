@@ -40,7 +40,7 @@ def test_cache_roundtrip(tmp_path, monkeypatch):
 def test_candidates_respect_knob_domains():
     for op, cands in autotune.CANDIDATES.items():
         for c in cands:
-            assert c["tile_n"] in (128, 256) and c["chunk_kt"] in (1, 2), (op, c)
+            assert c["tile_n"] in (0, 128, 256) and c["chunk_kt"] in (1, 2), (op, c)
 
 
 @pytest.mark.gpu
@@ -58,7 +58,7 @@ def test_tuning_pass_and_cached_use(tmp_path, monkeypatch):
     shape = (300, 260, 200, 280)
     best = autotune.tune("gemm_chain", shape, "3xbf16", reps=3)
     assert best in autotune.CANDIDATES["gemm_chain"]
-    assert api.get_tuning("tile_n") == 256 and api.get_tuning("chunk_kt") == 2  # defaults restored
+    assert api.get_tuning("tile_n") == 0 and api.get_tuning("chunk_kt") == 2  # defaults restored
     monkeypatch.setenv("LN_AUTOTUNE", "cached")
     d = inputs.chain_inputs(*shape, seed=3)
     t = {k: torch.from_numpy(d[k]).cuda() for k in "ABCD"}
@@ -73,7 +73,7 @@ def test_tuning_pass_and_cached_use(tmp_path, monkeypatch):
         E, F = api.gemm_chain(t["A"], t["B"], t["C"], t["D"], d["alpha"], d["beta"], prec="3xbf16")
         torch.cuda.synchronize()
         assert inputs.rel_fro(F.cpu().numpy(), F_ref) <= 1e-5, cfg
-    api.set_tuning("tile_n", 256)
+    api.set_tuning("tile_n", 0)
     api.set_tuning("chunk_kt", 2)
 
 
@@ -107,5 +107,5 @@ def test_knob_settings_keep_parity(tile_n, chunk_kt):
         cov = api.covariance(torch.from_numpy(X).cuda(), prec="6xbf16")
         assert inputs.rel_fro(cov.cpu().numpy(), oracle.covariance(X)) <= 1e-5
     finally:
-        api.set_tuning("tile_n", 256)
+        api.set_tuning("tile_n", 0)
         api.set_tuning("chunk_kt", 2)
