@@ -373,7 +373,18 @@ ln_status launch_pack_stream(const PackMulti &m, cudaStream_t st) {
     const int tiles = m.prefix[m.count];
     const int grid = std::min(tiles, sm_count());
     LaunchScope ls_(FAM_PACK, st);
-    k_pack_stream<P, NT><<<grid, NT, bytes, st>>>(m, ns, nout);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = (size_t)bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, k_pack_stream<P, NT>, m, ns, nout);
+    if (le != cudaSuccess) return fail(LN_ERR_CUDA, "split-and-pack stream launch: %s", cudaGetErrorString(le));
     return check_launch("split-and-pack stream");
 }
 

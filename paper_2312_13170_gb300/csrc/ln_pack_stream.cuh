@@ -168,6 +168,10 @@ __device__ void pack_stream(const PackMulti &m, int cta, int ncta, unsigned char
     const int total = m.prefix[m.count];
     const int mine = total > cta ? (total - cta + ncta - 1) / ncta : 0;
     if (mine == 0) return;
+    // the pack stream's kernel may be launched programmatically: global memory
+    // only after the predecessor grid has completed
+    pdl_wait();
+    pdl_trigger();
     // one commit group per tile slot, empty past the end, so that "all but the
     // newest ns - 1 groups complete" always means "tile i has landed"
     for (int i = 0; i < ns - 1; ++i) {

@@ -511,6 +511,8 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
     const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
     if constexpr (EK == EK_PACK && !BATCHED && C::SIDE_OK) {
         if ((int)blockIdx.x >= tile_ctas) {
+            pdl_wait();
+            pdl_trigger();
             if (threadIdx.x < 256)
                 pack_stream<P, 256>(side, (int)blockIdx.x - tile_ctas, (int)gridDim.x - tile_ctas, smem_raw + pad,
                                     C::SIDE_NS, C::SIDE_NOUT);
@@ -551,6 +553,10 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = ctl->tmem_base;
+    // everything above touched only shared memory and TMEM: with a programmatic
+    // launch it overlapped the previous kernel; global memory only from here on
+    pdl_wait();
+    pdl_trigger();
     // Each warpgroup changes its register count at the top of its own branch
     // (the role code is then allocated under that count); the host checked that
     // the launch allocation covers the split.
@@ -904,8 +910,19 @@ ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int 
     UmmaProblem dummy{};
     {
         LaunchScope ls_(FAM_UMMA, st);
-        kern<<<tile_ctas + side_ctas, C::NTHREADS, C::SMEM, st>>>(single ? *single : dummy, probs, prefix, owner,
-                                                                  total, queue, side_ctas ? *side : none, tile_ctas);
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)(tile_ctas + side_ctas));
+        cfg.blockDim = dim3(C::NTHREADS);
+        cfg.dynamicSmemBytes = C::SMEM;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const cudaError_t le = cudaLaunchKernelEx(&cfg, kern, single ? *single : dummy, probs, prefix, owner, total,
+                                                  queue, side_ctas ? *side : none, tile_ctas);
+        if (le != cudaSuccess) return fail(LN_ERR_CUDA, "tcgen05 contraction launch: %s", cudaGetErrorString(le));
     }
     const ln_status ls = check_launch("tcgen05 contraction");
     if (side_done) *side_done = ls == LN_SUCCESS && side_ctas > 0;
