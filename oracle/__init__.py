@@ -57,6 +57,7 @@ def _load():
         "oracle_max_threads": (i, []),
         "oracle_gemm": (None, [i, i, i, d, P, P, d, P, P]),
         "oracle_gemm_chain": (None, [i, i, i, i, d, P, P, P, d, P, P, P, P]),
+        "oracle_3mm": (None, [i, i, i, i, i, P, P, P, P, P, P, P]),
         "oracle_col_stats": (None, [i, i, P, P, P]),
         "oracle_covariance": (None, [i, i, P, P]),
         "oracle_correlation": (None, [i, i, P, P]),
@@ -117,6 +118,21 @@ def gemm_chain(A, B, C, D=None, alpha=1.0, beta=0.0, return_T=False):
     _load().oracle_gemm_chain(ni, nj, nk, nl, float(alpha), _p(A), _p(B), _p(C), float(beta),
                               _p(Dp), _p(T), _p(E), _p(F))
     return (E, F, T) if return_T else (E, F)
+
+
+def three_mm(A, B, C, D, return_EF=False):
+    """E = A@B, F = C@D, G = E@F (polybench 3mm). Returns G or (G, E, F)."""
+    A, B, C, D = _f64(A), _f64(B), _f64(C), _f64(D)
+    ni, nk = A.shape
+    nj = B.shape[1]
+    nm = C.shape[1]
+    nl = D.shape[1]
+    assert B.shape[0] == nk and C.shape[0] == nj and D.shape[0] == nm
+    E = np.empty((ni, nj), np.float64)
+    F = np.empty((nj, nl), np.float64)
+    G = np.empty((ni, nl), np.float64)
+    _load().oracle_3mm(ni, nj, nk, nl, nm, _p(A), _p(B), _p(C), _p(D), _p(E), _p(F), _p(G))
+    return (G, E, F) if return_EF else G
 
 
 def col_stats(X):

@@ -1,8 +1,9 @@
 /*
  * FP64 CPU oracle for the loop nests that loop internalization (paper Sec. VI-C)
  * and array-reduction detection (paper Sec. VI-B) speed up: GEMM, a chain of
- * two GEMMs (polybench 2mm), covariance, correlation, SYRK and SYR2K, plus the
- * vector-Jacobian products of the chain, covariance and correlation.
+ * two GEMMs (polybench 2mm), three chained products (polybench 3mm),
+ * covariance, correlation, SYRK and SYR2K, plus the vector-Jacobian products of
+ * the chain, covariance and correlation.
  *
  * TEST INFRASTRUCTURE ONLY. This file is the plain definition of what the GPU
  * library computes, written as straightforward FP64 loops with no blocking, no
@@ -163,6 +164,24 @@ void oracle_correlation(int n, int m, const double *X, double *corr) {
     }
     free(mean);
     free(ss);
+}
+
+/*
+ * Three chained products (polybench 3mm, paper Sec. VIII, one of the kernels
+ * loop internalization speeds up): E = A*B, F = C*D, G = E*F, no scaling.
+ * A is ni x nk, B is nk x nj, C is nj x nm, D is nm x nl; E is ni x nj,
+ * F is nj x nl, G is ni x nl. E and F are kept in FP64 and returned when the
+ * pointers are not NULL.
+ */
+void oracle_3mm(int ni, int nj, int nk, int nl, int nm, const double *A, const double *B,
+                const double *C, const double *D, double *E_out, double *F_out, double *G) {
+    double *E = E_out ? E_out : (double *)malloc(sizeof(double) * (size_t)ni * nj + 1);
+    double *F = F_out ? F_out : (double *)malloc(sizeof(double) * (size_t)nj * nl + 1);
+    oracle_gemm(ni, nj, nk, 1.0, A, B, 0.0, NULL, E);
+    oracle_gemm(nj, nl, nm, 1.0, C, D, 0.0, NULL, F);
+    oracle_gemm(ni, nl, nj, 1.0, E, F, 0.0, NULL, G);
+    if (!E_out) free(E);
+    if (!F_out) free(F);
 }
 
 static int in_fill(int fill, int i, int j) {

@@ -72,6 +72,16 @@ def test_chain_exact_bruteforce(ni, nj, nk, nl):
     assert close(t, T) and close(e, E) and close(f, Fx)
 
 
+@pytest.mark.parametrize("ni,nj,nk,nl,nm", [(1, 1, 1, 1, 1), (3, 4, 2, 5, 3), (6, 2, 5, 4, 7), (2, 7, 3, 1, 4)])
+def test_3mm_exact_bruteforce(ni, nj, nk, nl, nm):
+    A, B, C, D = fmat(ni, nk, 11), fmat(nk, nj, 12), fmat(nj, nm, 13), fmat(nm, nl, 14)
+    E = exact_mm(F(A), F(B))
+    Fm = exact_mm(F(C), F(D))
+    G = exact_mm(E, Fm)
+    g, e, f = oracle.three_mm(A, B, C, D, return_EF=True)
+    assert close(e, E) and close(f, Fm) and close(g, G)
+
+
 def exact_cov(X):
     Xf = F(X)
     n, m = len(Xf), len(Xf[0])
@@ -171,6 +181,30 @@ def test_chain_associativity_and_identity():
     AB = oracle.gemm(A, B)
     assert np.array_equal(E2, AB)
     assert np.array_equal(F2, 2.0 * AB + 0.5 * fmat(40, 20, 4).astype(np.float64))
+
+
+def test_3mm_associativity_identity_and_rank1():
+    """G = (A B)(C D) = A (B (C D)) up to rounding; C = I reduces 3mm to the
+    2mm chain (A B) D exactly; rank-one factors have a closed form."""
+    A, B, C, D = fmat(20, 15, 1), fmat(15, 12, 2), fmat(12, 18, 3), fmat(18, 9, 4)
+    G = oracle.three_mm(A, B, C, D)
+    Ad, Bd, Cd, Dd = (x.astype(np.float64) for x in (A, B, C, D))
+    assert np.max(np.abs(G - Ad @ (Bd @ (Cd @ Dd)))) < 1e-12 * max(1.0, np.max(np.abs(G)))
+    I = np.eye(12, dtype=np.float32)
+    G2 = oracle.three_mm(A, B, I, fmat(12, 9, 5))
+    E2, _ = oracle.gemm_chain(A, B, fmat(12, 9, 5))
+    assert np.array_equal(G2, E2)
+    # A = u 1^T, B = 1 v^T, C = 1 w^T, D = 1 y^T (all-ones inner vectors):
+    # A B = nk u v^T, C D = nm 1 y^T, G = nk nm (v . 1) u y^T
+    ni, nk, nj, nm, nl = 4, 3, 5, 2, 6
+    u, v, y = fmat(ni, 1, 6), fmat(1, nj, 7), fmat(1, nl, 8)
+    A = np.repeat(u, nk, axis=1)
+    B = np.repeat(v, nk, axis=0)
+    C = np.ones((nj, nm), np.float32)
+    D = np.repeat(y, nm, axis=0)
+    G = oracle.three_mm(A, B, C, D)
+    ref = nk * nm * float(np.sum(v.astype(np.float64))) * (u.astype(np.float64) @ y.astype(np.float64))
+    assert np.max(np.abs(G - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref)))
 
 
 def test_covariance_invariants():
@@ -311,6 +345,11 @@ def test_pins_reject_planted_mistakes():
     _, _, S = exact_cov(X)
     wrong = [[S[i][j] / 8 for j in range(4)] for i in range(4)]  # divisor n instead of n-1
     assert not close(oracle.covariance(X), wrong)
+    # 3mm with a transposed F (E F^T) or with the factors swapped (F E) must miss
+    A, B, Cm, Dm = fmat(n, n, 4), fmat(n, n, 5), fmat(n, n, 6), fmat(n, n, 8)
+    G = exact_mm(exact_mm(F(A), F(B)), exact_mm(F(Cm), F(Dm)))
+    assert not close(oracle.three_mm(A, B, Dm.T.copy(), Cm.T.copy()), G)
+    assert not close(oracle.three_mm(Cm, Dm, A, B), G)
 
 
 def test_cov_rows_matches_full():
