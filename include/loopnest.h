@@ -179,6 +179,24 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
                         size_t workspace_bytes, ln_form form, ln_precision prec, void *stream);
 
 /*
+ * Three chained products (polybench 3mm, Sec. VIII):
+ *   E = A * B;  F = C * D;  G = E * F
+ * A is ni x nk, B is nk x nj, C is nj x nm, D is nm x nl, G is ni x nl; all
+ * contiguous (ld = columns). E (ni x nj) and F (nj x nl) live in the
+ * workspace: in FP32 for FP32 forms; for tensor-core forms E is written by its
+ * product's epilogue directly as the packed BF16 row operand of G, and F (as
+ * F^T = D^T C^T) as the packed column operand, so neither exists in FP32.
+ * G must not overlap an input. A, B, C, D and G may be host memory the GPU
+ * can reach, as for ln_gemm_chain. Sizes of 0 are allowed (G = 0 when
+ * nj, nk or nm is 0).
+ */
+ln_status ln_3mm_workspace_size(int ni, int nj, int nk, int nl, int nm, ln_form form, ln_precision prec,
+                                size_t *bytes /*host*/);
+ln_status ln_3mm(int ni, int nj, int nk, int nl, int nm, const float *A, const float *B, const float *C,
+                 const float *D, float *G, void *workspace, size_t workspace_bytes, ln_form form, ln_precision prec,
+                 void *stream);
+
+/*
  * Column statistics of a data matrix X (nsamples x nfeat, ldx), the array
  * reductions of polybench covariance/correlation (Sec. VI-B, Sec. VIII), two
  * passes: mean[j] = sum_s X[s][j] / n; ss[j] = sum_s (X[s][j] - mean[j])^2.

@@ -63,6 +63,8 @@ _SIGS = {
     "ln_gemm": (_I, [_I, _I, _I, _F, _P, _I, _P, _I, _F, _P, _I, _P, _SZ, _I, _I, _P]),
     "ln_gemm_chain_workspace_size": (_I, [_I, _I, _I, _I, _I, _I, _P]),
     "ln_gemm_chain": (_I, [_I, _I, _I, _I, _F, _P, _P, _P, _F, _P, _P, _P, _P, _SZ, _I, _I, _P]),
+    "ln_3mm_workspace_size": (_I, [_I, _I, _I, _I, _I, _I, _I, _P]),
+    "ln_3mm": (_I, [_I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _SZ, _I, _I, _P]),
     "ln_col_stats_workspace_size": (_I, [_I, _I, _I, _P]),
     "ln_col_stats": (_I, [_I, _I, _P, _I, _P, _P, _P, _SZ, _I, _P]),
     "ln_covariance_workspace_size": (_I, [_I, _I, _I, _I, _P]),
@@ -130,7 +132,7 @@ def _f32(t, name, host_ok=False):
         raise TypeError(f"{name} must be a float32 tensor")
     if not t.is_cuda and not (host_ok and t.is_pinned()):
         raise TypeError(f"{name} must be a CUDA tensor" + (" or a pinned host tensor" if host_ok else ""))
-    if t.dim() != 2 or t.stride(1) != 1:
+    if t.dim() != 2 or (t.stride(1) != 1 and t.numel() > 0):
         raise ValueError(f"{name} must be a 2-D row-major tensor (unit column stride)")
     return t
 
@@ -241,6 +243,33 @@ def gemm_chain(A, B, C, D=None, alpha=1.0, beta=0.0, form="internalized", prec="
     _check(lib().ln_gemm_chain(ni, nj, nk, nl, alpha, _ptr(A), _ptr(B), _ptr(C), beta, _ptr(D), _ptr(E), _ptr(F),
                                _ptr(ws), nb, fm, pr, _stream(stream)), "ln_gemm_chain")
     return E, F
+
+
+def three_mm(A, B, C, D, form="internalized", prec="3xbf16", stream=None, out=None):
+    """G = (A@B)@(C@D) (polybench 3mm); returns G. Operands may be pinned host
+    tensors as for gemm_chain."""
+    for t, nme in ((A, "A"), (B, "B"), (C, "C"), (D, "D")):
+        _f32(t, nme, host_ok=True)
+        if not t.is_contiguous():
+            raise ValueError(f"{nme} must be contiguous")
+    ni, nk = A.shape
+    nj, nm, nl = B.shape[1], C.shape[1], D.shape[1]
+    if B.shape[0] != nk or C.shape[0] != nj or D.shape[0] != nm:
+        raise ValueError("shape mismatch")
+    fm, pr = _enum(FORMS, form, "form"), _enum(PRECS, prec, "precision")
+    if out is None:
+        G = torch.empty((ni, nl), dtype=torch.float32, device=A.device, pin_memory=not A.is_cuda)
+    else:
+        G = out
+        _f32(G, "G", host_ok=True)
+        if tuple(G.shape) != (ni, nl) or not G.is_contiguous():
+            raise ValueError("out must be contiguous ni x nl")
+    dev = A.device if A.is_cuda else torch.device("cuda", torch.cuda.current_device())
+    _autotune("three_mm", (ni, nj, nk, nl, nm), prec)
+    ws, nb = _workspace(_ws_query("ln_3mm_workspace_size", ni, nj, nk, nl, nm, fm, pr), dev)
+    _check(lib().ln_3mm(ni, nj, nk, nl, nm, _ptr(A), _ptr(B), _ptr(C), _ptr(D), _ptr(G), _ptr(ws), nb, fm, pr,
+                        _stream(stream)), "ln_3mm")
+    return G
 
 
 def col_stats(X, form="internalized", stream=None):

@@ -380,6 +380,43 @@ void plan_chain(Ws &w, int ni, int nj, int nk, int nl, ln_form form, ln_precisio
     plan_split(w, (long long)p.g2.mt * p.g2.nt, p.g2.kt, p.g2.bn, p.s2);
 }
 
+// ------------------------------------------------------------------ 3mm
+// FP32 forms keep E = A B and F = C D in the workspace. Tensor-core forms: the
+// first product's epilogue writes E as the packed row operand of G = E F; the
+// second product computes F^T = D^T C^T, whose packing epilogue writes exactly
+// the packed column operand of G (rows = G's columns, K = nj).
+struct Mm3Plan {
+    float *E = nullptr, *F = nullptr;
+    char *pa = nullptr, *pb = nullptr, *pc = nullptr, *pd = nullptr, *pe = nullptr, *pf = nullptr;
+    ContractPlan gE, gF, gG;  // E = A B; F^T = D^T C^T; G = E F
+    int ktE = 0, ktF = 0, rowsF = 0;
+    SplitPlan sE, sF, sG;
+};
+
+void plan_3mm(Ws &w, int ni, int nj, int nk, int nl, int nm, ln_form form, ln_precision prec, Mm3Plan &p) {
+    if (form != LN_FORM_INTERNALIZED || !tensor_prec(prec)) {
+        p.E = w.take<float>(sizeof(float) * (size_t)ni * nj);
+        p.F = w.take<float>(sizeof(float) * (size_t)nj * nl);
+        return;
+    }
+    const int P = prec_terms(prec);
+    contract_geometry(ni, nj, nk, P, p.gE);
+    contract_geometry(nl, nj, nm, P, p.gF);
+    contract_geometry(ni, nl, nj, P, p.gG);
+    p.ktE = p.gE.yrt * (PK_ROWS / PK_K);        // k tiles the first product writes (K of G = nj)
+    p.ktF = p.gF.yrt * (PK_ROWS / PK_K);        // k tiles the second product writes
+    p.rowsF = std::max(p.gF.mt, p.gG.yrt);      // G reads gG.yrt row tiles of F^T
+    p.pa = w.take<char>(packed_bytes(p.gE.mt, p.gE.kt, P));
+    p.pb = w.take<char>(packed_bytes(p.gE.yrt, p.gE.kt, P));
+    p.pd = w.take<char>(packed_bytes(p.gF.mt, p.gF.kt, P));
+    p.pc = w.take<char>(packed_bytes(p.gF.yrt, p.gF.kt, P));
+    p.pe = w.take<char>(packed_bytes(p.gE.mt, p.ktE, P));
+    p.pf = w.take<char>(packed_bytes(p.rowsF, p.ktF, P));
+    plan_split(w, (long long)p.gE.mt * p.gE.nt, p.gE.kt, p.gE.bn, p.sE);
+    plan_split(w, (long long)p.gF.mt * p.gF.nt, p.gF.kt, p.gF.bn, p.sF);
+    plan_split(w, (long long)p.gG.mt * p.gG.nt, p.gG.kt, p.gG.bn, p.sG);
+}
+
 // ------------------------------------------------------------------ covariance / correlation
 struct CovPlan {
     double *mean = nullptr, *ss = nullptr, *partials = nullptr;
@@ -1025,6 +1062,119 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
     g2.bn = p.g2.bn;
     g2.epi = ef;
     return umma_contract(g2, P, st);
+}
+
+// ------------------------------------------------------------------ 3mm
+ln_status ln_3mm_workspace_size(int ni, int nj, int nk, int nl, int nm, ln_form form, ln_precision prec,
+                                size_t *bytes) {
+    clear_error();
+    LN_TRY(check_dims({ni, nj, nk, nl, nm}));
+    LN_TRY(check_form(form, prec));
+    if (!bytes) return fail(LN_ERR_INVALID_VALUE, "NULL bytes");
+    Ws w(nullptr);
+    Mm3Plan p;
+    plan_3mm(w, ni, nj, nk, nl, nm, form, prec, p);
+    *bytes = w.off;
+    return LN_SUCCESS;
+}
+
+ln_status ln_3mm(int ni, int nj, int nk, int nl, int nm, const float *A, const float *B, const float *C,
+                 const float *D, float *G, void *ws, size_t wsb, ln_form form, ln_precision prec, void *stream) {
+    clear_error();
+    LN_TRY(check_dims({ni, nj, nk, nl, nm}));
+    LN_TRY(check_form(form, prec));
+    if (ni == 0 || nl == 0) return LN_SUCCESS;
+    const bool zero = nj == 0 || nk == 0 || nm == 0;  // E or F is empty: G = 0
+    if (!G || (!zero && (!A || !B || !C || !D))) return fail(LN_ERR_INVALID_VALUE, "NULL operand");
+    const Span sg = mspan(G, ni, nl, nl);
+    const Span ins[4] = {mspan(A, ni, nk, nk), mspan(B, nk, nj, nj), mspan(C, nj, nm, nm), mspan(D, nm, nl, nl)};
+    for (const Span &x : ins)
+        if (!zero && overlap(sg, x)) return fail(LN_ERR_ALIASING, "G overlaps an input");
+    LN_TRY(device_view(A, &A, "A"));
+    LN_TRY(device_view(B, &B, "B"));
+    LN_TRY(device_view(C, &C, "C"));
+    LN_TRY(device_view(D, &D, "D"));
+    LN_TRY(device_view(G, &G, "G"));
+    cudaStream_t st = S(stream);
+    const EpiParams eg = epi_store(ni, nl, 1.0f, G, nl);
+    if (zero) return plain_gemm(ni, nl, 0, nullptr, 0, 0, nullptr, 0, 0, eg, st);
+    Ws count(nullptr);
+    Mm3Plan p;
+    plan_3mm(count, ni, nj, nk, nl, nm, form, prec, p);
+    LN_TRY(check_ws(ws, wsb, count.off));
+    Ws w(ws);
+    plan_3mm(w, ni, nj, nk, nl, nm, form, prec, p);
+    if (p.E) {
+        ContractPlan none;
+        LN_TRY(run_contract(ni, nj, nk, {A, nk, 0}, {B, nj, 0}, epi_store(ni, nj, 1.0f, p.E, nj), form, prec, none,
+                            st));
+        LN_TRY(run_contract(nj, nl, nm, {C, nm, 0}, {D, nl, 0}, epi_store(nj, nl, 1.0f, p.F, nl), form, prec, none,
+                            st));
+        return run_contract(ni, nl, nj, {p.E, nj, 0}, {p.F, nl, 0}, eg, form, prec, none, st);
+    }
+    const int P = prec_terms(prec);
+    // E = A B: rows of A, columns of B (B^T K-major); F^T = D^T C^T: rows of
+    // D^T (D transposed), columns of C^T = rows of C (K = nm contiguous)
+    PackSrc ps[4] = {{A, nk, 0, ni, nk, nullptr, nullptr, p.pa, p.gE.mt, p.gE.kt},
+                     {B, nj, 1, nj, nk, nullptr, nullptr, p.pb, p.gE.yrt, p.gE.kt},
+                     {D, nl, 1, nl, nm, nullptr, nullptr, p.pd, p.gF.mt, p.gF.kt},
+                     {C, nm, 0, nj, nm, nullptr, nullptr, p.pc, p.gF.yrt, p.gF.kt}};
+    PackMulti side;
+    const bool try_side = p.gE.bn == 256 && make_pack_multi(ps + 2, 2, side) && pack_stream_eligible(side);
+    LN_TRY(pack_operands(ps, try_side ? 2 : 4, P, st));
+    UmmaProblem gE{};
+    gE.seg[0] = {p.pa, p.pb};
+    gE.nseg = 1;
+    gE.kt = p.gE.kt;
+    gE.x_kt = gE.y_kt = p.gE.kt;
+    gE.mt = p.gE.mt;
+    gE.nt = p.gE.nt;
+    gE.chunk_kt = tune_chunk_kt();
+    gE.inject_timeout = inject_timeout_requested();
+    apply_split(gE, p.sE);
+    gE.bn = p.gE.bn;
+    gE.epi.mode = EPI_PACK;
+    gE.epi.M = ni;
+    gE.epi.N = nj;
+    gE.epi.pack = p.pe;
+    gE.epi.pack_kt = p.ktE;
+    bool side_done = false;
+    LN_TRY(umma_contract(gE, P, st, try_side ? &side : nullptr, &side_done));
+    if (try_side && !side_done) LN_TRY(pack_operands(ps + 2, 2, P, st));
+    if (p.rowsF > p.gF.mt)  // row tiles of F^T that G reads but no product writes
+        LN_CUDA_TRY(cudaMemsetAsync(p.pf + packed_bytes(p.gF.mt, p.ktF, P), 0,
+                                    packed_bytes(p.rowsF - p.gF.mt, p.ktF, P), st));
+    UmmaProblem gF{};
+    gF.seg[0] = {p.pd, p.pc};
+    gF.nseg = 1;
+    gF.kt = p.gF.kt;
+    gF.x_kt = gF.y_kt = p.gF.kt;
+    gF.mt = p.gF.mt;
+    gF.nt = p.gF.nt;
+    gF.chunk_kt = tune_chunk_kt();
+    gF.inject_timeout = gE.inject_timeout;
+    apply_split(gF, p.sF);
+    gF.bn = p.gF.bn;
+    gF.epi.mode = EPI_PACK;
+    gF.epi.M = nl;
+    gF.epi.N = nj;
+    gF.epi.pack = p.pf;
+    gF.epi.pack_kt = p.ktF;
+    LN_TRY(umma_contract(gF, P, st));
+    UmmaProblem gG{};
+    gG.seg[0] = {p.pe, p.pf};
+    gG.nseg = 1;
+    gG.kt = p.gG.kt;
+    gG.x_kt = p.ktE;
+    gG.y_kt = p.ktF;
+    gG.mt = p.gG.mt;
+    gG.nt = p.gG.nt;
+    gG.chunk_kt = tune_chunk_kt();
+    gG.inject_timeout = gE.inject_timeout;
+    apply_split(gG, p.sG);
+    gG.bn = p.gG.bn;
+    gG.epi = eg;
+    return umma_contract(gG, P, st);
 }
 
 // ------------------------------------------------------------------ statistics, covariance, correlation

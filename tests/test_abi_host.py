@@ -128,3 +128,26 @@ def test_batched_validation(L):
 
 def test_stream_check_symbol_present(L):
     assert callable(L.ln_stream_check)
+
+
+def test_3mm_validation_and_workspace(L):
+    FAKE_D, FAKE_G = 0x7F0000300000, 0x7F0000400000
+    ws = ctypes.c_size_t(0)
+    # negative size, bad form, NULL operand, G aliasing an input
+    assert L.ln_3mm(-1, 4, 4, 4, 4, P(FAKE_A), P(FAKE_B), P(FAKE_C), P(FAKE_D), P(FAKE_G), None, 0, 1, 2, None) == 1
+    assert L.ln_3mm(4, 4, 4, 4, 4, P(FAKE_A), P(FAKE_B), P(FAKE_C), P(FAKE_D), P(FAKE_G), None, 0, 7, 2, None) == 1
+    assert L.ln_3mm(4, 4, 4, 4, 4, P(FAKE_A), None, P(FAKE_C), P(FAKE_D), P(FAKE_G), None, 0, 1, 2, None) == 1
+    assert "NULL" in last(L)
+    assert L.ln_3mm(8, 8, 8, 8, 8, P(FAKE_A), P(FAKE_B), P(FAKE_C), P(FAKE_D), P(FAKE_A + 64), None, 0, 1, 2,
+                    None) == 2
+    # empty outputs are a no-op
+    assert L.ln_3mm(0, 4, 4, 4, 4, None, None, None, None, None, None, 0, 1, 2, None) == 0
+    # FP32 forms keep E (ni x nj) and F (nj x nl) in the workspace, 256-byte aligned each
+    assert L.ln_3mm_workspace_size(100, 60, 70, 80, 90, 1, 0, ctypes.byref(ws)) == 0
+    up = lambda b: (b + 255) // 256 * 256
+    assert ws.value == up(100 * 60 * 4) + up(60 * 80 * 4)
+    # tensor-core forms: packed A, B^T, D^T, C, E (row operand) and F^T (column operand)
+    assert L.ln_3mm_workspace_size(256, 256, 256, 256, 256, 1, 2, ctypes.byref(ws)) == 0
+    tile = 2 * 16384  # two split terms of a 128 x 64 tile
+    expect = tile * (2 * 4 + 2 * 4 + 2 * 4 + 2 * 4 + 2 * 4 + 2 * 4)
+    assert ws.value == expect
