@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the CPU baseline sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
     ap.add_argument("--suite", action="store_true", help="measure every workload and form, one JSON line each")
-    ap.add_argument("--only", default="", help="suite: comma-separated workloads (gemm,chain,cov,batched,backward)")
+    ap.add_argument("--only", default="", help="suite: comma-separated workloads (gemm,chain,3mm,cov,batched,backward)")
     ap.add_argument("--modes", default="", help="suite: comma-separated form/precision pairs, e.g. internalized/3xbf16")
     return ap.parse_args()
 
@@ -489,12 +489,13 @@ def run_suite(args):
              ("internalized", "6xbf16")]
     if args.modes:
         modes = [tuple(x.split("/")) for x in args.modes.split(",")]
-    only = set(args.only.split(",")) if args.only else {"gemm", "chain", "cov", "batched", "backward"}
+    only = set(args.only.split(",")) if args.only else {"gemm", "chain", "3mm", "cov", "batched", "backward"}
     cores = oracle.max_threads()
 
     # -------------------------------------------------- GEMM 256^3
     run_gemm_256(only, modes, api, inputs, oracle, cores, time_it, emit)
     run_chain_2048(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
+    run_3mm(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
     run_cov(only, modes, api, inputs, oracle, cores, time_it, emit, reps, hbm)
     run_batched(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
     run_backward(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
@@ -544,6 +545,32 @@ def run_chain_2048(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
                                             prec=prec, out=out), n=3 if form == "plain" else reps)
         emit("chain 2048^2", "gemm_chain", form, prec, 4.0 * n ** 3, 6 * 4 * n * n, ms, err, cpu)
 
+
+
+def run_3mm(only, modes, api, inputs, oracle, cores, time_it, emit, reps):
+    """Polybench 3mm, G = (A B)(C D), at the paper's problem size (1024) and at
+    2048; entries U[-1,1], seed 0, drawn in the order A, B, C, D."""
+    import torch
+
+    if "3mm" not in only:
+        return
+    for n in (1024, 2048):
+        rng = np.random.default_rng(0)
+        A, B, C, D = (rng.uniform(-1.0, 1.0, size=(n, n)).astype(np.float32) for _ in range(4))
+        rows = 64
+        t0 = time.perf_counter()
+        Gr = oracle.three_mm(A[:rows], B, C, D)  # full F = C D, then the sampled rows of G
+        dt = time.perf_counter() - t0
+        cpu = {"kind": "oracle", "cores": cores, "seconds": dt, "sample": f"first {rows} rows of G (with all of F)",
+               "gflops": 2.0 * (rows * n * n + n ** 3 + rows * n * n) / dt / 1e9}
+        T = [torch.from_numpy(x).cuda() for x in (A, B, C, D)]
+        for form, prec in modes:
+            if form == "plain" and n > 1024:
+                continue
+            G = api.three_mm(*T, form=form, prec=prec)
+            err = inputs.rel_fro(G[:rows].cpu().numpy(), Gr)
+            ms = time_it(lambda: api.three_mm(*T, form=form, prec=prec, out=G), n=3 if form == "plain" else reps)
+            emit(f"3mm {n}^3 (G = (A*B)*(C*D))", "3mm", form, prec, 6.0 * n ** 3, 5 * 4 * n * n, ms, err, cpu)
 
 
 def run_cov(only, modes, api, inputs, oracle, cores, time_it, emit, reps, hbm):
