@@ -58,6 +58,7 @@ def _load():
         "oracle_gemm": (None, [i, i, i, d, P, P, d, P, P]),
         "oracle_gemm_chain": (None, [i, i, i, i, d, P, P, P, d, P, P, P, P]),
         "oracle_3mm": (None, [i, i, i, i, i, P, P, P, P, P, P, P]),
+        "oracle_3mm_vjp": (None, [i, i, i, i, i, P, P, P, P, P, P, P, P, P]),
         "oracle_col_stats": (None, [i, i, P, P, P]),
         "oracle_covariance": (None, [i, i, P, P]),
         "oracle_correlation": (None, [i, i, P, P]),
@@ -133,6 +134,18 @@ def three_mm(A, B, C, D, return_EF=False):
     G = np.empty((ni, nl), np.float64)
     _load().oracle_3mm(ni, nj, nk, nl, nm, _p(A), _p(B), _p(C), _p(D), _p(E), _p(F), _p(G))
     return (G, E, F) if return_EF else G
+
+
+def three_mm_vjp(A, B, C, D, Gb):
+    """(dA, dB, dC, dD) for G = (A@B)@(C@D) with upstream gradient Gb = dL/dG."""
+    A, B, C, D, Gb = _f64(A), _f64(B), _f64(C), _f64(D), _f64(Gb)
+    ni, nk = A.shape
+    nj = B.shape[1]
+    nm = C.shape[1]
+    nl = D.shape[1]
+    out = [np.empty(s, np.float64) for s in ((ni, nk), (nk, nj), (nj, nm), (nm, nl))]
+    _load().oracle_3mm_vjp(ni, nj, nk, nl, nm, _p(A), _p(B), _p(C), _p(D), _p(Gb), *(_p(x) for x in out))
+    return tuple(out)
 
 
 def col_stats(X):

@@ -3,7 +3,7 @@
  * and array-reduction detection (paper Sec. VI-B) speed up: GEMM, a chain of
  * two GEMMs (polybench 2mm), three chained products (polybench 3mm),
  * covariance, correlation, SYRK and SYR2K, plus the vector-Jacobian products of
- * the chain, covariance and correlation.
+ * the chain, 3mm, covariance and correlation.
  *
  * TEST INFRASTRUCTURE ONLY. This file is the plain definition of what the GPU
  * library computes, written as straightforward FP64 loops with no blocking, no
@@ -182,6 +182,56 @@ void oracle_3mm(int ni, int nj, int nk, int nl, int nm, const double *A, const d
     oracle_gemm(ni, nl, nj, 1.0, E, F, 0.0, NULL, G);
     if (!E_out) free(E);
     if (!F_out) free(F);
+}
+
+/*
+ * X_out = P * Q^T (P is r x c, Q is s x c, X_out is r x s), the contraction
+ * over the shared trailing index that the 3mm adjoint uses.
+ */
+static void oracle_mm_nt(int r, int s, int c, const double *Pm, const double *Qm, double *X_out) {
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < s; ++j) {
+            double acc = 0.0;
+            for (int q = 0; q < c; ++q) acc += Pm[(size_t)i * c + q] * Qm[(size_t)j * c + q];
+            X_out[(size_t)i * s + j] = acc;
+        }
+}
+
+/* X_out = P^T * Q (P is c x r, Q is c x s, X_out is r x s). */
+static void oracle_mm_tn(int r, int s, int c, const double *Pm, const double *Qm, double *X_out) {
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < s; ++j) {
+            double acc = 0.0;
+            for (int q = 0; q < c; ++q) acc += Pm[(size_t)q * r + i] * Qm[(size_t)q * s + j];
+            X_out[(size_t)i * s + j] = acc;
+        }
+}
+
+/*
+ * Vector-Jacobian product of 3mm, G = (A B)(C D), for an upstream gradient
+ * Gb = dL/dG (ni x nl). With E = A B and F = C D: dE = Gb F^T, dF = E^T Gb,
+ * dA = dE B^T, dB = A^T dE, dC = dF D^T, dD = C^T dF.
+ */
+void oracle_3mm_vjp(int ni, int nj, int nk, int nl, int nm, const double *A, const double *B, const double *C,
+                    const double *D, const double *Gb, double *dA, double *dB, double *dC, double *dD) {
+    double *E = (double *)malloc(sizeof(double) * (size_t)ni * nj + 1);
+    double *F = (double *)malloc(sizeof(double) * (size_t)nj * nl + 1);
+    double *dE = (double *)malloc(sizeof(double) * (size_t)ni * nj + 1);
+    double *dF = (double *)malloc(sizeof(double) * (size_t)nj * nl + 1);
+    oracle_gemm(ni, nj, nk, 1.0, A, B, 0.0, NULL, E);
+    oracle_gemm(nj, nl, nm, 1.0, C, D, 0.0, NULL, F);
+    oracle_mm_nt(ni, nj, nl, Gb, F, dE);
+    oracle_mm_tn(nj, nl, ni, E, Gb, dF);
+    oracle_mm_nt(ni, nk, nj, dE, B, dA);
+    oracle_mm_tn(nk, nj, ni, A, dE, dB);
+    oracle_mm_nt(nj, nm, nl, dF, D, dC);
+    oracle_mm_tn(nm, nl, nj, C, dF, dD);
+    free(E);
+    free(F);
+    free(dE);
+    free(dF);
 }
 
 static int in_fill(int fill, int i, int j) {

@@ -283,6 +283,38 @@ def test_chain_vjp_exact_directional():
         assert abs(got - exact) <= 1e-13 * max(1.0, abs(exact))
 
 
+def test_3mm_vjp_exact_directional():
+    """G = (A B)(C D) is linear in each factor, so <dL/dX, H> = L(X+H) - L(X)
+    exactly for L = <Gb, G> and any one factor X. The adjoint of a plausible
+    mistake, G' = (A B)(C D)^T (F transposed, square factors), must fail it."""
+    ni, nj, nk, nl, nm = 3, 4, 2, 4, 4
+    A, B, C, D, Gb = fmat(ni, nk, 1), fmat(nk, nj, 2), fmat(nj, nm, 3), fmat(nm, nl, 4), fmat(ni, nl, 5)
+    H = [fmat(ni, nk, 6), fmat(nk, nj, 7), fmat(nj, nm, 8), fmat(nm, nl, 9)]
+
+    def L(a, b, c, d):
+        G = exact_mm(exact_mm(F(a), F(b)), exact_mm(F(c), F(d)))
+        Gf = F(Gb)
+        return sum(Gf[i][l] * G[i][l] for i in range(ni) for l in range(nl))
+
+    base_args = [x.astype(np.float64) for x in (A, B, C, D)]
+    base = L(*base_args)
+
+    def matches(grads):
+        for idx, grad in enumerate(grads):
+            args = list(base_args)
+            args[idx] = args[idx] + H[idx].astype(np.float64)
+            exact = float(L(*args) - base)
+            got = float(np.sum(grad * H[idx].astype(np.float64)))
+            if abs(got - exact) > 1e-13 * max(1.0, abs(exact)):
+                return False
+        return True
+
+    assert matches(oracle.three_mm_vjp(A, B, C, D, Gb))
+    # (C D)^T = D^T C^T: the adjoint of E (D^T C^T) in place of E (C D)
+    wrong = oracle.three_mm_vjp(A, B, np.ascontiguousarray(D.T), np.ascontiguousarray(C.T), Gb)
+    assert not matches((wrong[0], wrong[1], np.ascontiguousarray(wrong[3].T), np.ascontiguousarray(wrong[2].T)))
+
+
 def _fd_check(fun, X, dX, h_rel=1e-6, tol=1e-7, seed=0):
     rng = np.random.default_rng(seed)
     n, m = X.shape
