@@ -295,6 +295,19 @@ ln_status ln_syr2k_batched(ln_fill fill, int count, const ln_sym_desc *h_descs /
                            size_t workspace_bytes, ln_form form, ln_precision prec, void *stream);
 
 /*
+ * Adjoint of 3mm (ln_3mm), G = (A B)(C D): given Gb = dL/dG (ni x nl), writes
+ * dA = Gb (C D)^T B^T, dB = A^T Gb (C D)^T, dC = (A B)^T Gb D^T and
+ * dD = C^T (A B)^T Gb (E = A B and F = C D are recomputed in the workspace).
+ * Shapes as in ln_3mm; every matrix contiguous; gradient outputs must not
+ * overlap each other or an input.
+ */
+ln_status ln_3mm_bwd_workspace_size(int ni, int nj, int nk, int nl, int nm, ln_form form, ln_precision prec,
+                                    size_t *bytes /*host*/);
+ln_status ln_3mm_bwd(int ni, int nj, int nk, int nl, int nm, const float *A, const float *B, const float *C,
+                     const float *D, const float *Gb, float *dA, float *dB, float *dC, float *dD, void *workspace,
+                     size_t workspace_bytes, ln_form form, ln_precision prec, void *stream);
+
+/*
  * Vector-Jacobian products (hand-written adjoints).
  *
  * Chain: for E = (A*B)*C and an upstream gradient G = dL/dE (ni x nl),

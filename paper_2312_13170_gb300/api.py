@@ -65,6 +65,8 @@ _SIGS = {
     "ln_gemm_chain": (_I, [_I, _I, _I, _I, _F, _P, _P, _P, _F, _P, _P, _P, _P, _SZ, _I, _I, _P]),
     "ln_3mm_workspace_size": (_I, [_I, _I, _I, _I, _I, _I, _I, _P]),
     "ln_3mm": (_I, [_I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _SZ, _I, _I, _P]),
+    "ln_3mm_bwd_workspace_size": (_I, [_I, _I, _I, _I, _I, _I, _I, _P]),
+    "ln_3mm_bwd": (_I, [_I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _I, _I, _P]),
     "ln_col_stats_workspace_size": (_I, [_I, _I, _I, _P]),
     "ln_col_stats": (_I, [_I, _I, _P, _I, _P, _P, _P, _SZ, _I, _P]),
     "ln_covariance_workspace_size": (_I, [_I, _I, _I, _I, _P]),
@@ -400,6 +402,41 @@ def covariance_bwd(X, W, stats=None, form="internalized", prec="3xbf16", stream=
 
 def correlation_bwd(X, W, stats=None, form="internalized", prec="3xbf16", stream=None):
     return _cov_bwd("ln_correlation_bwd", X, W, stats, form, prec, stream)
+
+
+def three_mm_bwd(A, B, C, D, Gb, form="internalized", prec="3xbf16", stream=None):
+    """(dA, dB, dC, dD) for G = (A@B)@(C@D) with upstream gradient Gb."""
+    for t, nme in ((A, "A"), (B, "B"), (C, "C"), (D, "D"), (Gb, "Gb")):
+        _f32(t, nme)
+        if not t.is_contiguous():
+            raise ValueError(f"{nme} must be contiguous")
+    ni, nk = A.shape
+    nj, nm, nl = B.shape[1], C.shape[1], D.shape[1]
+    if B.shape[0] != nk or C.shape[0] != nj or D.shape[0] != nm or tuple(Gb.shape) != (ni, nl):
+        raise ValueError("shape mismatch")
+    fm, pr = _enum(FORMS, form, "form"), _enum(PRECS, prec, "precision")
+    grads = [torch.empty(x.shape, dtype=torch.float32, device=A.device) for x in (A, B, C, D)]
+    ws, nb = _workspace(_ws_query("ln_3mm_bwd_workspace_size", ni, nj, nk, nl, nm, fm, pr), A.device)
+    _check(lib().ln_3mm_bwd(ni, nj, nk, nl, nm, _ptr(A), _ptr(B), _ptr(C), _ptr(D), _ptr(Gb),
+                            *(_ptr(g) for g in grads), _ptr(ws), nb, fm, pr, _stream(stream)), "ln_3mm_bwd")
+    return tuple(grads)
+
+
+class ThreeMmFn(torch.autograd.Function):
+    """G = (A@B)@(C@D) with the hand-written adjoint (ln_3mm_bwd)."""
+
+    @staticmethod
+    def forward(ctx, A, B, C, D, form="internalized", prec="3xbf16"):
+        ts = [t.contiguous() for t in (A, B, C, D)]
+        ctx.save_for_backward(*ts)
+        ctx.cfg = (form, prec)
+        return three_mm(*ts, form=form, prec=prec)
+
+    @staticmethod
+    def backward(ctx, gG):
+        A, B, C, D = ctx.saved_tensors
+        dA, dB, dC, dD = three_mm_bwd(A, B, C, D, gG.contiguous(), *ctx.cfg)
+        return dA, dB, dC, dD, None, None
 
 
 class GemmChainFn(torch.autograd.Function):

@@ -741,6 +741,42 @@ ln_status contract_into(int M, int N, int K, Operand a, Operand b, const EpiPara
     return run_contract(M, N, K, a, b, e, form, prec, cp, st);
 }
 
+// E = A B and F = C D recomputed; dE = Gb F^T, dF = E^T Gb; then the four
+// factor gradients. Contractions (M, N, K) in execution order:
+constexpr int MM3_BWD_N = 8;
+void mm3_bwd_dims(int ni, int nj, int nk, int nl, int nm, int (*d)[3]) {
+    const int dims[MM3_BWD_N][3] = {{ni, nj, nk}, {nj, nl, nm}, {ni, nj, nl}, {nj, nl, ni},
+                                    {ni, nk, nj}, {nk, nj, ni}, {nj, nm, nl}, {nm, nl, nj}};
+    for (int i = 0; i < MM3_BWD_N; ++i)
+        for (int q = 0; q < 3; ++q) d[i][q] = dims[i][q];
+}
+
+struct Mm3BwdPlan {
+    float *E = nullptr, *F = nullptr, *dE = nullptr, *dF = nullptr;
+    char *pack = nullptr;
+    SplitArea split;
+};
+
+void plan_3mm_bwd(Ws &w, int ni, int nj, int nk, int nl, int nm, ln_form form, ln_precision prec, Mm3BwdPlan &p) {
+    p.E = w.take<float>(sizeof(float) * (size_t)ni * nj);
+    p.F = w.take<float>(sizeof(float) * (size_t)nj * nl);
+    p.dE = w.take<float>(sizeof(float) * (size_t)ni * nj);
+    p.dF = w.take<float>(sizeof(float) * (size_t)nj * nl);
+    if (form == LN_FORM_INTERNALIZED && tensor_prec(prec)) {
+        const int P = prec_terms(prec);
+        int dims[MM3_BWD_N][3];
+        mm3_bwd_dims(ni, nj, nk, nl, nm, dims);
+        size_t best = 0;
+        for (auto &d : dims) {
+            ContractPlan g;
+            contract_geometry(d[0], d[1], d[2], P, g);
+            best = std::max(best, contract_pack_bytes(g, P));
+        }
+        p.pack = w.take<char>(best);
+        plan_split_area(w, dims, MM3_BWD_N, P, p.split);
+    }
+}
+
 struct CovBwdPlan {
     double *mean = nullptr, *ss = nullptr, *partials = nullptr;
     float *hi = nullptr, *lo = nullptr, *rs = nullptr;
@@ -1175,6 +1211,54 @@ ln_status ln_3mm(int ni, int nj, int nk, int nl, int nm, const float *A, const f
     gG.bn = p.gG.bn;
     gG.epi = eg;
     return umma_contract(gG, P, st);
+}
+
+ln_status ln_3mm_bwd_workspace_size(int ni, int nj, int nk, int nl, int nm, ln_form form, ln_precision prec,
+                                    size_t *bytes) {
+    clear_error();
+    LN_TRY(check_dims({ni, nj, nk, nl, nm}));
+    LN_TRY(check_form(form, prec));
+    if (!bytes) return fail(LN_ERR_INVALID_VALUE, "NULL bytes");
+    Ws w(nullptr);
+    Mm3BwdPlan p;
+    plan_3mm_bwd(w, ni, nj, nk, nl, nm, form, prec, p);
+    *bytes = w.off;
+    return LN_SUCCESS;
+}
+
+ln_status ln_3mm_bwd(int ni, int nj, int nk, int nl, int nm, const float *A, const float *B, const float *C,
+                     const float *D, const float *Gb, float *dA, float *dB, float *dC, float *dD, void *ws,
+                     size_t wsb, ln_form form, ln_precision prec, void *stream) {
+    clear_error();
+    LN_TRY(check_dims({ni, nj, nk, nl, nm}));
+    LN_TRY(check_form(form, prec));
+    if (!A || !B || !C || !D || !Gb || !dA || !dB || !dC || !dD) return fail(LN_ERR_INVALID_VALUE, "NULL operand");
+    const Span outs[4] = {mspan(dA, ni, nk, nk), mspan(dB, nk, nj, nj), mspan(dC, nj, nm, nm), mspan(dD, nm, nl, nl)};
+    const Span ins[5] = {mspan(A, ni, nk, nk), mspan(B, nk, nj, nj), mspan(C, nj, nm, nm), mspan(D, nm, nl, nl),
+                         mspan(Gb, ni, nl, nl)};
+    for (int i = 0; i < 4; ++i) {
+        for (int j = i + 1; j < 4; ++j)
+            if (overlap(outs[i], outs[j])) return fail(LN_ERR_ALIASING, "gradient outputs overlap");
+        for (const Span &x : ins)
+            if (overlap(outs[i], x)) return fail(LN_ERR_ALIASING, "a gradient output overlaps an input");
+    }
+    Ws count(nullptr);
+    Mm3BwdPlan p;
+    plan_3mm_bwd(count, ni, nj, nk, nl, nm, form, prec, p);
+    LN_TRY(check_ws(ws, wsb, count.off));
+    Ws w(ws);
+    plan_3mm_bwd(w, ni, nj, nk, nl, nm, form, prec, p);
+    cudaStream_t st = S(stream);
+    char *pk = p.pack;
+    // Operand {p, ld, t}: t = 1 reads the stored matrix transposed
+    LN_TRY(contract_into(ni, nj, nk, {A, nk, 0}, {B, nj, 0}, epi_store(ni, nj, 1.0f, p.E, nj), form, prec, pk, p.split, st));
+    LN_TRY(contract_into(nj, nl, nm, {C, nm, 0}, {D, nl, 0}, epi_store(nj, nl, 1.0f, p.F, nl), form, prec, pk, p.split, st));
+    LN_TRY(contract_into(ni, nj, nl, {Gb, nl, 0}, {p.F, nl, 1}, epi_store(ni, nj, 1.0f, p.dE, nj), form, prec, pk, p.split, st));
+    LN_TRY(contract_into(nj, nl, ni, {p.E, nj, 1}, {Gb, nl, 0}, epi_store(nj, nl, 1.0f, p.dF, nl), form, prec, pk, p.split, st));
+    LN_TRY(contract_into(ni, nk, nj, {p.dE, nj, 0}, {B, nj, 1}, epi_store(ni, nk, 1.0f, dA, nk), form, prec, pk, p.split, st));
+    LN_TRY(contract_into(nk, nj, ni, {A, nk, 1}, {p.dE, nj, 0}, epi_store(nk, nj, 1.0f, dB, nj), form, prec, pk, p.split, st));
+    LN_TRY(contract_into(nj, nm, nl, {p.dF, nl, 0}, {D, nl, 1}, epi_store(nj, nm, 1.0f, dC, nm), form, prec, pk, p.split, st));
+    return contract_into(nm, nl, nj, {C, nm, 1}, {p.dF, nl, 0}, epi_store(nm, nl, 1.0f, dD, nl), form, prec, pk, p.split, st);
 }
 
 // ------------------------------------------------------------------ statistics, covariance, correlation

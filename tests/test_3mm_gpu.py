@@ -78,3 +78,28 @@ def test_3mm_empty_inner_and_host_operands(api):
     api.stream_check()
     assert not Gh.is_cuda and torch.equal(Gh, Gd.cpu())
     assert inputs.rel_fro(Gh.numpy(), oracle.three_mm(A, B, C, D)) <= GATE
+
+
+@pytest.mark.parametrize("form,prec", [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16"),
+                                       ("internalized", "6xbf16")])
+@pytest.mark.parametrize("ni,nj,nk,nl,nm", [(70, 129, 65, 90, 33), (1024, 1024, 1024, 1024, 1024)])
+def test_3mm_bwd(api, form, prec, ni, nj, nk, nl, nm):
+    if form == "plain" and ni > 512:
+        pytest.skip("plain form at the large size is slow and adds nothing")
+    A, B, C, D, Gb = uni((ni, nk), 21), uni((nk, nj), 22), uni((nj, nm), 23), uni((nm, nl), 24), uni((ni, nl), 25)
+    ref = oracle.three_mm_vjp(A, B, C, D, Gb)
+    got = api.three_mm_bwd(dev(A), dev(B), dev(C), dev(D), dev(Gb), form=form, prec=prec)
+    api.stream_check()
+    for g, r in zip(got, ref):
+        assert inputs.rel_fro(host(g), r) <= GATE
+
+
+def test_3mm_autograd(api):
+    A, B, C, D = (dev(uni(s, 30 + i)).requires_grad_(True) for i, s in
+                  enumerate([(96, 80), (80, 72), (72, 88), (88, 64)]))
+    W = dev(uni((96, 64), 35))
+    G = api.ThreeMmFn.apply(A, B, C, D, "internalized", "3xbf16")
+    (G * W).sum().backward()
+    ref = oracle.three_mm_vjp(*(host(t) for t in (A, B, C, D)), host(W))
+    for t, r in zip((A, B, C, D), ref):
+        assert inputs.rel_fro(host(t.grad), r) <= GATE

@@ -151,3 +151,18 @@ def test_3mm_validation_and_workspace(L):
     tile = 2 * 16384  # two split terms of a 128 x 64 tile
     expect = tile * (2 * 4 + 2 * 4 + 2 * 4 + 2 * 4 + 2 * 4 + 2 * 4)
     assert ws.value == expect
+
+
+def test_3mm_bwd_validation(L):
+    F = [0x7F0000000000 + i * 0x100000 for i in range(9)]
+    ws = ctypes.c_size_t(0)
+    assert L.ln_3mm_bwd(4, 4, 4, 4, 4, *(P(x) for x in F[:5]), None, P(F[6]), P(F[7]), P(F[8]), None, 0, 1, 2,
+                        None) == 1
+    # dB aliasing dA, and dD aliasing the upstream gradient
+    assert L.ln_3mm_bwd(8, 8, 8, 8, 8, *(P(x) for x in F[:5]), P(F[5]), P(F[5] + 64), P(F[7]), P(F[8]), None, 0,
+                        1, 2, None) == 2
+    assert L.ln_3mm_bwd(8, 8, 8, 8, 8, *(P(x) for x in F[:5]), P(F[5]), P(F[6]), P(F[7]), P(F[4]), None, 0, 1, 2,
+                        None) == 2
+    assert L.ln_3mm_bwd_workspace_size(100, 60, 70, 80, 90, 1, 0, ctypes.byref(ws)) == 0
+    up = lambda b: (b + 255) // 256 * 256
+    assert ws.value == 2 * (up(100 * 60 * 4) + up(60 * 80 * 4))
