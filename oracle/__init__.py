@@ -68,6 +68,7 @@ def _load():
         "oracle_covariance_vjp": (None, [i, i, P, P, P]),
         "oracle_correlation_vjp": (None, [i, i, P, P, P]),
         "oracle_cov_rows": (None, [i, i, P, i, i, P, P]),
+        "oracle_gramschmidt": (None, [i, i, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -228,3 +229,13 @@ def cov_rows(X, rows, corr=False):
     out = np.empty((len(r), m), np.float64)
     _load().oracle_cov_rows(n, m, _p(X), 1 if corr else 0, len(r), _p(r), _p(out))
     return out
+
+
+def gramschmidt(A):
+    """(Q, R) of modified Gram-Schmidt on A (m x n), polybench gramschmidt order."""
+    A = _f64(A)
+    m, n = A.shape
+    Q = np.empty((m, n), np.float64)
+    R = np.empty((n, n), np.float64)
+    _load().oracle_gramschmidt(m, n, _p(A), _p(Q), _p(R))
+    return Q, R

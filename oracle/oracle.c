@@ -3,7 +3,8 @@
  * and array-reduction detection (paper Sec. VI-B) speed up: GEMM, a chain of
  * two GEMMs (polybench 2mm), three chained products (polybench 3mm),
  * covariance, correlation, SYRK and SYR2K, plus the vector-Jacobian products of
- * the chain, 3mm, covariance and correlation.
+ * the chain, 3mm, covariance and correlation, and Gram-Schmidt QR (polybench
+ * gramschmidt).
  *
  * TEST INFRASTRUCTURE ONLY. This file is the plain definition of what the GPU
  * library computes, written as straightforward FP64 loops with no blocking, no
@@ -440,4 +441,41 @@ void oracle_cov_rows(int n, int m, const double *X, int corr, int nrows, const i
     }
     free(mean);
     free(ss);
+}
+
+/*
+ * Gram-Schmidt QR (polybench gramschmidt, paper Sec. VIII; the kernel whose
+ * candidate loop sits in a divergent region, Sec. VI-C and Sec. VIII). For
+ * the m x n matrix A, modified Gram-Schmidt one column at a time, with W a
+ * working copy of A that is overwritten as in the benchmark:
+ *   for k = 0 .. n-1:
+ *     R[k][k] = sqrt(sum_i W[i][k]^2)
+ *     Q[i][k] = W[i][k] / R[k][k]
+ *     for j = k+1 .. n-1:
+ *       R[k][j] = sum_i Q[i][k] * W[i][j]
+ *       W[i][j] = W[i][j] - Q[i][k] * R[k][j]
+ * Q is m x n, R is n x n with its strictly lower triangle set to zero.
+ * Reading where the benchmark would divide by zero: a column whose norm is
+ * exactly zero gets R[k][k] = 0 and a zero column of Q (so R[k][j] = 0 for
+ * j > k and the later columns are left as they are).
+ */
+void oracle_gramschmidt(int m, int n, const double *A, double *Q, double *R) {
+    double *W = (double *)malloc(sizeof(double) * (size_t)m * n + 1);
+    memcpy(W, A, sizeof(double) * (size_t)m * n);
+    memset(R, 0, sizeof(double) * (size_t)n * n);
+    for (int k = 0; k < n; ++k) {
+        double nrm = 0.0;
+        for (int i = 0; i < m; ++i) nrm += W[(size_t)i * n + k] * W[(size_t)i * n + k];
+        const double rkk = sqrt(nrm);
+        R[(size_t)k * n + k] = rkk;
+        for (int i = 0; i < m; ++i) Q[(size_t)i * n + k] = rkk > 0.0 ? W[(size_t)i * n + k] / rkk : 0.0;
+#pragma omp parallel for schedule(static)
+        for (int j = k + 1; j < n; ++j) {
+            double acc = 0.0;
+            for (int i = 0; i < m; ++i) acc += Q[(size_t)i * n + k] * W[(size_t)i * n + j];
+            R[(size_t)k * n + j] = acc;
+            for (int i = 0; i < m; ++i) W[(size_t)i * n + j] -= Q[(size_t)i * n + k] * acc;
+        }
+    }
+    free(W);
 }

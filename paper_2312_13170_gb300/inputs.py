@@ -22,6 +22,11 @@ row-major, as FP64, then cast to FP32):
 * ``backward`` X (n x m) = N(0,1) * scale_j, scale_j = exp(U[ln 0.1, ln 10])
              (order: scales, X), then W (m x m), A, B, C (p x p) ~ U[-1,1];
              4096 x 1024 and p = 1024.
+* ``gramschmidt`` A (m x n) ~ U[-1,1]; 1024 x 1024 in the benchmark (the
+             paper's polybench size). Square uniform matrices of this size have
+             a 2-norm condition number of a few thousand, so FP32 Gram-Schmidt
+             loses about that factor of orthogonality (tests scale their bound
+             for Q with it).
 
 These stand in for the polybench workloads of SYCL-Bench used in the paper's
 evaluation (Sec. VIII), whose sources and data are not part of this project:
@@ -125,3 +130,8 @@ def rel_fro(y, ref) -> float:
     den = float(np.linalg.norm(ref))
     num = float(np.linalg.norm(y - ref))
     return num / den if den > 0 else num
+
+
+def gramschmidt_inputs(m=1024, n=1024, seed=0):
+    rng = np.random.default_rng(seed)
+    return {"A": _u(rng, (m, n))}
