@@ -76,7 +76,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the CPU baseline sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
     ap.add_argument("--suite", action="store_true", help="measure every workload and form, one JSON line each")
-    ap.add_argument("--only", default="", help="suite: comma-separated workloads (gemm,chain,3mm,cov,batched,backward)")
+    ap.add_argument("--only", default="",
+                    help="suite: comma-separated workloads (gemm,chain,3mm,cov,batched,backward,gramschmidt)")
     ap.add_argument("--modes", default="", help="suite: comma-separated form/precision pairs, e.g. internalized/3xbf16")
     return ap.parse_args()
 
@@ -489,7 +490,8 @@ def run_suite(args):
              ("internalized", "6xbf16")]
     if args.modes:
         modes = [tuple(x.split("/")) for x in args.modes.split(",")]
-    only = set(args.only.split(",")) if args.only else {"gemm", "chain", "3mm", "cov", "batched", "backward"}
+    only = set(args.only.split(",")) if args.only else {"gemm", "chain", "3mm", "cov", "batched", "backward",
+                                                        "gramschmidt"}
     cores = oracle.max_threads()
 
     # -------------------------------------------------- GEMM 256^3
@@ -499,6 +501,7 @@ def run_suite(args):
     run_cov(only, modes, api, inputs, oracle, cores, time_it, emit, reps, hbm)
     run_batched(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
     run_backward(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
+    run_gramschmidt(only, api, inputs, oracle, cores, time_it, reps, fp32_peak)
     return 0
 
 
@@ -717,6 +720,46 @@ def main():
     if args.suite:
         return run_suite(args)
     return run_own(args)
+
+
+def run_gramschmidt(only, api, inputs, oracle, cores, time_it, reps, fp32_peak):
+    """Polybench Gram-Schmidt QR at the paper's size (1024 x 1024, U[-1,1]),
+    both forms, FP32. Flops as the loop nest counts them: per column k, 2m
+    for the norm, m for the scaling and 4m per later column."""
+    import torch
+
+    if "gramschmidt" not in only:
+        return
+    m = n = 1024
+    A = inputs.gramschmidt_inputs(m, n, seed=0)["A"]
+    t0 = time.perf_counter()
+    Qo, Ro = oracle.gramschmidt(A)
+    dt = time.perf_counter() - t0
+    flops = sum(3.0 * m + 4.0 * m * (n - k - 1) for k in range(n))
+    cpu = {"kind": "oracle", "cores": cores, "seconds": dt, "sample": "the whole 1024 x 1024 factorisation",
+           "gflops": flops / dt / 1e9}
+    kappa = float(np.linalg.cond(A.astype(np.float64)))
+    Ad = torch.from_numpy(A).cuda()
+    Q = torch.empty_like(Ad)
+    R = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    for form in ("plain", "internalized"):
+        api.gramschmidt(Ad, form=form, Q=Q, R=R)
+        errR = inputs.rel_fro(R.cpu().numpy(), Ro)
+        errQ = inputs.rel_fro(Q.cpu().numpy(), Qo)
+        ms = time_it(lambda: api.gramschmidt(Ad, form=form, Q=Q, R=R), n=3 if form == "plain" else reps)
+        gflops = flops / (ms[0] / 1e3) / 1e9
+        line = {"suite": True, "workload": "Gram-Schmidt QR 1024 x 1024 (modified, polybench order)",
+                "op": "gramschmidt", "form": form, "precision": "fp32",
+                "launch": "one CUDA graph replay per timed step, L2 flushed before each",
+                "launches_per_call": 3 * n if form == "plain" else 2 * ((n + 31) // 32) - 1,
+                "ms_median": ms[0], "ms_mean": ms[1], "gflops": gflops,
+                "bound": "latency",
+                "bound_note": "n dependent column steps, each a reduction over all m rows; "
+                              "the FP32 fraction below is of the whole GPU's FP32 rate",
+                "fp32_frac": gflops / 1e3 / fp32_peak,
+                "rel_err": errR, "rel_err_Q": errQ, "kappa": kappa, "Q_bound": max(1e-5, kappa * 2.0 ** -24),
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

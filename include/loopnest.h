@@ -138,7 +138,10 @@ ln_status ln_timing_read(const char *family, double *total_ms /*host*/, int *lau
  *   "split_k"  0 or 1 (default 0): split the K range of tensor-core
  *              contractions whose output tiles fill less than half the GPU
  *              (slices exchange FP32 partial sums through the workspace; the
- *              last slice of a tile to finish adds them in slice order).
+ *              last slice of a tile to finish adds them in slice order);
+ *   "gs_rows"  2 or 4 (default 4): rows of the matrix each thread holds in
+ *              registers in the internalized Gram-Schmidt panel kernel when
+ *              512 < m <= 1024 (512 or 256 threads per panel CTA).
  * A knob changes the workspace size of later calls: set it before the
  * *_workspace_size query of a call, not between the query and the call.
  * Unknown keys or values give LN_ERR_INVALID_VALUE. Not for use while kernels
@@ -293,6 +296,33 @@ ln_status ln_syr2k_batched_workspace_size(int count, const ln_sym_desc *h_descs 
 ln_status ln_syr2k_batched(ln_fill fill, int count, const ln_sym_desc *h_descs /*host*/,
                            const ln_sym_desc *d_descs, float alpha, float beta, void *workspace,
                            size_t workspace_bytes, ln_form form, ln_precision prec, void *stream);
+
+/*
+ * Gram-Schmidt QR (polybench gramschmidt, paper Sec. VIII; the kernel whose
+ * candidate loop lies in a divergent region, Sec. VI-C): modified
+ * Gram-Schmidt on A (m x n, lda), column by column in the benchmark's order,
+ *   R[k][k] = ||w_k||,  Q[:,k] = w_k / R[k][k],
+ *   R[k][j] = Q[:,k] . w_j,  w_j -= R[k][j] Q[:,k]   (j > k),
+ * with w the working columns (initially A). Outputs: Q (m x n, ldq) with
+ * orthonormal columns when A has full column rank, and R (n x n, ldr) upper
+ * triangular with R[k][k] >= 0 and zeros below the diagonal. A column whose
+ * norm is exactly zero gives R[k][k] = 0, a zero column of Q and a zero row
+ * of R. Arithmetic is FP32 (LN_PREC_FP32 only; the forward error of Q grows
+ * with the condition number of A, as for any Gram-Schmidt).
+ *
+ * LN_FORM_PLAIN runs the benchmark's three kernels per column (3n launches:
+ * a single work-item computes the norm, one work-item per row scales, one
+ * per later column projects). LN_FORM_INTERNALIZED factorises 32-column
+ * panels in one CTA each (rows held in registers for m <= 1024, in shared
+ * memory or L2 above) and applies each panel to the later columns in a
+ * second kernel (2 ceil(n/32) launches). No workspace: Q is the working
+ * array. A == Q with lda == ldq factorises in place (A is overwritten, as in
+ * the benchmark); otherwise Q must not overlap A, and R overlaps neither.
+ * Pointers are device memory, or pinned/managed host memory the GPU can reach
+ * (slow: every column step crosses the host link). Stream-ordered.
+ */
+ln_status ln_gramschmidt(int m, int n, const float *A, int lda, float *Q, int ldq, float *R, int ldr, ln_form form,
+                         void *stream);
 
 /*
  * Adjoint of 3mm (ln_3mm), G = (A B)(C D): given Gb = dL/dG (ni x nl), writes

@@ -69,6 +69,7 @@ _SIGS = {
     "ln_3mm_bwd": (_I, [_I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _I, _I, _P]),
     "ln_col_stats_workspace_size": (_I, [_I, _I, _I, _P]),
     "ln_col_stats": (_I, [_I, _I, _P, _I, _P, _P, _P, _SZ, _I, _P]),
+    "ln_gramschmidt": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _I, _P]),
     "ln_covariance_workspace_size": (_I, [_I, _I, _I, _I, _P]),
     "ln_covariance": (_I, [_I, _I, _P, _I, _P, _I, _P, _SZ, _I, _I, _P]),
     "ln_correlation": (_I, [_I, _I, _P, _I, _P, _I, _P, _SZ, _I, _I, _P]),
@@ -272,6 +273,33 @@ def three_mm(A, B, C, D, form="internalized", prec="3xbf16", stream=None, out=No
     _check(lib().ln_3mm(ni, nj, nk, nl, nm, _ptr(A), _ptr(B), _ptr(C), _ptr(D), _ptr(G), _ptr(ws), nb, fm, pr,
                         _stream(stream)), "ln_3mm")
     return G
+
+
+def gramschmidt(A, form="internalized", stream=None, Q=None, R=None, in_place=False):
+    """(Q, R) of modified Gram-Schmidt on A (m x n, polybench gramschmidt).
+
+    With in_place=True, A is overwritten by Q (the benchmark's semantics) and
+    returned as Q. Q and R may be given as preallocated outputs."""
+    _f32(A, "A")
+    m, n = A.shape
+    fm = _enum(FORMS, form, "form")
+    if in_place:
+        Q = A
+    elif Q is None:
+        Q = torch.empty((m, n), dtype=torch.float32, device=A.device)
+    else:
+        _f32(Q, "Q")
+        if tuple(Q.shape) != (m, n):
+            raise ValueError("Q must be m x n")
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float32, device=A.device)
+    else:
+        _f32(R, "R")
+        if tuple(R.shape) != (n, n):
+            raise ValueError("R must be n x n")
+    _check(lib().ln_gramschmidt(m, n, _ptr(A), _ld(A), _ptr(Q), _ld(Q), _ptr(R), _ld(R), fm, _stream(stream)),
+           "ln_gramschmidt")
+    return Q, R
 
 
 def col_stats(X, form="internalized", stream=None):

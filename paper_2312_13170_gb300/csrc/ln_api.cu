@@ -8,6 +8,7 @@
 #include <cstring>
 #include <vector>
 
+#include "ln_gs.h"
 #include "ln_internal.h"
 
 namespace ln {
@@ -79,12 +80,14 @@ std::atomic<int> g_chunk_kt{2};
 std::atomic<int> g_tile_n{0};
 std::atomic<int> g_pack_threads{512};
 std::atomic<int> g_split_k{0};
+std::atomic<int> g_gs_rows{4};
 }  // namespace
 
 int tune_chunk_kt() { return g_chunk_kt.load(std::memory_order_relaxed); }
 int tune_tile_n() { return g_tile_n.load(std::memory_order_relaxed); }
 int tune_pack_threads() { return g_pack_threads.load(std::memory_order_relaxed); }
 int tune_split_k() { return g_split_k.load(std::memory_order_relaxed); }
+int tune_gs_rows() { return g_gs_rows.load(std::memory_order_relaxed); }
 
 bool inject_timeout_requested() {
     const char *v = getenv("LN_FAULT_INJECT");
@@ -902,6 +905,11 @@ ln_status ln_set_tuning(const char *key, int value) {
         g_split_k.store(value);
         return LN_SUCCESS;
     }
+    if (strcmp(key, "gs_rows") == 0) {
+        if (value != 2 && value != 4) return fail(LN_ERR_INVALID_VALUE, "gs_rows must be 2 or 4 (got %d)", value);
+        g_gs_rows.store(value);
+        return LN_SUCCESS;
+    }
     if (strcmp(key, "pack_threads") == 0) {
         if (value != 512 && value != 1024)
             return fail(LN_ERR_INVALID_VALUE, "pack_threads must be 512 or 1024 (got %d)", value);
@@ -918,6 +926,7 @@ ln_status ln_get_tuning(const char *key, int *value) {
     else if (strcmp(key, "tile_n") == 0) *value = g_tile_n.load();
     else if (strcmp(key, "pack_threads") == 0) *value = g_pack_threads.load();
     else if (strcmp(key, "split_k") == 0) *value = g_split_k.load();
+    else if (strcmp(key, "gs_rows") == 0) *value = g_gs_rows.load();
     else return fail(LN_ERR_INVALID_VALUE, "unknown tuning key '%s'", key);
     return LN_SUCCESS;
 }
@@ -1459,6 +1468,31 @@ ln_status ln_correlation_bwd(int nsamples, int nfeat, const float *X, int ldx, c
                              ln_precision prec, void *stream) {
     clear_error();
     return run_cov_bwd(true, nsamples, nfeat, X, ldx, W, ldw, stats, dX, lddx, ws, wsb, form, prec, S(stream));
+}
+
+ln_status ln_gramschmidt(int m, int n, const float *A, int lda, float *Q, int ldq, float *R, int ldr, ln_form form,
+                         void *stream) {
+    clear_error();
+    LN_TRY(check_dims({m, n}));
+    LN_TRY(check_form(form, LN_PREC_FP32));
+    if (n == 0) return LN_SUCCESS;
+    if (!R || (m > 0 && (!A || !Q))) return fail(LN_ERR_INVALID_VALUE, "NULL operand");
+    if (lda < n || ldq < n || ldr < n) return fail(LN_ERR_INVALID_VALUE, "a leading dimension is smaller than n");
+    const bool in_place = m > 0 && A == Q && lda == ldq;
+    const Span sa = mspan(A, m, n, lda), sq = mspan(Q, m, n, ldq), sr = mspan(R, n, n, ldr);
+    if (!in_place && overlap(sa, sq))
+        return fail(LN_ERR_ALIASING, "A and Q overlap (only A == Q with lda == ldq, in place, is allowed)");
+    if (overlap(sr, sa) || overlap(sr, sq)) return fail(LN_ERR_ALIASING, "R overlaps A or Q");
+    LN_TRY(device_view(R, &R, "R"));
+    if (m > 0) {
+        LN_TRY(device_view(A, &A, "A"));
+        LN_TRY(device_view(Q, &Q, "Q"));
+    }
+    cudaStream_t st = S(stream);
+    if (m > 0 && !in_place)
+        LN_CUDA_TRY(cudaMemcpy2DAsync(Q, (size_t)ldq * 4, A, (size_t)lda * 4, (size_t)n * 4, (size_t)m,
+                                      cudaMemcpyDefault, st));
+    return form == LN_FORM_PLAIN ? gs_plain(m, n, Q, ldq, R, ldr, st) : gs_blocked(m, n, Q, ldq, R, ldr, st);
 }
 
 }  // extern "C"

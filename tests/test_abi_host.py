@@ -166,3 +166,23 @@ def test_3mm_bwd_validation(L):
     assert L.ln_3mm_bwd_workspace_size(100, 60, 70, 80, 90, 1, 0, ctypes.byref(ws)) == 0
     up = lambda b: (b + 255) // 256 * 256
     assert ws.value == 2 * (up(100 * 60 * 4) + up(60 * 80 * 4))
+
+
+def test_gramschmidt_validation(L):
+    FA, FQ, FR = 0x7F0000000000, 0x7F0000100000, 0x7F0000200000
+    # negative size, unknown form, NULL operand, leading dimension below n
+    assert L.ln_gramschmidt(-1, 4, P(FA), 4, P(FQ), 4, P(FR), 4, 1, None) == 1
+    assert L.ln_gramschmidt(4, 4, P(FA), 4, P(FQ), 4, P(FR), 4, 5, None) == 1
+    assert L.ln_gramschmidt(4, 4, P(FA), 4, P(FQ), 4, None, 4, 1, None) == 1
+    assert "NULL" in last(L)
+    assert L.ln_gramschmidt(4, 4, P(FA), 3, P(FQ), 4, P(FR), 4, 1, None) == 1
+    # Q overlapping A other than exactly in place, R overlapping Q
+    assert L.ln_gramschmidt(8, 8, P(FA), 8, P(FA + 64), 8, P(FR), 8, 1, None) == 2
+    assert L.ln_gramschmidt(8, 8, P(FA), 8, P(FA), 9, P(FR), 8, 0, None) == 2
+    assert L.ln_gramschmidt(8, 8, P(FA), 8, P(FQ), 8, P(FQ + 32), 8, 1, None) == 2
+    # n == 0 is a no-op
+    assert L.ln_gramschmidt(5, 0, None, 0, None, 0, None, 0, 1, None) == 0
+    # tuning knob
+    v = ctypes.c_int(0)
+    assert L.ln_get_tuning(b"gs_rows", ctypes.byref(v)) == 0 and v.value == 4
+    assert L.ln_set_tuning(b"gs_rows", 3) == 1
