@@ -43,6 +43,13 @@ constexpr int GS_BW = 32;    // panel width (columns)
 constexpr int GS_CB = 8;     // later columns per CTA of the trailing update
 constexpr int GS_UNT = 256;  // threads of the trailing update
 constexpr int GS_PAD = 33;   // shared-memory row stride of a panel held in shared memory
+constexpr int GS_TS = 36;    // row stride (floats) of the register-resident panel's tile
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
 
 // ------------------------------------------------------------------ plain form
 __global__ void k_gs_norm(int m, int k, const float *Q, long long ldq, float *R, long long ldr) {
@@ -125,108 +132,161 @@ __device__ __forceinline__ float gs_reduce(float (&v)[32], int c, int bw, int p0
     return r;
 }
 
-// Zero the strictly lower part of the panel's rows of R (columns < k).
-__device__ __forceinline__ void gs_zero_lower(int p0, int bw, float *R, long long ldr, int nt) {
-    for (int c = 0; c < bw; ++c)
-        for (int j = threadIdx.x; j < p0 + c; j += nt) R[(long long)(p0 + c) * ldr + j] = 0.f;
-}
-
-// One column step of the register-resident panel. Slot 0 of w holds the
-// current column k = p0 + c of this thread's rows, slot j the column k + j;
-// slots >= WD are zero. The squared norm and the dot products with the later
-// columns come out of one CTA-wide reduction; the normalised column goes to
-// column c of the shared-memory tile qs (column-major, stride S*NT + 1) and
-// the later columns, after removing their projection, move down one slot, so
-// the next column is again in slot 0 and every register index is a constant.
-template <int S, int NT, int WD>
-__device__ __forceinline__ void gs_reg_step(float (&w)[S][GS_BW], int c, int bw, int p0, float *qs, float *R,
-                                            long long ldr, float (*red)[NT / 32][32], float (*rcs)[32]) {
-    constexpr int NW = NT / 32;
+// One column step of the register-resident panel. w holds this thread's
+// rows as 16 pairs of slots; the current column k = p0 + c sits in slot PH
+// (= c & 1) and slot j holds column k - PH + j; slots >= WD are zero, as is
+// everything before the current slot that still matters. The squared norm
+// and the dot products with the later columns come out of one CTA-wide
+// reduction (packed FP32x2 multiply-adds, then warp_reduce_cols and one
+// barrier); the normalised column goes to column c of the shared-memory tile
+// and the later columns lose their projection. After a PH = 1 step every
+// pair moves down one place, so the next column is again in slot 0 and every
+// register index is a constant.
+template <int S, int NT, int WD, int PH>
+__device__ __forceinline__ void gs_reg_step(float2 (&w)[S][GS_BW / 2], int c, int bw, int p0, float *tile,
+                                            float *R, long long ldr, float (*red)[NT / 32][32], float (*rcs)[32]) {
+    constexpr int NW = NT / 32, NP = WD / 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float v[WD];
+    float2 v2[NP];
 #pragma unroll
-    for (int j = 0; j < WD; ++j) v[j] = 0.f;
+    for (int p = 0; p < NP; ++p) v2[p] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        const float x = w[s][0];
+        const float x = PH ? w[s][0].y : w[s][0].x;
+        const float2 x2 = make_float2(x, x);
+        if (PH == 0) v2[0] = __ffma2_rn(x2, w[s][0], v2[0]);
+        else v2[0].y = fmaf(x, x, v2[0].y);
 #pragma unroll
-        for (int j = 0; j < WD; ++j) v[j] = fmaf(x, w[s][j], v[j]);
+        for (int p = 1; p < NP; ++p) v2[p] = __ffma2_rn(x2, w[s][p], v2[p]);
     }
-    warp_reduce_cols<WD>(v, lane);
+    float v[WD];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        v[2 * p] = v2[p].x;
+        v[2 * p + 1] = v2[p].y;
+    }
+    warp_reduce_cols<WD>(v, lane);  // lane l: the warp's total for slot l % WD
     float(*rb)[32] = red[c & 1];
     rb[warp][lane] = v[0];
     __syncthreads();
-    float tot = 0.f;
+    float part[NW];
 #pragma unroll
-    for (int q = 0; q < NW; ++q) tot += rb[q][lane];
-    const float r = __fsqrt_rn(__shfl_sync(0xffffffffu, tot, 0));
-    const float inv = r > 0.f ? __frcp_rn(r) : 0.f;
-    const float rc = tot * inv;  // R[k][k + lane % WD] for lane % WD > 0
-    if (warp == 0 && lane < WD && c + lane < bw) R[(long long)(p0 + c) * ldr + p0 + c + lane] = lane == 0 ? r : rc;
-    rcs[warp][lane] = rc;
+    for (int q = 0; q < NW; ++q) part[q] = rb[q][lane];
+#pragma unroll
+    for (int h = 1; h < NW; h <<= 1)  // fixed pairwise tree: the same in every warp
+#pragma unroll
+        for (int q = 0; q + h < NW; q += 2 * h) part[q] += part[q + h];
+    const float tot = part[0];
+    const float nrm2 = __shfl_sync(0xffffffffu, tot, PH);
+    const float r = __fsqrt_rn(nrm2);
+    const float inv = nrm2 > 0.f ? __frsqrt_rn(nrm2) : 0.f;
+    const float rc = tot * inv;  // R[k][k + l - PH] for slot l > PH
+    if (warp == 0 && lane >= PH && lane < WD && c + lane - PH < bw)
+        R[(long long)(p0 + c) * ldr + p0 + c + lane - PH] = lane == PH ? r : rc;
+    rcs[warp][lane] = -rc;
     __syncwarp();
-    float rr[WD];
+    float nr[WD];
     const float4 *r4 = reinterpret_cast<const float4 *>(rcs[warp]);
 #pragma unroll
     for (int g = 0; g < WD / 4; ++g) {
         const float4 t = r4[g];
-        rr[4 * g] = t.x;
-        rr[4 * g + 1] = t.y;
-        rr[4 * g + 2] = t.z;
-        rr[4 * g + 3] = t.w;
+        nr[4 * g] = t.x;
+        nr[4 * g + 1] = t.y;
+        nr[4 * g + 2] = t.z;
+        nr[4 * g + 3] = t.w;
     }
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        const float q = w[s][0] * inv;
-        qs[c * (S * NT + 1) + tid + s * NT] = q;
+        const float q = (PH ? w[s][0].y : w[s][0].x) * inv;
+        tile[(tid + s * NT) * GS_TS + c] = q;
+        const float2 q2 = make_float2(q, q);
+        if (PH == 0) {
+            w[s][0].y = fmaf(nr[1], q, w[s][0].y);
 #pragma unroll
-        for (int j = 1; j < WD; ++j) w[s][j - 1] = fmaf(-rr[j], q, w[s][j]);
-        w[s][WD - 1] = 0.f;
+            for (int p = 1; p < NP; ++p) w[s][p] = __ffma2_rn(make_float2(nr[2 * p], nr[2 * p + 1]), q2, w[s][p]);
+        } else {
+#pragma unroll
+            for (int p = 1; p < NP; ++p)
+                w[s][p - 1] = __ffma2_rn(make_float2(nr[2 * p], nr[2 * p + 1]), q2, w[s][p]);
+            w[s][NP - 1] = make_float2(0.f, 0.f);
+        }
     }
 }
 
+template <int S, int NT, int PH>
+__device__ __forceinline__ void gs_reg_step_any(float2 (&w)[S][GS_BW / 2], int c, int bw, int p0, float *tile,
+                                                float *R, long long ldr, float (*red)[NT / 32][32],
+                                                float (*rcs)[32]) {
+    const int need = PH + bw - c;  // slots the step must cover
+    if (need > 16) gs_reg_step<S, NT, 32, PH>(w, c, bw, p0, tile, R, ldr, red, rcs);
+    else if (need > 8) gs_reg_step<S, NT, 16, PH>(w, c, bw, p0, tile, R, ldr, red, rcs);
+    else gs_reg_step<S, NT, 8, PH>(w, c, bw, p0, tile, R, ldr, red, rcs);
+}
+
 // Panel of up to 32 columns, rows in registers: thread t holds rows t + s*NT
-// (s < S). The panel goes from Q to registers and back through a
-// column-major shared-memory tile (coalesced global accesses both ways). The
-// column loop is a runtime loop over gs_reg_step; the step's width drops to
-// 16 and then 8 slots once that many columns remain.
+// (s < S). The panel comes into a row-major shared-memory tile (row stride
+// GS_TS) by 16-byte asynchronous copies (plain loads when rows are not
+// 16-byte aligned), goes to registers, and the normalised columns go back to
+// the tile and out to Q with 16-byte stores.
 template <int S, int NT>
 __host__ __device__ constexpr size_t gs_panel_smem() {
-    return (size_t)GS_BW * (S * NT + 1) * sizeof(float);
+    return (size_t)S * NT * GS_TS * sizeof(float);
 }
 
 template <int S, int NT>
 __global__ void __launch_bounds__(NT, 1)
-    k_gs_panel_reg(int m, int p0, int bw, float *Q, long long ldq, float *R, long long ldr) {
-    constexpr int LD = S * NT + 1;  // column stride of the tile
-    extern __shared__ __align__(16) float qs[];
+    k_gs_panel_reg(int m, int p0, int bw, float *Q, long long ldq, float *R, long long ldr, int vec) {
+    extern __shared__ __align__(16) float tile[];
     __shared__ float red[2][NT / 32][32];
     __shared__ __align__(16) float rcs[NT / 32][32];
     const int tid = threadIdx.x;
-    // S * 32 loads per thread, unrolled so that many are in flight at once
+    if (vec) {
+#pragma unroll 8
+        for (int it = 0; it < S * 8; ++it) {
+            const int e = tid + it * NT, i = e / 8, k = e % 8;
+            const int valid = i < m ? min(max(bw - 4 * k, 0), 4) : 0;
+            const float *src = valid ? Q + (long long)i * ldq + p0 + 4 * k : Q;
+            cp_async16(tile + i * GS_TS + 4 * k, src, 4 * valid);
+        }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    } else {
 #pragma unroll 32
-    for (int it = 0; it < S * GS_BW; ++it) {
-        const int e = tid + it * NT, i = e / GS_BW, j = e % GS_BW;
-        qs[j * LD + i] = (i < m && j < bw) ? Q[(long long)i * ldq + p0 + j] : 0.f;
+        for (int it = 0; it < S * GS_BW; ++it) {
+            const int e = tid + it * NT, i = e / GS_BW, j = e % GS_BW;
+            tile[i * GS_TS + j] = (i < m && j < bw) ? Q[(long long)i * ldq + p0 + j] : 0.f;
+        }
     }
     __syncthreads();
-    float w[S][GS_BW];
+    float2 w[S][GS_BW / 2];
 #pragma unroll
-    for (int s = 0; s < S; ++s)
+    for (int s = 0; s < S; ++s) {
+        const float4 *row = reinterpret_cast<const float4 *>(tile + (tid + s * NT) * GS_TS);
 #pragma unroll
-        for (int j = 0; j < GS_BW; ++j) w[s][j] = qs[j * LD + tid + s * NT];
+        for (int g = 0; g < GS_BW / 4; ++g) {
+            const float4 t = row[g];
+            w[s][2 * g] = make_float2(t.x, t.y);
+            w[s][2 * g + 1] = make_float2(t.z, t.w);
+        }
+    }
     // between the two barriers each thread reads and rewrites only its own rows of the tile
-    int c = 0;
-    for (; c < bw && bw - c > 16; ++c) gs_reg_step<S, NT, 32>(w, c, bw, p0, qs, R, ldr, red, rcs);
-    for (; c < bw && bw - c > 8; ++c) gs_reg_step<S, NT, 16>(w, c, bw, p0, qs, R, ldr, red, rcs);
-    for (; c < bw; ++c) gs_reg_step<S, NT, 8>(w, c, bw, p0, qs, R, ldr, red, rcs);
+    for (int c = 0; c < bw; ++c) {
+        if (c & 1) gs_reg_step_any<S, NT, 1>(w, c, bw, p0, tile, R, ldr, red, rcs);
+        else gs_reg_step_any<S, NT, 0>(w, c, bw, p0, tile, R, ldr, red, rcs);
+    }
     __syncthreads();
 #pragma unroll 8
-    for (int it = 0; it < S * GS_BW; ++it) {
-        const int e = tid + it * NT, i = e / GS_BW, j = e % GS_BW;
-        if (i < m && j < bw) Q[(long long)i * ldq + p0 + j] = qs[j * LD + i];
+    for (int it = 0; it < S * 8; ++it) {
+        const int e = tid + it * NT, i = e / 8, k = e % 8;
+        if (i >= m || 4 * k >= bw) continue;
+        const float4 t = *reinterpret_cast<const float4 *>(tile + i * GS_TS + 4 * k);
+        float *dst = Q + (long long)i * ldq + p0 + 4 * k;
+        if (vec && 4 * k + 4 <= bw) {
+            *reinterpret_cast<float4 *>(dst) = t;
+        } else {
+            const float tv[4] = {t.x, t.y, t.z, t.w};
+            for (int q = 0; q < 4 && 4 * k + q < bw; ++q) dst[q] = tv[q];
+        }
     }
-    gs_zero_lower(p0, bw, R, ldr, NT);
 }
 
 // Panel of up to 32 columns for matrices taller than the register-resident
@@ -282,7 +342,6 @@ __global__ void __launch_bounds__(NT, 1)
             if (j < bw) Q[(long long)i * ldq + p0 + j] = pan[(long long)i * GS_PAD + j];
         }
     }
-    gs_zero_lower(p0, bw, R, ldr, NT);
 }
 
 // ------------------------------------------------------------------ trailing update
@@ -291,12 +350,6 @@ constexpr int GS_QP = 36;     // shared-memory row stride (floats) of staged pan
 
 __host__ __device__ constexpr size_t gs_update_smem(int m) {
     return (size_t)(m < GS_URC ? m : GS_URC) * (GS_QP + GS_CB) * sizeof(float);
-}
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src), "r"(src_bytes)
-                 : "memory");
 }
 
 // Stage rows i0 .. i0+nr-1 of the panel (32 floats each, stride GS_QP) and of
@@ -347,28 +400,31 @@ __global__ void __launch_bounds__(GS_UNT, 1)
     const int tid = threadIdx.x, g = tid / GS_CB, jj = tid % GS_CB;
     const int j0 = p1 + blockIdx.x * GS_CB, j = j0 + jj;
     const int ncols = min(GS_CB, n - j0);
-    float acc[GS_BW];
+    float2 acc[GS_BW / 2];
 #pragma unroll
-    for (int a = 0; a < GS_BW; ++a) acc[a] = 0.f;
+    for (int a = 0; a < GS_BW / 2; ++a) acc[a] = make_float2(0.f, 0.f);
     for (int i0 = 0; i0 < m; i0 += GS_URC) {
         const int nr = min(GS_URC, m - i0);
         if (i0 > 0) __syncthreads();  // the previous chunk is no longer read
         gs_stage(Q, ldq, p0, j0, ncols, i0, nr, Qs, Ws, vec != 0);
+#pragma unroll 2
         for (int i = g; i < nr; i += NG) {
             const float4 *q4 = reinterpret_cast<const float4 *>(Qs + i * GS_QP);
             const float x = Ws[i * GS_CB + jj];
+            const float2 x2 = make_float2(x, x);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const float4 t = q4[k];
-                acc[4 * k] = fmaf(t.x, x, acc[4 * k]);
-                acc[4 * k + 1] = fmaf(t.y, x, acc[4 * k + 1]);
-                acc[4 * k + 2] = fmaf(t.z, x, acc[4 * k + 2]);
-                acc[4 * k + 3] = fmaf(t.w, x, acc[4 * k + 3]);
+                acc[2 * k] = __ffma2_rn(make_float2(t.x, t.y), x2, acc[2 * k]);
+                acc[2 * k + 1] = __ffma2_rn(make_float2(t.z, t.w), x2, acc[2 * k + 1]);
             }
         }
     }
 #pragma unroll
-    for (int a = 0; a < GS_BW; ++a) red[g][jj][a] = acc[a];
+    for (int a = 0; a < GS_BW / 2; ++a) {
+        red[g][jj][2 * a] = acc[a].x;
+        red[g][jj][2 * a + 1] = acc[a].y;
+    }
     __syncthreads();
     for (int o = tid; o < GS_BW * GS_CB; o += GS_UNT) {
         const int a = o / GS_CB, cc = o % GS_CB;
@@ -379,9 +435,9 @@ __global__ void __launch_bounds__(GS_UNT, 1)
         if (cc < ncols) R[(long long)(p0 + a) * ldr + j0 + cc] = s;
     }
     __syncthreads();
-    float rr[GS_BW];
+    float2 rr[GS_BW / 2];
 #pragma unroll
-    for (int a = 0; a < GS_BW; ++a) rr[a] = Rs[a][jj];
+    for (int a = 0; a < GS_BW / 2; ++a) rr[a] = make_float2(Rs[2 * a][jj], Rs[2 * a + 1][jj]);
     // the last staged chunk is still in shared memory: walk the chunks backwards
     for (int i0 = ((m - 1) / GS_URC) * GS_URC; i0 >= 0; i0 -= GS_URC) {
         const int nr = min(GS_URC, m - i0);
@@ -390,17 +446,23 @@ __global__ void __launch_bounds__(GS_UNT, 1)
             gs_stage(Q, ldq, p0, j0, ncols, i0, nr, Qs, Ws, vec != 0);
         }
         if (jj < ncols) {
+#pragma unroll 2
             for (int i = g; i < nr; i += NG) {
                 const float4 *q4 = reinterpret_cast<const float4 *>(Qs + i * GS_QP);
-                float s = 0.f;
+                // sum_a Q[i][a] R[a][j] as four interleaved partial sums (even/odd a, two halves)
+                float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const float4 t = q4[k];
-                    s = fmaf(t.x, rr[4 * k], s);
-                    s = fmaf(t.y, rr[4 * k + 1], s);
-                    s = fmaf(t.z, rr[4 * k + 2], s);
-                    s = fmaf(t.w, rr[4 * k + 3], s);
+                    if (k < 4) {
+                        s0 = __ffma2_rn(make_float2(t.x, t.y), rr[2 * k], s0);
+                        s0 = __ffma2_rn(make_float2(t.z, t.w), rr[2 * k + 1], s0);
+                    } else {
+                        s1 = __ffma2_rn(make_float2(t.x, t.y), rr[2 * k], s1);
+                        s1 = __ffma2_rn(make_float2(t.z, t.w), rr[2 * k + 1], s1);
+                    }
                 }
+                const float s = (s0.x + s0.y) + (s1.x + s1.y);
                 Q[(long long)(i0 + i) * ldq + j] = Ws[i * GS_CB + jj] - s;
             }
         }
@@ -437,10 +499,9 @@ ln_status gs_plain(int m, int n, float *Q, long long ldq, float *R, long long ld
 
 ln_status gs_blocked(int m, int n, float *Q, long long ldq, float *R, long long ldr, cudaStream_t st) {
     if (n == 0) return LN_SUCCESS;
-    if (m == 0) {
-        LN_CUDA_TRY(cudaMemset2DAsync(R, (size_t)ldr * 4, 0, (size_t)n * 4, (size_t)n, st));
-        return LN_SUCCESS;
-    }
+    // the kernels write R on and above the diagonal; zero the whole of it first
+    LN_CUDA_TRY(cudaMemset2DAsync(R, (size_t)ldr * 4, 0, (size_t)n * 4, (size_t)n, st));
+    if (m == 0) return LN_SUCCESS;
     const int vec = (reinterpret_cast<uintptr_t>(Q) % 16 == 0 && ldq % 4 == 0) ? 1 : 0;
     // tall panels: shared memory when the 33-float rows fit beside the static arrays
     const size_t mem_bytes = (size_t)m * GS_PAD * sizeof(float);
@@ -462,11 +523,11 @@ ln_status gs_blocked(int m, int n, float *Q, long long ldq, float *R, long long 
         {
             LaunchScope ls_(FAM_SIMT, st);
             if (m <= 512)
-                k_gs_panel_reg<2, 256><<<1, 256, gs_panel_smem<2, 256>(), st>>>(m, p0, bw, Q, ldq, R, ldr);
+                k_gs_panel_reg<2, 256><<<1, 256, gs_panel_smem<2, 256>(), st>>>(m, p0, bw, Q, ldq, R, ldr, vec);
             else if (m <= 1024 && rows == 2)
-                k_gs_panel_reg<2, 512><<<1, 512, gs_panel_smem<2, 512>(), st>>>(m, p0, bw, Q, ldq, R, ldr);
+                k_gs_panel_reg<2, 512><<<1, 512, gs_panel_smem<2, 512>(), st>>>(m, p0, bw, Q, ldq, R, ldr, vec);
             else if (m <= 1024)
-                k_gs_panel_reg<4, 256><<<1, 256, gs_panel_smem<4, 256>(), st>>>(m, p0, bw, Q, ldq, R, ldr);
+                k_gs_panel_reg<4, 256><<<1, 256, gs_panel_smem<4, 256>(), st>>>(m, p0, bw, Q, ldq, R, ldr, vec);
             else
                 k_gs_panel_mem<GS_MEM_NT><<<1, GS_MEM_NT, in_smem ? mem_bytes : 0, st>>>(m, p0, bw, Q, ldq, R, ldr,
                                                                                       in_smem);
