@@ -501,7 +501,7 @@ def run_suite(args):
     run_cov(only, modes, api, inputs, oracle, cores, time_it, emit, reps, hbm)
     run_batched(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
     run_backward(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
-    run_gramschmidt(only, api, inputs, oracle, cores, time_it, reps, fp32_peak)
+    run_gramschmidt(only, modes, api, inputs, oracle, cores, time_it, reps, fp32_peak)
     return 0
 
 
@@ -722,13 +722,14 @@ def main():
     return run_own(args)
 
 
-def run_gramschmidt(only, api, inputs, oracle, cores, time_it, reps, fp32_peak):
+def run_gramschmidt(only, modes, api, inputs, oracle, cores, time_it, reps, fp32_peak):
     """Polybench Gram-Schmidt QR at the paper's size (1024 x 1024, U[-1,1]),
-    both forms, FP32. Flops as the loop nest counts them: per column k, 2m
-    for the norm, m for the scaling and 4m per later column."""
+    the FP32 forms among `modes`. Flops as the loop nest counts them: per
+    column k, 2m for the norm, m for the scaling and 4m per later column."""
     import torch
 
-    if "gramschmidt" not in only:
+    forms = [f for f, p in modes if p == "fp32"]
+    if "gramschmidt" not in only or not forms:
         return
     m = n = 1024
     A = inputs.gramschmidt_inputs(m, n, seed=0)["A"]
@@ -742,7 +743,7 @@ def run_gramschmidt(only, api, inputs, oracle, cores, time_it, reps, fp32_peak):
     Ad = torch.from_numpy(A).cuda()
     Q = torch.empty_like(Ad)
     R = torch.empty((n, n), dtype=torch.float32, device="cuda")
-    for form in ("plain", "internalized"):
+    for form in forms:
         api.gramschmidt(Ad, form=form, Q=Q, R=R)
         errR = inputs.rel_fro(R.cpu().numpy(), Ro)
         errQ = inputs.rel_fro(Q.cpu().numpy(), Qo)
