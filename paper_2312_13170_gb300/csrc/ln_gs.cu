@@ -26,6 +26,7 @@
 
 #include <cstdint>
 
+#include "ln_async.cuh"
 #include "ln_gs.h"
 #include "ln_internal.h"
 
@@ -240,6 +241,9 @@ __global__ void __launch_bounds__(NT, 1)
     __shared__ float red[2][NT / 32][32];
     __shared__ __align__(16) float rcs[NT / 32][32];
     const int tid = threadIdx.x;
+    // launched programmatically after the previous update: Q only after it has completed
+    pdl_wait();
+    pdl_trigger();
     if (vec) {
 #pragma unroll 8
         for (int it = 0; it < S * 8; ++it) {
@@ -300,6 +304,8 @@ __global__ void __launch_bounds__(NT, 1)
     __shared__ float red[2][NW][32];
     __shared__ __align__(16) float rcs[NW][32];
     const int tid = threadIdx.x, warp = tid >> 5;
+    pdl_wait();
+    pdl_trigger();
     float *P = Q + p0;
     long long ldp = ldq;
     if (in_smem) {
@@ -400,6 +406,9 @@ __global__ void __launch_bounds__(GS_UNT, 1)
     const int tid = threadIdx.x, g = tid / GS_CB, jj = tid % GS_CB;
     const int j0 = p1 + blockIdx.x * GS_CB, j = j0 + jj;
     const int ncols = min(GS_CB, n - j0);
+    // launched programmatically after the panel: its Q and R only after it has completed
+    pdl_wait();
+    pdl_trigger();
     float2 acc[GS_BW / 2];
 #pragma unroll
     for (int a = 0; a < GS_BW / 2; ++a) acc[a] = make_float2(0.f, 0.f);
@@ -474,6 +483,27 @@ constexpr int GS_MEM_NT = 512;
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
+// Launch with programmatic stream serialisation: the kernel's CTAs may start
+// while its predecessor in the stream finishes, and wait for it in
+// griddepcontrol.wait before touching memory.
+template <class... KArgs, class... Args>
+ln_status gs_launch(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                    const char *what, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+    if (e != cudaSuccess) return fail(LN_ERR_CUDA, "%s launch: %s", what, cudaGetErrorString(e));
+    return check_launch(what);
+}
+
 ln_status gs_plain(int m, int n, float *Q, long long ldq, float *R, long long ldr, cudaStream_t st) {
     for (int k = 0; k < n; ++k) {
         {
@@ -522,25 +552,27 @@ ln_status gs_blocked(int m, int n, float *Q, long long ldq, float *R, long long 
         const int bw = n - p0 < GS_BW ? n - p0 : GS_BW;
         {
             LaunchScope ls_(FAM_SIMT, st);
+            ln_status ps;
             if (m <= 512)
-                k_gs_panel_reg<2, 256><<<1, 256, gs_panel_smem<2, 256>(), st>>>(m, p0, bw, Q, ldq, R, ldr, vec);
+                ps = gs_launch(k_gs_panel_reg<2, 256>, 1, 256, gs_panel_smem<2, 256>(), st, "k_gs_panel", m, p0, bw, Q,
+                               ldq, R, ldr, vec);
             else if (m <= 1024 && rows == 2)
-                k_gs_panel_reg<2, 512><<<1, 512, gs_panel_smem<2, 512>(), st>>>(m, p0, bw, Q, ldq, R, ldr, vec);
+                ps = gs_launch(k_gs_panel_reg<2, 512>, 1, 512, gs_panel_smem<2, 512>(), st, "k_gs_panel", m, p0, bw, Q,
+                               ldq, R, ldr, vec);
             else if (m <= 1024)
-                k_gs_panel_reg<4, 256><<<1, 256, gs_panel_smem<4, 256>(), st>>>(m, p0, bw, Q, ldq, R, ldr, vec);
+                ps = gs_launch(k_gs_panel_reg<4, 256>, 1, 256, gs_panel_smem<4, 256>(), st, "k_gs_panel", m, p0, bw, Q,
+                               ldq, R, ldr, vec);
             else
-                k_gs_panel_mem<GS_MEM_NT><<<1, GS_MEM_NT, in_smem ? mem_bytes : 0, st>>>(m, p0, bw, Q, ldq, R, ldr,
-                                                                                      in_smem);
+                ps = gs_launch(k_gs_panel_mem<GS_MEM_NT>, 1, GS_MEM_NT, in_smem ? mem_bytes : 0, st, "k_gs_panel", m,
+                               p0, bw, Q, ldq, R, ldr, in_smem);
+            if (ps != LN_SUCCESS) return ps;
         }
-        LN_TRY_LAUNCH("k_gs_panel");
         const int p1 = p0 + bw;
         if (p1 < n) {
-            {
-                LaunchScope ls_(FAM_SIMT, st);
-                k_gs_update<<<(unsigned)ceil_div(n - p1, GS_CB), GS_UNT, gs_update_smem(m), st>>>(m, n, p0, p1, Q, ldq,
-                                                                                                R, ldr, vec);
-            }
-            LN_TRY_LAUNCH("k_gs_update");
+            LaunchScope ls_(FAM_SIMT, st);
+            const ln_status us = gs_launch(k_gs_update, (unsigned)ceil_div(n - p1, GS_CB), GS_UNT, gs_update_smem(m), st,
+                                           "k_gs_update", m, n, p0, p1, Q, ldq, R, ldr, vec);
+            if (us != LN_SUCCESS) return us;
         }
     }
     return LN_SUCCESS;
