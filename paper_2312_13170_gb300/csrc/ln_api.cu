@@ -10,6 +10,7 @@
 
 #include "ln_gs.h"
 #include "ln_internal.h"
+#include "ln_stats.h"
 
 namespace ln {
 
@@ -475,7 +476,9 @@ ln_status run_cov(bool corr, int n, int m, const float *X, int ldx, float *out, 
         LN_TRY(stats_derive(m, p.mean, p.ss, nullptr, nullptr, p.rs, st));
         return plain_cov(n, m, X, ldx, p.mean, e, st);
     }
-    LN_TRY(col_stats(n, m, X, ldx, p.mean, p.ss, p.hi, p.lo, p.rs, p.partials, st));
+    // covariance centres with the means only; correlation also needs the second pass (1/s)
+    if (corr) LN_TRY(col_stats(n, m, X, ldx, p.mean, p.ss, p.hi, p.lo, p.rs, p.partials, st));
+    else LN_TRY(col_mean(n, m, X, ldx, p.mean, p.hi, p.lo, p.partials, st));
     if (!tensor_prec(prec)) {
         SimtOperands op{};
         op.A[0] = op.A[1] = X;

@@ -10,6 +10,7 @@
 // fixed order (deterministic, no atomics). Two passes: the mean first, then
 // the squared deviations from it.
 #include "ln_internal.h"
+#include "ln_stats.h"
 
 namespace ln {
 
@@ -129,7 +130,13 @@ __global__ __launch_bounds__(256) void k_col_final(int n, int m, int nchunks, co
 #pragma unroll
     for (int k = 1; k < 8; ++k) s += red[k][cx];
     if (PASS == 0) {
-        out[j] = s / (double)n;
+        const double mu = s / (double)n;
+        out[j] = mu;
+        if (off_hi) {  // centring pair from the mean (mean-only statistics)
+            const float h = (float)mu;
+            off_hi[j] = h;
+            off_lo[j] = (float)(mu - (double)h);
+        }
         return;
     }
     const double mu = mean[j];
@@ -375,6 +382,20 @@ ln_status col_stats(int n, int m, const float *X, long long ldx, double *mean, d
         k_col_final<1><<<gf, 256, 0, st>>>(n, m, nch, partials, mean, ss, off_hi, off_lo, rs);
     }
     return check_launch("column statistics");
+}
+
+ln_status col_mean(int n, int m, const float *X, long long ldx, double *mean, float *off_hi, float *off_lo,
+                   double *partials, cudaStream_t st) {
+    const int sr = stats_rows(n, m);
+    const int nch = (int)ceil_div(n, sr);
+    dim3 grid((unsigned)ceil_div(m, SC), (unsigned)nch);
+    const unsigned gf = (unsigned)ceil_div(m, 32);
+    { LaunchScope ls_(FAM_STATS, st); k_col_partial<0><<<grid, 256, 0, st>>>(n, m, X, ldx, nullptr, partials, sr); }
+    {
+        LaunchScope ls_(FAM_STATS, st);
+        k_col_final<0><<<gf, 256, 0, st>>>(n, m, nch, partials, nullptr, mean, off_hi, off_lo, nullptr);
+    }
+    return check_launch("column means");
 }
 
 ln_status stats_derive(int m, const double *mean, const double *ss, float *off_hi, float *off_lo, float *rs,
