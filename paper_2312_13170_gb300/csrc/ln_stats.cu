@@ -64,7 +64,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &t) {
 template <int PASS>
 __global__ __launch_bounds__(256) void k_col_partial(int n, int m, const float *__restrict__ X, long long ldx,
                                                      const double *__restrict__ mean, double *partials, int sr) {
-    __shared__ double red[8][SC];
+    __shared__ float red_h[8][SC], red_l[8][SC];
     const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
     const int c = blockIdx.x * SC + cx * 4;
     const int r0 = blockIdx.y * sr;
@@ -99,14 +99,24 @@ __global__ __launch_bounds__(256) void k_col_partial(int n, int m, const float *
         }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) red[ry][cx * 4 + q] = (double)h[q] + (double)l[q];
+    for (int q = 0; q < 4; ++q) {
+        red_h[ry][cx * 4 + q] = h[q];
+        red_l[ry][cx * 4 + q] = l[q];
+    }
     __syncthreads();
+    // the 8 row groups' pairs combine in FP32 with the same error-free sum (FP64
+    // is a narrow pipe on this GPU); one FP64 value per column leaves the CTA
     if (threadIdx.x < SC) {
-        int col = blockIdx.x * SC + threadIdx.x;
-        double s = 0.0;
+        const int col = blockIdx.x * SC + threadIdx.x;
+        float H = red_h[0][threadIdx.x], L = red_l[0][threadIdx.x];
 #pragma unroll
-        for (int g = 0; g < 8; ++g) s += red[g][threadIdx.x];
-        if (col < m) partials[(long long)blockIdx.y * m + col] = s;
+        for (int g = 1; g < 8; ++g) {
+            float s, t;
+            two_sum(H, red_h[g][threadIdx.x], s, t);
+            H = s;
+            L += t + red_l[g][threadIdx.x];
+        }
+        if (col < m) partials[(long long)blockIdx.y * m + col] = (double)H + (double)L;
     }
 }
 
