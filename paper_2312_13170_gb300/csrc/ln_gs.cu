@@ -29,6 +29,7 @@
 #include "ln_async.cuh"
 #include "ln_gs.h"
 #include "ln_internal.h"
+#include "ln_launch.h"
 
 #define LN_TRY_LAUNCH(what)                      \
     do {                                         \
@@ -483,27 +484,6 @@ constexpr int GS_MEM_NT = 512;
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
-// Launch with programmatic stream serialisation: the kernel's CTAs may start
-// while its predecessor in the stream finishes, and wait for it in
-// griddepcontrol.wait before touching memory.
-template <class... KArgs, class... Args>
-ln_status gs_launch(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
-                    const char *what, Args... args) {
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
-    if (e != cudaSuccess) return fail(LN_ERR_CUDA, "%s launch: %s", what, cudaGetErrorString(e));
-    return check_launch(what);
-}
-
 ln_status gs_plain(int m, int n, float *Q, long long ldq, float *R, long long ldr, cudaStream_t st) {
     for (int k = 0; k < n; ++k) {
         {
@@ -554,23 +534,23 @@ ln_status gs_blocked(int m, int n, float *Q, long long ldq, float *R, long long 
             LaunchScope ls_(FAM_SIMT, st);
             ln_status ps;
             if (m <= 512)
-                ps = gs_launch(k_gs_panel_reg<2, 256>, 1, 256, gs_panel_smem<2, 256>(), st, "k_gs_panel", m, p0, bw, Q,
+                ps = pdl_launch(k_gs_panel_reg<2, 256>, 1, 256, gs_panel_smem<2, 256>(), st, "k_gs_panel", m, p0, bw, Q,
                                ldq, R, ldr, vec);
             else if (m <= 1024 && rows == 2)
-                ps = gs_launch(k_gs_panel_reg<2, 512>, 1, 512, gs_panel_smem<2, 512>(), st, "k_gs_panel", m, p0, bw, Q,
+                ps = pdl_launch(k_gs_panel_reg<2, 512>, 1, 512, gs_panel_smem<2, 512>(), st, "k_gs_panel", m, p0, bw, Q,
                                ldq, R, ldr, vec);
             else if (m <= 1024)
-                ps = gs_launch(k_gs_panel_reg<4, 256>, 1, 256, gs_panel_smem<4, 256>(), st, "k_gs_panel", m, p0, bw, Q,
+                ps = pdl_launch(k_gs_panel_reg<4, 256>, 1, 256, gs_panel_smem<4, 256>(), st, "k_gs_panel", m, p0, bw, Q,
                                ldq, R, ldr, vec);
             else
-                ps = gs_launch(k_gs_panel_mem<GS_MEM_NT>, 1, GS_MEM_NT, in_smem ? mem_bytes : 0, st, "k_gs_panel", m,
+                ps = pdl_launch(k_gs_panel_mem<GS_MEM_NT>, 1, GS_MEM_NT, in_smem ? mem_bytes : 0, st, "k_gs_panel", m,
                                p0, bw, Q, ldq, R, ldr, in_smem);
             if (ps != LN_SUCCESS) return ps;
         }
         const int p1 = p0 + bw;
         if (p1 < n) {
             LaunchScope ls_(FAM_SIMT, st);
-            const ln_status us = gs_launch(k_gs_update, (unsigned)ceil_div(n - p1, GS_CB), GS_UNT, gs_update_smem(m), st,
+            const ln_status us = pdl_launch(k_gs_update, (unsigned)ceil_div(n - p1, GS_CB), GS_UNT, gs_update_smem(m), st,
                                            "k_gs_update", m, n, p0, p1, Q, ldq, R, ldr, vec);
             if (us != LN_SUCCESS) return us;
         }

@@ -9,8 +9,16 @@
 // writes one FP64 partial per column; a second kernel adds the partials in a
 // fixed order (deterministic, no atomics). Two passes: the mean first, then
 // the squared deviations from it.
+#include "ln_async.cuh"
 #include "ln_internal.h"
+#include "ln_launch.h"
 #include "ln_stats.h"
+
+#define LN_TRY_STATUS(expr)            \
+    do {                               \
+        const ln_status s_ = (expr);   \
+        if (s_ != LN_SUCCESS) return s_; \
+    } while (0)
 
 namespace ln {
 
@@ -68,6 +76,8 @@ __global__ __launch_bounds__(256) void k_col_partial(int n, int m, const float *
     const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
     const int c = blockIdx.x * SC + cx * 4;
     const int r0 = blockIdx.y * sr;
+    pdl_wait();  // X and the mean may come from the preceding launch
+    pdl_trigger();
     const bool vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && ((ldx & 3) == 0);
     float mh[4] = {0, 0, 0, 0};
     if (PASS == 1) {
@@ -131,6 +141,8 @@ __global__ __launch_bounds__(256) void k_col_final(int n, int m, int nchunks, co
     __shared__ double red[8][32];
     const int cx = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int j = blockIdx.x * 32 + cx;
+    pdl_wait();  // the partial sums come from the preceding launch
+    pdl_trigger();
     double s = 0.0;
     if (j < m)
         for (int ch = g; ch < nchunks; ch += 8) s += partials[(long long)ch * m + j];
@@ -381,17 +393,29 @@ ln_status col_stats(int n, int m, const float *X, long long ldx, double *mean, d
     const int nch = (int)ceil_div(n, sr);
     dim3 grid((unsigned)ceil_div(m, SC), (unsigned)nch);
     const unsigned gf = (unsigned)ceil_div(m, 32);
-    { LaunchScope ls_(FAM_STATS, st); k_col_partial<0><<<grid, 256, 0, st>>>(n, m, X, ldx, nullptr, partials, sr); }
+    const double *no_mean = nullptr;
+    float *no_f = nullptr;
     {
         LaunchScope ls_(FAM_STATS, st);
-        k_col_final<0><<<gf, 256, 0, st>>>(n, m, nch, partials, nullptr, mean, nullptr, nullptr, nullptr);
+        LN_TRY_STATUS(pdl_launch(k_col_partial<0>, grid, dim3(256), 0, st, "column statistics", n, m, X, ldx, no_mean,
+                                 partials, sr));
     }
-    { LaunchScope ls_(FAM_STATS, st); k_col_partial<1><<<grid, 256, 0, st>>>(n, m, X, ldx, mean, partials, sr); }
     {
         LaunchScope ls_(FAM_STATS, st);
-        k_col_final<1><<<gf, 256, 0, st>>>(n, m, nch, partials, mean, ss, off_hi, off_lo, rs);
+        LN_TRY_STATUS(pdl_launch(k_col_final<0>, dim3(gf), dim3(256), 0, st, "column statistics", n, m, nch,
+                                 (const double *)partials, no_mean, mean, no_f, no_f, no_f));
     }
-    return check_launch("column statistics");
+    {
+        LaunchScope ls_(FAM_STATS, st);
+        LN_TRY_STATUS(pdl_launch(k_col_partial<1>, grid, dim3(256), 0, st, "column statistics", n, m, X, ldx,
+                                 (const double *)mean, partials, sr));
+    }
+    {
+        LaunchScope ls_(FAM_STATS, st);
+        LN_TRY_STATUS(pdl_launch(k_col_final<1>, dim3(gf), dim3(256), 0, st, "column statistics", n, m, nch,
+                                 (const double *)partials, (const double *)mean, ss, off_hi, off_lo, rs));
+    }
+    return LN_SUCCESS;
 }
 
 ln_status col_mean(int n, int m, const float *X, long long ldx, double *mean, float *off_hi, float *off_lo,
@@ -400,12 +424,19 @@ ln_status col_mean(int n, int m, const float *X, long long ldx, double *mean, fl
     const int nch = (int)ceil_div(n, sr);
     dim3 grid((unsigned)ceil_div(m, SC), (unsigned)nch);
     const unsigned gf = (unsigned)ceil_div(m, 32);
-    { LaunchScope ls_(FAM_STATS, st); k_col_partial<0><<<grid, 256, 0, st>>>(n, m, X, ldx, nullptr, partials, sr); }
+    const double *no_mean = nullptr;
+    float *no_f = nullptr;
     {
         LaunchScope ls_(FAM_STATS, st);
-        k_col_final<0><<<gf, 256, 0, st>>>(n, m, nch, partials, nullptr, mean, off_hi, off_lo, nullptr);
+        LN_TRY_STATUS(pdl_launch(k_col_partial<0>, grid, dim3(256), 0, st, "column means", n, m, X, ldx, no_mean,
+                                 partials, sr));
     }
-    return check_launch("column means");
+    {
+        LaunchScope ls_(FAM_STATS, st);
+        LN_TRY_STATUS(pdl_launch(k_col_final<0>, dim3(gf), dim3(256), 0, st, "column means", n, m, nch,
+                                 (const double *)partials, no_mean, mean, off_hi, off_lo, no_f));
+    }
+    return LN_SUCCESS;
 }
 
 ln_status stats_derive(int m, const double *mean, const double *ss, float *off_hi, float *off_lo, float *rs,
