@@ -191,7 +191,12 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
  * F^T = D^T C^T) as the packed column operand, so neither exists in FP32.
  * G must not overlap an input. A, B, C, D and G may be host memory the GPU
  * can reach, as for ln_gemm_chain. Sizes of 0 are allowed (G = 0 when
- * nj, nk or nm is 0).
+ * nj, nk or nm is 0). Tensor-core forms whose E and F products fit on the GPU
+ * together run F on a second stream of the library. That stream is one per
+ * host thread and device, created on first use outside graph capture (a call
+ * made while `stream` is capturing and before that first use stays on
+ * `stream`). It is ordered after `stream` by an event and joined back before
+ * G, so the call stays stream-ordered on `stream`.
  */
 ln_status ln_3mm_workspace_size(int ni, int nj, int nk, int nl, int nm, ln_form form, ln_precision prec,
                                 size_t *bytes /*host*/);

@@ -205,6 +205,41 @@ ln_status device_view(T *p, T **out, const char *name) {
     }
 }
 
+// ------------------------------------------------------------------ a second stream
+// For independent contractions that fit on the GPU together: one extra stream
+// and two events per host thread and device, created on first use outside
+// graph capture (a call that finds none while its stream is capturing runs
+// everything in its own stream).
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+thread_local SideStream t_side[64];
+
+SideStream *side_stream(cudaStream_t st) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    SideStream &g = t_side[dev];
+    if (!g.s) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        if (cudaStreamCreateWithFlags(&g.s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            g = SideStream{};
+            return nullptr;
+        }
+    }
+    return &g;
+}
+
 // ------------------------------------------------------------------ validation helpers
 struct Span {
     const void *p;
@@ -1186,12 +1221,6 @@ ln_status ln_3mm(int ni, int nj, int nk, int nl, int nm, const float *A, const f
     gE.epi.N = nj;
     gE.epi.pack = p.pe;
     gE.epi.pack_kt = p.ktE;
-    bool side_done = false;
-    LN_TRY(umma_contract(gE, P, st, try_side ? &side : nullptr, &side_done));
-    if (try_side && !side_done) LN_TRY(pack_operands(ps + 2, 2, P, st));
-    if (p.rowsF > p.gF.mt)  // row tiles of F^T that G reads but no product writes
-        LN_CUDA_TRY(cudaMemsetAsync(p.pf + packed_bytes(p.gF.mt, p.ktF, P), 0,
-                                    packed_bytes(p.rowsF - p.gF.mt, p.ktF, P), st));
     UmmaProblem gF{};
     gF.seg[0] = {p.pd, p.pc};
     gF.nseg = 1;
@@ -1208,7 +1237,28 @@ ln_status ln_3mm(int ni, int nj, int nk, int nl, int nm, const float *A, const f
     gF.epi.N = nj;
     gF.epi.pack = p.pf;
     gF.epi.pack_kt = p.ktF;
-    LN_TRY(umma_contract(gF, P, st));
+    // E and F are independent: when both fit on the GPU at once (one
+    // persistent CTA per work item) F runs on a second stream beside E
+    const long long wE = (long long)gE.mt * gE.nt * (gE.ksplit > 1 ? gE.ksplit : 1);
+    const long long wF = (long long)gF.mt * gF.nt * (gF.ksplit > 1 ? gF.ksplit : 1);
+    SideStream *ss = (!try_side && wE + wF <= sm_count()) ? side_stream(st) : nullptr;
+    if (ss) {
+        LN_CUDA_TRY(cudaEventRecord(ss->fork, st));
+        LN_CUDA_TRY(cudaStreamWaitEvent(ss->s, ss->fork, 0));
+        const ln_status sf = umma_contract(gF, P, ss->s);
+        LN_CUDA_TRY(cudaEventRecord(ss->join, ss->s));  // joined below even if F failed to launch
+        LN_TRY(umma_contract(gE, P, st));
+        LN_CUDA_TRY(cudaStreamWaitEvent(st, ss->join, 0));
+        LN_TRY(sf);
+    } else {
+        bool side_done = false;
+        LN_TRY(umma_contract(gE, P, st, try_side ? &side : nullptr, &side_done));
+        if (try_side && !side_done) LN_TRY(pack_operands(ps + 2, 2, P, st));
+        LN_TRY(umma_contract(gF, P, st));
+    }
+    if (p.rowsF > p.gF.mt)  // row tiles of F^T that G reads but no product writes
+        LN_CUDA_TRY(cudaMemsetAsync(p.pf + packed_bytes(p.gF.mt, p.ktF, P), 0,
+                                    packed_bytes(p.rowsF - p.gF.mt, p.ktF, P), st));
     UmmaProblem gG{};
     gG.seg[0] = {p.pe, p.pf};
     gG.nseg = 1;

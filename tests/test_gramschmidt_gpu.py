@@ -141,3 +141,23 @@ def test_gramschmidt_graph_replay(api):
     assert np.array_equal(host(Q), Qe) and np.array_equal(host(R), Re)
     Qo, Ro = oracle.gramschmidt(A)
     check(A, Qe, Re, Qo, Ro)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("m,n", [(300, 100), (1100, 70)])
+def test_gramschmidt_strided_unaligned(api, form, m, n):
+    # leading dimensions that are not multiples of 4: the scalar fill, write-out and staging paths
+    A = inputs.gramschmidt_inputs(m, n, seed=11)["A"]
+    Qo, Ro = oracle.gramschmidt(A)
+    big = torch.full((m, n + 3), float("nan"), dtype=torch.float32, device="cuda")
+    big[:, 1:n + 1] = dev(A)
+    Av = big[:, 1:n + 1]
+    Qbig = torch.full((m, n + 5), float("nan"), dtype=torch.float32, device="cuda")
+    Rbig = torch.full((n, n + 2), float("nan"), dtype=torch.float32, device="cuda")
+    Q, R = api.gramschmidt(Av, form=form, Q=Qbig[:, 2:n + 2], R=Rbig[:, 1:n + 1])
+    api.stream_check()
+    check(A, host(Q), host(R), Qo, Ro)
+    # nothing outside the views was written
+    assert torch.isnan(Qbig[:, :2]).all() and torch.isnan(Qbig[:, n + 2:]).all()
+    assert torch.isnan(Rbig[:, :1]).all() and torch.isnan(Rbig[:, n + 1:]).all()
+    assert torch.isnan(big[:, 0]).all() and torch.isnan(big[:, n + 1:]).all()
