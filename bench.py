@@ -224,6 +224,24 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- replicas
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The slowest rank's step time; every rank receives it (one replica per
+    GPU, so the job is as fast as its slowest replica)."""
+    if dist is None:
+        return float(ms)
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gflops(flops_per_replica_step, world_size, ms_max):
+    """Whole-job throughput: every replica does one step's work per ms_max."""
+    return flops_per_replica_step * world_size / (ms_max / 1e3) / 1e9
+
+
 # ---------------------------------------------------------------- GPU leg
 def run_own(args):
     import torch
@@ -319,12 +337,8 @@ def run_own(args):
     ms, launches, fams = timed(args.steps, args.warmup, "internalized", "3xbf16", with_timing=True)
     clk = clocks.stop()
     E_int = E.clone()
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = FLOPS * ws / (ms_max / 1e3) / 1e9
+    ms_max = max_over_ranks(ms, dist, dev)
+    value = whole_job_gflops(FLOPS, ws, ms_max)
 
     # plain and exact-FP32 tiled forms: same work, fewer steps
     ms_plain, _, _ = timed(args.plain_steps, 1, "plain", "fp32")
