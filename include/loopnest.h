@@ -347,7 +347,11 @@ ln_status ln_3mm_bwd(int ni, int nj, int nk, int nl, int nm, const float *A, con
  *
  * Chain: for E = (A*B)*C and an upstream gradient G = dL/dE (ni x nl),
  *   dA = G (B C)^T,  dB = A^T G C^T,  dC = (A B)^T G.
- * All contiguous; dA/dB/dC must not overlap the inputs or each other.
+ * All contiguous; dA/dB/dC must not overlap the inputs or each other. In the
+ * tensor-core forms the dB branch (G C^T, then dB) may run on the library's
+ * second stream. That happens when its contractions fit on the GPU beside
+ * those of the other branches, and the stream rules are those of ln_3mm. The
+ * call stays stream-ordered on `stream`.
  *
  * Covariance: for an upstream gradient W = dL/dcov (nfeat x nfeat, ldw),
  *   dX = Xc (W + W^T) / (nsamples - 1).

@@ -744,6 +744,8 @@ struct ChainBwdPlan {
     float *BC = nullptr, *GCt = nullptr, *T = nullptr;
     ContractPlan c;  // sized for the largest of the contractions, reused in stream order
     SplitArea split;
+    char *px2 = nullptr;  // the same again for the branch that may run on a second stream
+    SplitArea split2;
 };
 
 void plan_chain_bwd(Ws &w, int ni, int nj, int nk, int nl, ln_form form, ln_precision prec, ChainBwdPlan &p) {
@@ -762,7 +764,18 @@ void plan_chain_bwd(Ws &w, int ni, int nj, int nk, int nl, ln_form form, ln_prec
         }
         p.c.px = w.take<char>(best);
         plan_split_area(w, dims, 6, P, p.split);
+        p.px2 = w.take<char>(best);
+        plan_split_area(w, dims, 6, P, p.split2);
     }
+}
+
+// Work items (output tiles x K slices) of one tensor-core contraction, the
+// number of persistent CTAs it launches at most.
+long long contract_work(int M, int N, int K, int P) {
+    ContractPlan g;
+    contract_geometry(M, N, K, P, g);
+    const long long t = (long long)g.mt * g.nt;
+    return t * umma_ksplit(t, g.kt);
 }
 
 ln_status contract_into(int M, int N, int K, Operand a, Operand b, const EpiParams &e, ln_form form, ln_precision prec,
@@ -1486,15 +1499,46 @@ ln_status ln_gemm_chain_bwd(int ni, int nj, int nk, int nl, const float *A, cons
     plan_chain_bwd(w, ni, nj, nk, nl, form, prec, p);
     cudaStream_t st = S(stream);
     char *pk = p.c.px;
-    // BC = B C (nk x nl); dA = G BC^T
-    LN_TRY(contract_into(nk, nl, nj, {B, nj, 0}, {C, nl, 0}, epi_store(nk, nl, 1.0f, p.BC, nl), form, prec, pk, p.split, st));
-    LN_TRY(contract_into(ni, nk, nl, {G, nl, 0}, {p.BC, nl, 1}, epi_store(ni, nk, 1.0f, dA, nk), form, prec, pk, p.split, st));
-    // GCt = G C^T (ni x nj); dB = A^T GCt
-    LN_TRY(contract_into(ni, nj, nl, {G, nl, 0}, {C, nl, 1}, epi_store(ni, nj, 1.0f, p.GCt, nj), form, prec, pk, p.split, st));
-    LN_TRY(contract_into(nk, nj, ni, {A, nk, 1}, {p.GCt, nj, 0}, epi_store(nk, nj, 1.0f, dB, nj), form, prec, pk, p.split, st));
-    // T = A B (ni x nj); dC = T^T G
-    LN_TRY(contract_into(ni, nj, nk, {A, nk, 0}, {B, nj, 0}, epi_store(ni, nj, 1.0f, p.T, nj), form, prec, pk, p.split, st));
-    return contract_into(nj, nl, ni, {p.T, nj, 1}, {G, nl, 0}, epi_store(nj, nl, 1.0f, dC, nl), form, prec, pk, p.split, st);
+    // three independent branches: BC = B C (nk x nl), dA = G BC^T;
+    // GCt = G C^T (ni x nj), dB = A^T GCt; T = A B (ni x nj), dC = T^T G.
+    // When the first two branches' contractions fit on the GPU side by side,
+    // the GCt branch runs on a second stream (its own pack and split areas).
+    auto branch_b = [&](char *area, const SplitArea &sa, cudaStream_t s) -> ln_status {
+        LN_TRY(contract_into(ni, nj, nl, {G, nl, 0}, {C, nl, 1}, epi_store(ni, nj, 1.0f, p.GCt, nj), form, prec, area,
+                             sa, s));
+        return contract_into(nk, nj, ni, {A, nk, 1}, {p.GCt, nj, 0}, epi_store(nk, nj, 1.0f, dB, nj), form, prec, area,
+                             sa, s);
+    };
+    auto branches_ac = [&]() -> ln_status {
+        LN_TRY(contract_into(nk, nl, nj, {B, nj, 0}, {C, nl, 0}, epi_store(nk, nl, 1.0f, p.BC, nl), form, prec, pk,
+                             p.split, st));
+        LN_TRY(contract_into(ni, nk, nl, {G, nl, 0}, {p.BC, nl, 1}, epi_store(ni, nk, 1.0f, dA, nk), form, prec, pk,
+                             p.split, st));
+        LN_TRY(contract_into(ni, nj, nk, {A, nk, 0}, {B, nj, 0}, epi_store(ni, nj, 1.0f, p.T, nj), form, prec, pk,
+                             p.split, st));
+        return contract_into(nj, nl, ni, {p.T, nj, 1}, {G, nl, 0}, epi_store(nj, nl, 1.0f, dC, nl), form, prec, pk,
+                             p.split, st);
+    };
+    SideStream *ss = nullptr;
+    if (p.px2) {
+        const int P = prec_terms(prec);
+        const long long sms = sm_count();
+        if (contract_work(nk, nl, nj, P) + contract_work(ni, nj, nl, P) <= sms &&
+            contract_work(ni, nk, nl, P) + contract_work(nk, nj, ni, P) <= sms)
+            ss = side_stream(st);
+    }
+    if (!ss) {
+        LN_TRY(branches_ac());
+        return branch_b(pk, p.split, st);
+    }
+    LN_CUDA_TRY(cudaEventRecord(ss->fork, st));
+    LN_CUDA_TRY(cudaStreamWaitEvent(ss->s, ss->fork, 0));
+    const ln_status sb = branch_b(p.px2, p.split2, ss->s);
+    LN_CUDA_TRY(cudaEventRecord(ss->join, ss->s));
+    const ln_status sa = branches_ac();
+    LN_CUDA_TRY(cudaStreamWaitEvent(st, ss->join, 0));  // joined whatever either branch returned
+    LN_TRY(sb);
+    return sa;
 }
 
 ln_status ln_covariance_bwd_workspace_size(int nsamples, int nfeat, ln_form form, ln_precision prec, size_t *bytes) {
