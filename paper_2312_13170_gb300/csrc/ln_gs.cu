@@ -180,8 +180,9 @@ __device__ __forceinline__ void gs_reg_step(float2 (&w)[S][GS_BW / 2], int c, in
         for (int q = 0; q + h < NW; q += 2 * h) part[q] += part[q + h];
     const float tot = part[0];
     const float nrm2 = __shfl_sync(0xffffffffu, tot, PH);
-    const float r = __fsqrt_rn(nrm2);
-    const float inv = nrm2 > 0.f ? __frsqrt_rn(nrm2) : 0.f;
+    // hardware reciprocal square root (a few ulps; the norm is nrm2 * inv)
+    const float inv = nrm2 > 0.f ? rsqrtf(nrm2) : 0.f;
+    const float r = nrm2 * inv;
     const float rc = tot * inv;  // R[k][k + l - PH] for slot l > PH
     if (warp == 0 && lane >= PH && lane < WD && c + lane - PH < bw)
         R[(long long)(p0 + c) * ldr + p0 + c + lane - PH] = lane == PH ? r : rc;
