@@ -566,7 +566,8 @@ def run_chain_2048(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
 
 def run_3mm(only, modes, api, inputs, oracle, cores, time_it, emit, reps):
     """Polybench 3mm, G = (A B)(C D), at the paper's problem size (1024) and at
-    2048; entries U[-1,1], seed 0, drawn in the order A, B, C, D."""
+    2048; entries U[-1,1], seed 0, drawn in the order A, B, C, D. At 1024 also
+    its adjoint (dA, dB, dC, dD for an upstream gradient U[-1,1], seed 1)."""
     import torch
 
     if "3mm" not in only:
@@ -588,6 +589,22 @@ def run_3mm(only, modes, api, inputs, oracle, cores, time_it, emit, reps):
             err = inputs.rel_fro(G[:rows].cpu().numpy(), Gr)
             ms = time_it(lambda: api.three_mm(*T, form=form, prec=prec, out=G), n=3 if form == "plain" else reps)
             emit(f"3mm {n}^3 (G = (A*B)*(C*D))", "3mm", form, prec, 6.0 * n ** 3, 5 * 4 * n * n, ms, err, cpu)
+        if n != 1024:
+            continue
+        # the adjoint at the paper's size: upstream gradient U[-1,1] (seed 1)
+        Gb = np.random.default_rng(1).uniform(-1.0, 1.0, size=(n, n)).astype(np.float32)
+        t0 = time.perf_counter()
+        ref = oracle.three_mm_vjp(A, B, C, D, Gb)
+        dt = time.perf_counter() - t0
+        cpu_b = {"kind": "oracle", "cores": cores, "seconds": dt, "sample": "the whole adjoint (8 products)",
+                 "gflops": 16.0 * n ** 3 / dt / 1e9}
+        Gbt = torch.from_numpy(Gb).cuda()
+        for form, prec in modes:
+            grads = api.three_mm_bwd(*T, Gbt, form=form, prec=prec)
+            err = max(inputs.rel_fro(g.cpu().numpy(), r) for g, r in zip(grads, ref))
+            ms = time_it(lambda: api.three_mm_bwd(*T, Gbt, form=form, prec=prec), n=3 if form == "plain" else reps)
+            emit(f"3mm adjoint {n}^3 (dA, dB, dC, dD)", "3mm_bwd", form, prec, 16.0 * n ** 3, 9 * 4 * n * n, ms, err,
+                 cpu_b)
 
 
 def run_cov(only, modes, api, inputs, oracle, cores, time_it, emit, reps, hbm):

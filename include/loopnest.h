@@ -335,6 +335,9 @@ ln_status ln_gramschmidt(int m, int n, const float *A, int lda, float *Q, int ld
  * dD = C^T (A B)^T Gb (E = A B and F = C D are recomputed in the workspace).
  * Shapes as in ln_3mm; every matrix contiguous; gradient outputs must not
  * overlap each other or an input.
+ * Tensor-core forms run the two halves (E, dE, dA, dB and F, dF, dC, dD) on
+ * `stream` and the library's second stream when their contractions fit on
+ * the GPU side by side (stream rules as for ln_3mm).
  */
 ln_status ln_3mm_bwd_workspace_size(int ni, int nj, int nk, int nl, int nm, ln_form form, ln_precision prec,
                                     size_t *bytes /*host*/);

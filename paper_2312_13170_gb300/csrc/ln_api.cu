@@ -212,7 +212,7 @@ ln_status device_view(T *p, T **out, const char *name) {
 // everything in its own stream).
 struct SideStream {
     cudaStream_t s = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, mid_a = nullptr, mid_b = nullptr;
 };
 thread_local SideStream t_side[64];
 
@@ -231,7 +231,9 @@ SideStream *side_stream(cudaStream_t st) {
         }
         if (cudaStreamCreateWithFlags(&g.s, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g.mid_a, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g.mid_b, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             g = SideStream{};
             return nullptr;
@@ -809,6 +811,8 @@ struct Mm3BwdPlan {
     float *E = nullptr, *F = nullptr, *dE = nullptr, *dF = nullptr;
     char *pack = nullptr;
     SplitArea split;
+    char *pack2 = nullptr;  // the same again for the half that may run on a second stream
+    SplitArea split2;
 };
 
 void plan_3mm_bwd(Ws &w, int ni, int nj, int nk, int nl, int nm, ln_form form, ln_precision prec, Mm3BwdPlan &p) {
@@ -828,6 +832,8 @@ void plan_3mm_bwd(Ws &w, int ni, int nj, int nk, int nl, int nm, ln_form form, l
         }
         p.pack = w.take<char>(best);
         plan_split_area(w, dims, MM3_BWD_N, P, p.split);
+        p.pack2 = w.take<char>(best);
+        plan_split_area(w, dims, MM3_BWD_N, P, p.split2);
     }
 }
 
@@ -1324,16 +1330,65 @@ ln_status ln_3mm_bwd(int ni, int nj, int nk, int nl, int nm, const float *A, con
     Ws w(ws);
     plan_3mm_bwd(w, ni, nj, nk, nl, nm, form, prec, p);
     cudaStream_t st = S(stream);
-    char *pk = p.pack;
-    // Operand {p, ld, t}: t = 1 reads the stored matrix transposed
-    LN_TRY(contract_into(ni, nj, nk, {A, nk, 0}, {B, nj, 0}, epi_store(ni, nj, 1.0f, p.E, nj), form, prec, pk, p.split, st));
-    LN_TRY(contract_into(nj, nl, nm, {C, nm, 0}, {D, nl, 0}, epi_store(nj, nl, 1.0f, p.F, nl), form, prec, pk, p.split, st));
-    LN_TRY(contract_into(ni, nj, nl, {Gb, nl, 0}, {p.F, nl, 1}, epi_store(ni, nj, 1.0f, p.dE, nj), form, prec, pk, p.split, st));
-    LN_TRY(contract_into(nj, nl, ni, {p.E, nj, 1}, {Gb, nl, 0}, epi_store(nj, nl, 1.0f, p.dF, nl), form, prec, pk, p.split, st));
-    LN_TRY(contract_into(ni, nk, nj, {p.dE, nj, 0}, {B, nj, 1}, epi_store(ni, nk, 1.0f, dA, nk), form, prec, pk, p.split, st));
-    LN_TRY(contract_into(nk, nj, ni, {A, nk, 1}, {p.dE, nj, 0}, epi_store(nk, nj, 1.0f, dB, nj), form, prec, pk, p.split, st));
-    LN_TRY(contract_into(nj, nm, nl, {p.dF, nl, 0}, {D, nl, 1}, epi_store(nj, nm, 1.0f, dC, nm), form, prec, pk, p.split, st));
-    return contract_into(nm, nl, nj, {C, nm, 1}, {p.dF, nl, 0}, epi_store(nm, nl, 1.0f, dD, nl), form, prec, pk, p.split, st);
+    // Operand {p, ld, t}: t = 1 reads the stored matrix transposed. Two halves:
+    // E = A B, then (with F) dE = Gb F^T, dA = dE B^T, dB = A^T dE; and
+    // F = C D, then (with E) dF = E^T Gb, dC = dF D^T, dD = C^T dF.
+    auto prod_E = [&](char *pk, const SplitArea &sa, cudaStream_t s) {
+        return contract_into(ni, nj, nk, {A, nk, 0}, {B, nj, 0}, epi_store(ni, nj, 1.0f, p.E, nj), form, prec, pk, sa,
+                             s);
+    };
+    auto prod_F = [&](char *pk, const SplitArea &sa, cudaStream_t s) {
+        return contract_into(nj, nl, nm, {C, nm, 0}, {D, nl, 0}, epi_store(nj, nl, 1.0f, p.F, nl), form, prec, pk, sa,
+                             s);
+    };
+    auto grads_AB = [&](char *pk, const SplitArea &sa, cudaStream_t s) -> ln_status {
+        LN_TRY(contract_into(ni, nj, nl, {Gb, nl, 0}, {p.F, nl, 1}, epi_store(ni, nj, 1.0f, p.dE, nj), form, prec, pk,
+                             sa, s));
+        LN_TRY(contract_into(ni, nk, nj, {p.dE, nj, 0}, {B, nj, 1}, epi_store(ni, nk, 1.0f, dA, nk), form, prec, pk,
+                             sa, s));
+        return contract_into(nk, nj, ni, {A, nk, 1}, {p.dE, nj, 0}, epi_store(nk, nj, 1.0f, dB, nj), form, prec, pk,
+                             sa, s);
+    };
+    auto grads_CD = [&](char *pk, const SplitArea &sa, cudaStream_t s) -> ln_status {
+        LN_TRY(contract_into(nj, nl, ni, {p.E, nj, 1}, {Gb, nl, 0}, epi_store(nj, nl, 1.0f, p.dF, nl), form, prec, pk,
+                             sa, s));
+        LN_TRY(contract_into(nj, nm, nl, {p.dF, nl, 0}, {D, nl, 1}, epi_store(nj, nm, 1.0f, dC, nm), form, prec, pk,
+                             sa, s));
+        return contract_into(nm, nl, nj, {C, nm, 1}, {p.dF, nl, 0}, epi_store(nm, nl, 1.0f, dD, nl), form, prec, pk,
+                             sa, s);
+    };
+    // the two halves side by side when each pair of concurrent contractions fits on the GPU
+    SideStream *ss = nullptr;
+    if (p.pack2) {
+        const int P = prec_terms(prec);
+        int d[MM3_BWD_N][3];
+        mm3_bwd_dims(ni, nj, nk, nl, nm, d);
+        auto wk = [&](int i) { return contract_work(d[i][0], d[i][1], d[i][2], P); };
+        const long long sms = sm_count();
+        // pairs in execution order: (E, F), (dE, dF), (dA, dC), (dB, dD)
+        if (wk(0) + wk(1) <= sms && wk(2) + wk(3) <= sms && wk(4) + wk(6) <= sms && wk(5) + wk(7) <= sms)
+            ss = side_stream(st);
+    }
+    if (!ss) {
+        LN_TRY(prod_E(p.pack, p.split, st));
+        LN_TRY(prod_F(p.pack, p.split, st));
+        LN_TRY(grads_AB(p.pack, p.split, st));
+        return grads_CD(p.pack, p.split, st);
+    }
+    LN_CUDA_TRY(cudaEventRecord(ss->fork, st));
+    LN_CUDA_TRY(cudaStreamWaitEvent(ss->s, ss->fork, 0));
+    ln_status sb = prod_F(p.pack2, p.split2, ss->s);
+    LN_CUDA_TRY(cudaEventRecord(ss->mid_b, ss->s));  // F written
+    ln_status sa = prod_E(p.pack, p.split, st);
+    LN_CUDA_TRY(cudaEventRecord(ss->mid_a, st));  // E written
+    LN_CUDA_TRY(cudaStreamWaitEvent(ss->s, ss->mid_a, 0));
+    if (sb == LN_SUCCESS) sb = grads_CD(p.pack2, p.split2, ss->s);
+    LN_CUDA_TRY(cudaEventRecord(ss->join, ss->s));
+    LN_CUDA_TRY(cudaStreamWaitEvent(st, ss->mid_b, 0));
+    if (sa == LN_SUCCESS) sa = grads_AB(p.pack, p.split, st);
+    LN_CUDA_TRY(cudaStreamWaitEvent(st, ss->join, 0));  // joined whatever either half returned
+    LN_TRY(sb);
+    return sa;
 }
 
 // ------------------------------------------------------------------ statistics, covariance, correlation

@@ -79,6 +79,17 @@ def test_gemm_validation(L):
 
 
 def test_workspace_queries(L):
+    # the automatic tile width depends on the GPU's SM count: pin 256-wide tiles
+    old = ctypes.c_int(0)
+    assert L.ln_get_tuning(b"tile_n", ctypes.byref(old)) == 0
+    assert L.ln_set_tuning(b"tile_n", 256) == 0
+    try:
+        _workspace_queries_256(L)
+    finally:
+        L.ln_set_tuning(b"tile_n", old.value)
+
+
+def _workspace_queries_256(L):
     n = ctypes.c_size_t()
     assert L.ln_gemm_workspace_size(256, 256, 256, 0, 0, ctypes.byref(n)) == 0 and n.value == 0
     assert L.ln_gemm_workspace_size(256, 256, 256, 1, 0, ctypes.byref(n)) == 0 and n.value == 0
