@@ -34,7 +34,7 @@ def _rank(rank, world, port, step_ms, out):
 def test_two_replicas_take_the_slowest_rank():
     world, port = 2, _free_port()
     step_ms = [0.25, 0.75]
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank, args=(world, port, step_ms, out), nprocs=world, join=True)
         res = dict(out)
