@@ -136,8 +136,8 @@ __device__ __forceinline__ float gs_reduce(float (&v)[32], int c, int bw, int p0
 
 // One column step of the register-resident panel. w holds this thread's
 // rows as 16 pairs of slots; the current column k = p0 + c sits in slot PH
-// (= c & 1) and slot j holds column k - PH + j; slots >= WD are zero, as is
-// everything before the current slot that still matters. The squared norm
+// (= c & 1) and slot j holds column k - PH + j; slots >= WD are zero, and in
+// a PH = 1 step slot 0 holds the previous, finished column. The squared norm
 // and the dot products with the later columns come out of one CTA-wide
 // reduction (packed FP32x2 multiply-adds, then warp_reduce_cols and one
 // barrier); the normalised column goes to column c of the shared-memory tile
