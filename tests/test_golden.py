@@ -1,6 +1,7 @@
 """Hand-derived examples (tests/golden/hand_examples.json) against the oracle."""
 import json
 import os
+from fractions import Fraction
 
 import numpy as np
 
@@ -26,3 +27,12 @@ def test_golden_oracle():
     assert np.array_equal(oracle.syrk(a(g["A"]), a(g["C"]), g["alpha"], g["beta"], g["fill"]), a(g["out"]))
     g = G["syr2k"]
     assert np.array_equal(oracle.syr2k(a(g["A"]), a(g["B"]), a(g["C"]), g["alpha"], g["beta"], g["fill"]), a(g["out"]))
+
+
+def test_golden_gramschmidt_oracle():
+    g = G["gramschmidt"]
+    Q, R = oracle.gramschmidt(a(g["A"]))
+    Qe = np.array([[float(Fraction(x)) for x in row] for row in g["Q"]])
+    Re = np.array([[float(Fraction(x)) for x in row] for row in g["R"]])
+    # one division and a square root per entry: within a few FP64 roundings
+    assert np.max(np.abs(Q - Qe)) < 1e-15 and np.max(np.abs(R - Re)) < 1e-14

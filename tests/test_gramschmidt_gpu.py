@@ -161,3 +161,18 @@ def test_gramschmidt_strided_unaligned(api, form, m, n):
     assert torch.isnan(Qbig[:, :2]).all() and torch.isnan(Qbig[:, n + 2:]).all()
     assert torch.isnan(Rbig[:, :1]).all() and torch.isnan(Rbig[:, n + 1:]).all()
     assert torch.isnan(big[:, 0]).all() and torch.isnan(big[:, n + 1:]).all()
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_gramschmidt_golden(api, form):
+    # the hand-derived worked example of tests/golden/hand_examples.json
+    import json
+    import os
+    from fractions import Fraction
+
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_examples.json")))["gramschmidt"]
+    Q, R = api.gramschmidt(dev(np.array(g["A"], np.float32)), form=form)
+    api.stream_check()
+    Qe = np.array([[float(Fraction(x)) for x in row] for row in g["Q"]])
+    Re = np.array([[float(Fraction(x)) for x in row] for row in g["R"]])
+    assert np.max(np.abs(host(Q) - Qe)) <= 2 ** -22 and np.max(np.abs(host(R) - Re)) <= 13 * 2 ** -22
