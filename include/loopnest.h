@@ -139,6 +139,13 @@ ln_status ln_timing_read(const char *family, double *total_ms /*host*/, int *lau
  *              contractions whose output tiles fill less than half the GPU
  *              (slices exchange FP32 partial sums through the workspace; the
  *              last slice of a tile to finish adds them in slice order);
+ *   "stream_k" 0 or 1 (default 0): stream-K for single tensor-core
+ *              contractions with fewer output tiles than SMs (covariance,
+ *              correlation, SYRK/SYR2K and the general contractions that do
+ *              not run beside another one): the tiles' k ranges are split
+ *              evenly over one CTA per SM; a tile spread over several CTAs
+ *              gets their FP32 partial sums through the workspace, added in
+ *              k order by the CTA that holds its first k tile;
  *   "gs_rows"  2 or 4 (default 4): rows of the matrix each thread holds in
  *              registers in the internalized Gram-Schmidt panel kernel when
  *              512 < m <= 1024 (512 or 256 threads per panel CTA).

@@ -82,6 +82,7 @@ std::atomic<int> g_tile_n{0};
 std::atomic<int> g_pack_threads{512};
 std::atomic<int> g_split_k{0};
 std::atomic<int> g_gs_rows{4};
+std::atomic<int> g_stream_k{0};
 }  // namespace
 
 int tune_chunk_kt() { return g_chunk_kt.load(std::memory_order_relaxed); }
@@ -89,6 +90,7 @@ int tune_tile_n() { return g_tile_n.load(std::memory_order_relaxed); }
 int tune_pack_threads() { return g_pack_threads.load(std::memory_order_relaxed); }
 int tune_split_k() { return g_split_k.load(std::memory_order_relaxed); }
 int tune_gs_rows() { return g_gs_rows.load(std::memory_order_relaxed); }
+int tune_stream_k() { return g_stream_k.load(std::memory_order_relaxed); }
 
 bool inject_timeout_requested() {
     const char *v = getenv("LN_FAULT_INJECT");
@@ -132,11 +134,15 @@ struct SplitArea {
     int *cnt = nullptr;
 };
 
-// Split-K of one tcgen05 contraction (umma_ksplit): slices and their workspace.
+// Split-K (umma_ksplit) or stream-K (umma_streamk) of one tcgen05
+// contraction, and their workspace.
 struct SplitPlan {
     int ksplit = 1;
     float *part = nullptr;
     int *cnt = nullptr;
+    int streamk = 0;
+    float *skpart = nullptr;
+    int *skflag = nullptr;
 };
 
 void plan_split(Ws &w, long long tiles, int ktot, int bn, SplitPlan &sp) {
@@ -144,7 +150,21 @@ void plan_split(Ws &w, long long tiles, int ktot, int bn, SplitPlan &sp) {
     if (sp.ksplit > 1) {
         sp.part = w.take<float>(umma_split_part_bytes(tiles, sp.ksplit, bn));
         sp.cnt = w.take<int>(umma_split_cnt_bytes(tiles, bn));
+        return;
     }
+    sp.streamk = umma_streamk(tiles, ktot);
+    if (sp.streamk) {
+        sp.skpart = w.take<float>(umma_streamk_part_bytes(bn));
+        sp.skflag = w.take<int>(umma_streamk_flag_bytes());
+    }
+}
+
+// Stream-K flags start at zero: cleared before the first kernel of the call,
+// so that the call's kernels still follow each other with programmatic
+// dependent launch.
+ln_status zero_streamk_flags(const SplitPlan &sp, cudaStream_t st) {
+    if (sp.streamk) LN_CUDA_TRY(cudaMemsetAsync(sp.skflag, 0, umma_streamk_flag_bytes(), st));
+    return LN_SUCCESS;
 }
 
 // dims: (M, N, K) of general contractions
@@ -169,6 +189,9 @@ void apply_split(UmmaProblem &pb, const SplitPlan &sp) {
     pb.ksplit = sp.ksplit;
     pb.kpart = sp.part;
     pb.kcnt = sp.cnt;
+    pb.streamk = sp.streamk;
+    pb.skpart = sp.skpart;
+    pb.skflag = sp.skflag;
 }
 
 // ------------------------------------------------------------------ host-resident operands
@@ -356,6 +379,7 @@ ln_status run_contract(int M, int N, int K, Operand a, Operand b, const EpiParam
     const int P = prec_terms(prec);
     PackSrc ps[2] = {{a.p, a.ld, a.t ? 1 : 0, M, K, nullptr, nullptr, cp.px, cp.mt, cp.kt},
                      {b.p, b.ld, b.t ? 0 : 1, N, K, nullptr, nullptr, cp.py, cp.yrt, cp.kt}};
+    LN_TRY(zero_streamk_flags(cp.split, st));
     LN_TRY(pack_operands(ps, 2, P, st));
     UmmaProblem pb{};
     pb.seg[0] = {cp.px, cp.py};
@@ -513,6 +537,7 @@ ln_status run_cov(bool corr, int n, int m, const float *X, int ldx, float *out, 
         LN_TRY(stats_derive(m, p.mean, p.ss, nullptr, nullptr, p.rs, st));
         return plain_cov(n, m, X, ldx, p.mean, e, st);
     }
+    LN_TRY(zero_streamk_flags(p.split, st));
     // covariance centres with the means only; correlation also needs the second pass (1/s)
     if (corr) LN_TRY(col_stats(n, m, X, ldx, p.mean, p.ss, p.hi, p.lo, p.rs, p.partials, st));
     else LN_TRY(col_mean(n, m, X, ldx, p.mean, p.hi, p.lo, p.partials, st));
@@ -611,6 +636,7 @@ ln_status run_sym(bool two, ln_fill fill, int n, int k, float alpha, const float
     const int P = prec_terms(prec);
     PackSrc ps[2] = {{A, lda, 0, n, k, nullptr, nullptr, p.pa, p.mt, p.kt},
                      {B, ldb, 0, n, k, nullptr, nullptr, p.pb, p.mt, p.kt}};
+    LN_TRY(zero_streamk_flags(p.split, st));
     LN_TRY(pack_operands(ps, two ? 2 : 1, P, st));
     UmmaProblem pb{};
     if (two) {
@@ -962,6 +988,11 @@ ln_status ln_set_tuning(const char *key, int value) {
         g_split_k.store(value);
         return LN_SUCCESS;
     }
+    if (strcmp(key, "stream_k") == 0) {
+        if (value != 0 && value != 1) return fail(LN_ERR_INVALID_VALUE, "stream_k must be 0 or 1 (got %d)", value);
+        g_stream_k.store(value);
+        return LN_SUCCESS;
+    }
     if (strcmp(key, "gs_rows") == 0) {
         if (value != 2 && value != 4) return fail(LN_ERR_INVALID_VALUE, "gs_rows must be 2 or 4 (got %d)", value);
         g_gs_rows.store(value);
@@ -984,6 +1015,7 @@ ln_status ln_get_tuning(const char *key, int *value) {
     else if (strcmp(key, "pack_threads") == 0) *value = g_pack_threads.load();
     else if (strcmp(key, "split_k") == 0) *value = g_split_k.load();
     else if (strcmp(key, "gs_rows") == 0) *value = g_gs_rows.load();
+    else if (strcmp(key, "stream_k") == 0) *value = g_stream_k.load();
     else return fail(LN_ERR_INVALID_VALUE, "unknown tuning key '%s'", key);
     return LN_SUCCESS;
 }
@@ -1127,9 +1159,13 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
                      {B, nj, 1, nj, nk, nullptr, nullptr, p.pb, p.g1.yrt, p.g1.kt},
                      {C, nl, 1, nl, nj, nullptr, nullptr, p.pc, p.g2.yrt, p.g2.kt}};
     // C is packed by the first contraction's spare CTAs when it has fewer
-    // output tiles than SMs, else here with A and B
+    // output tiles than SMs (and no stream-K, which gives every SM mainloop
+    // work), else here with A and B
     PackMulti side;
-    const bool try_side = p.g1.bn == 256 && make_pack_multi(ps + 2, 1, side) && pack_stream_eligible(side);
+    const bool try_side = p.g1.bn == 256 && !p.s1.streamk && make_pack_multi(ps + 2, 1, side) &&
+                          pack_stream_eligible(side);
+    LN_TRY(zero_streamk_flags(p.s1, st));
+    LN_TRY(zero_streamk_flags(p.s2, st));
     LN_TRY(pack_operands(ps, try_side ? 2 : 3, P, st));
     UmmaProblem g1{};
     g1.seg[0] = {p.pa, p.pb};
@@ -1222,7 +1258,11 @@ ln_status ln_3mm(int ni, int nj, int nk, int nl, int nm, const float *A, const f
                      {D, nl, 1, nl, nm, nullptr, nullptr, p.pd, p.gF.mt, p.gF.kt},
                      {C, nm, 0, nj, nm, nullptr, nullptr, p.pc, p.gF.yrt, p.gF.kt}};
     PackMulti side;
-    const bool try_side = p.gE.bn == 256 && make_pack_multi(ps + 2, 2, side) && pack_stream_eligible(side);
+    const bool try_side = p.gE.bn == 256 && !p.sE.streamk && make_pack_multi(ps + 2, 2, side) &&
+                          pack_stream_eligible(side);
+    LN_TRY(zero_streamk_flags(p.sE, st));
+    LN_TRY(zero_streamk_flags(p.sF, st));
+    LN_TRY(zero_streamk_flags(p.sG, st));
     LN_TRY(pack_operands(ps, try_side ? 2 : 4, P, st));
     UmmaProblem gE{};
     gE.seg[0] = {p.pa, p.pb};
@@ -1257,10 +1297,12 @@ ln_status ln_3mm(int ni, int nj, int nk, int nl, int nm, const float *A, const f
     gF.epi.pack = p.pf;
     gF.epi.pack_kt = p.ktF;
     // E and F are independent: when both fit on the GPU at once (one
-    // persistent CTA per work item) F runs on a second stream beside E
+    // persistent CTA per work item) F runs on a second stream beside E, then
+    // without stream-K (a stream-K launch needs all its CTAs on the GPU at once)
     const long long wE = (long long)gE.mt * gE.nt * (gE.ksplit > 1 ? gE.ksplit : 1);
     const long long wF = (long long)gF.mt * gF.nt * (gF.ksplit > 1 ? gF.ksplit : 1);
     SideStream *ss = (!try_side && wE + wF <= sm_count()) ? side_stream(st) : nullptr;
+    if (ss) gE.streamk = gF.streamk = 0;
     if (ss) {
         LN_CUDA_TRY(cudaEventRecord(ss->fork, st));
         LN_CUDA_TRY(cudaStreamWaitEvent(ss->s, ss->fork, 0));

@@ -180,6 +180,7 @@ int tune_chunk_kt();
 int tune_tile_n();
 int tune_pack_threads();  // threads per CTA of the split-and-pack stream (512 or 1024)
 int tune_split_k();       // 1: split the K range of contractions with few output tiles
+int tune_stream_k();      // 1: stream-K for general contractions with fewer tiles than SMs
 
 // ln_umma.cu: tcgen05 contraction over packed operands
 struct UmmaSeg {
@@ -206,6 +207,15 @@ struct UmmaProblem {
     float *kpart;
     int *kcnt;
     int bn;  // output tile width chosen at planning (umma_tile_n); 0: derive from epi.M, epi.N
+    // stream-K (single non-symmetric problems; 0: off): the tiles x (nseg * kt)
+    // k-tile units are split evenly over one CTA per SM. A CTA whose range starts
+    // inside a tile stores that segment's FP32 sums in skpart ([CTA][epilogue
+    // warp][EPW * 32]) and sets skflag[CTA][epilogue warp] (zero before the
+    // launch); the CTA holding the tile's first k tile adds them in k order and
+    // runs the epilogue.
+    int streamk;
+    float *skpart;
+    int *skflag;
     EpiParams epi;
 };
 // True when LN_FAULT_INJECT=timeout is set in the environment (read per call).
@@ -227,6 +237,14 @@ int umma_ksplit(long long tiles, int ktot);
 // 256-aligned in the plan).
 size_t umma_split_part_bytes(long long tiles, int ksplit, int bn);
 size_t umma_split_cnt_bytes(long long tiles, int bn);
+// Stream-K for a single general contraction of `tiles` output tiles of width bn
+// and `ktot` k tiles: 1 when the tiles leave SMs idle (fewer tiles than SMs),
+// every CTA gets at least four k tiles and the "stream_k" knob is on.
+int umma_streamk(long long tiles, int ktot);
+// Workspace of stream-K: the partial sums (one FP32 output tile per CTA) and
+// the flags (8 per CTA), which must be zero when the launch starts.
+size_t umma_streamk_part_bytes(int bn);
+size_t umma_streamk_flag_bytes();
 // With `side`, a contraction with the packing epilogue may also pack that
 // operand on SMs without an output tile; *side_done says whether it did (if
 // not, the caller packs it).

@@ -56,6 +56,16 @@ size_t umma_split_part_bytes(long long tiles, int ksplit, int bn) {
 // epilogue warps (Cfg::NEPI)
 size_t umma_split_cnt_bytes(long long tiles, int) { return (size_t)tiles * 8 * sizeof(int); }
 
+int umma_streamk(long long tiles, int ktot) {
+    const int sms = sm_count();
+    if (!tune_stream_k() || tiles <= 0 || tiles >= sms) return 0;
+    return tiles * ktot >= 4LL * sms ? 1 : 0;
+}
+
+// one FP32 output tile (128 x bn) of partial sums per CTA
+size_t umma_streamk_part_bytes(int bn) { return (size_t)sm_count() * 128 * bn * sizeof(float); }
+size_t umma_streamk_flag_bytes() { return (size_t)sm_count() * 8 * sizeof(int); }
+
 ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st, const PackMulti *side, bool *side_done) {
     if (side_done) *side_done = false;
     long long tiles = p.sym ? (long long)p.mt * (p.mt + 1) / 2 : (long long)p.mt * p.nt;
@@ -67,6 +77,7 @@ ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st, const 
         return umma_contract_sym(p, terms, st);
     }
     if (p.sym) return fail(LN_ERR_INVALID_VALUE, "symmetric problem needs the symmetric epilogue");
+    if (p.streamk && p.ksplit > 1) return fail(LN_ERR_INVALID_VALUE, "stream-K and split-K together");
     if (p.ksplit > 1) {
         if (!p.kpart || !p.kcnt) return fail(LN_ERR_INVALID_VALUE, "split-K without its workspace");
         tiles *= p.ksplit;

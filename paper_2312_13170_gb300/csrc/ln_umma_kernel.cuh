@@ -62,9 +62,22 @@ enum : int { ERR_PRODUCER = 1, ERR_MMA = 2, ERR_EPILOGUE = 4, ERR_DRAIN = 8 };
 // descriptor into shared memory; the MMA and epilogue roles read the slot and
 // release it (sempty) when they have finished the tile.
 struct SchedSlot {
-    int t, mi, ni, ks;  // work item, row tile, column tile, k slice
+    int t, mi, ni, ks;  // work item (stream-K: output tile), row tile, column tile, k slice
+    int qa, qb;         // k tiles [qa, qb) of the flattened nseg * kt range this item covers
     UmmaProblem prob;
 };
+
+// Stream-K decomposition (UmmaProblem::streamk): the tiles x ktot k-tile units
+// of a single problem, in tile-major order, are split evenly over the G CTAs of
+// the launch; CTA c covers units [sk_start(c), sk_start(c + 1)).
+__device__ __forceinline__ long long sk_start(int c, long long units, int G) { return (long long)c * units / G; }
+
+// Bounded wait until the int at f is non-zero (acquire, GPU scope).
+__device__ __forceinline__ int ld_acquire(const int *f) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+    return v;
+}
 
 // k tiles [qa, qb) of slice ks of a problem's nseg * kt flattened k range
 __device__ __forceinline__ void slice_range(const UmmaProblem &p, int ks, int &qa, int &qb) {
@@ -453,35 +466,37 @@ __device__ __forceinline__ bool block_epilogue(const EpiParams &e, float *sc, in
     const bool need_in = (EK == EK_GEMM || EK == EK_EF) && e.beta != 0.0f;
     const float *src = EK == EK_EF ? e.D : e.C;
     const long long lds = EK == EK_EF ? e.ld_ef : e.ldc;
-    // two halves of 16 rows: per half, all loads first, then the stores
+    // every load of the block (C or D) first, one latency per block; E does not
+    // wait for them
+    float4 in[8];
+    if (need_in) {
 #pragma unroll
-    for (int h0 = 0; h0 < 8; h0 += 4) {
-        float4 x[4], in[4];
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const int r = (h0 + h) * 4 + (lane >> 3);
-            x[h] = *reinterpret_cast<const float4 *>(sc + r * 32 + ((ch ^ (r & 7)) << 2));
-            if (need_in) in[h] = *reinterpret_cast<const float4 *>(src + (long long)(wrow0 + r) * lds + col);
+        for (int h = 0; h < 8; ++h) {
+            const int r = h * 4 + (lane >> 3);
+            in[h] = *reinterpret_cast<const float4 *>(src + (long long)(wrow0 + r) * lds + col);
         }
+    }
+    if (EK == EK_EF) {
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const int row = wrow0 + (h0 + h) * 4 + (lane >> 3);
-            const float4 o = x[h];
-            float4 f = make_float4(e.alpha * o.x, e.alpha * o.y, e.alpha * o.z, e.alpha * o.w);
-            if (need_in) {
-                f.x = fmaf(e.beta, in[h].x, f.x);
-                f.y = fmaf(e.beta, in[h].y, f.y);
-                f.z = fmaf(e.beta, in[h].z, f.z);
-                f.w = fmaf(e.beta, in[h].w, f.w);
-            }
-            if (EK == EK_EF) {
-                const long long off = (long long)row * e.ld_ef + col;
-                *reinterpret_cast<float4 *>(e.E + off) = o;
-                *reinterpret_cast<float4 *>(e.F + off) = f;
-            } else {
-                *reinterpret_cast<float4 *>(e.C + (long long)row * e.ldc + col) = f;
-            }
+        for (int h = 0; h < 8; ++h) {
+            const int r = h * 4 + (lane >> 3);
+            *reinterpret_cast<float4 *>(e.E + (long long)(wrow0 + r) * e.ld_ef + col) =
+                *reinterpret_cast<const float4 *>(sc + r * 32 + ((ch ^ (r & 7)) << 2));
         }
+    }
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+        const int r = h * 4 + (lane >> 3);
+        const float4 o = *reinterpret_cast<const float4 *>(sc + r * 32 + ((ch ^ (r & 7)) << 2));
+        float4 f = make_float4(e.alpha * o.x, e.alpha * o.y, e.alpha * o.z, e.alpha * o.w);
+        if (need_in) {
+            f.x = fmaf(e.beta, in[h].x, f.x);
+            f.y = fmaf(e.beta, in[h].y, f.y);
+            f.z = fmaf(e.beta, in[h].z, f.z);
+            f.w = fmaf(e.beta, in[h].w, f.w);
+        }
+        float *dst = EK == EK_EF ? e.F + (long long)(wrow0 + r) * e.ld_ef + col : e.C + (long long)(wrow0 + r) * e.ldc + col;
+        *reinterpret_cast<float4 *>(dst) = f;
     }
     __syncwarp();
     return true;
@@ -567,10 +582,25 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
         if (lane == 0) {
             int it = 0, sidx = 0;
             int next = blockIdx.x;
+            const bool sk = !BATCHED && single.streamk;
+            const int sk_ktot = single.nseg * single.kt;
+            const long long sk_units = (long long)total_tiles * sk_ktot;
+            long long sk_u = sk ? sk_start(blockIdx.x, sk_units, tile_ctas) : 0;
+            const long long sk_end = sk ? sk_start(blockIdx.x + 1, sk_units, tile_ctas) : 0;
             for (;;) {
-                int t;
-                if (queue) t = atomicAdd(queue, 1);
-                else {
+                int t, qa = 0, qb = 0;
+                if (sk) {
+                    if (sk_u < sk_end) {
+                        t = (int)(sk_u / sk_ktot);
+                        qa = (int)(sk_u - (long long)t * sk_ktot);
+                        qb = (int)(sk_end - sk_u < sk_ktot - qa ? qa + (sk_end - sk_u) : sk_ktot);
+                        sk_u += qb - qa;
+                    } else {
+                        t = -1;
+                    }
+                } else if (queue) {
+                    t = atomicAdd(queue, 1);
+                } else {
                     t = next;
                     next += tile_ctas;
                 }
@@ -579,13 +609,16 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
                 if (!wait_phase(ctl, &ctl->sempty[s], ((sidx / SCHED) & 1) ^ 1, ERR_PRODUCER, true, 64)) break;
                 SchedSlot &sl = ctl->slot[s];
                 TileRef tr{&single, 0, 0};
-                const int ksplit = (!BATCHED && single.ksplit > 1) ? single.ksplit : 1;
+                const int ksplit = (!BATCHED && !sk && single.ksplit > 1) ? single.ksplit : 1;
                 if (t >= 0) {
                     tr = resolve<BATCHED>(t / ksplit, &single, probs, prefix, owner);
                     sl.prob = *tr.p;  // roles read the problem from shared memory, not from registers
                     sl.mi = tr.mi;
                     sl.ni = tr.ni;
                     sl.ks = t - (t / ksplit) * ksplit;
+                    if (!sk) slice_range(*tr.p, sl.ks, qa, qb);
+                    sl.qa = qa;
+                    sl.qb = qb;
                 }
                 sl.t = t;
                 mbar_arrive(&ctl->sfull[s]);
@@ -594,8 +627,6 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
                 const UmmaProblem &pb = *tr.p;
                 if (pb.inject_timeout) break;  // nothing arrives on full[]: the MMA wait runs out
                 bool ok = true;
-                int qa, qb;
-                slice_range(pb, sl.ks, qa, qb);
                 {
                     for (int q = qa; q < qb; ++q) {
                         const int sg = q / pb.kt, kt = q - sg * pb.kt;
@@ -642,8 +673,7 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
                 ++sidx;
                 if (sl.t < 0) break;
                 const UmmaProblem &pb = sl.prob;
-                int qa, qb;
-                slice_range(pb, sl.ks, qa, qb);
+                const int qa = sl.qa, qb = sl.qb;
                 const int ck = pb.chunk_kt > 0 ? pb.chunk_kt : (qb - qa > 0 ? qb - qa : 1);
                 bool ok = true;
                 // one TMEM accumulator buffer per chunk of ck k tiles
@@ -705,8 +735,7 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
             if (sl.t < 0) break;
             const TileRef tr{nullptr, sl.mi, sl.ni};
             const UmmaProblem &pb = sl.prob;
-            int qa, qb;
-            slice_range(pb, sl.ks, qa, qb);
+            const int qa = sl.qa, qb = sl.qb;
             const int ck = pb.chunk_kt > 0 ? pb.chunk_kt : (qb - qa > 0 ? qb - qa : 1);
             const int nch = (qb - qa + ck - 1) / ck;
             {
@@ -772,7 +801,66 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
             }
             if (!ok) break;
             bool last = true;
-            if (!BATCHED && pb.ksplit > 1) {
+            if (!BATCHED && pb.streamk && !(qa == 0 && qb == pb.nseg * pb.kt)) {
+                // stream-K hand-off. A segment that starts inside the tile (qa > 0)
+                // is the first of its CTA's range: it publishes its FP32 sums and
+                // takes no epilogue. The segment with k tile 0 comes last in its
+                // CTA's range; it adds the later segments' sums, CTA by CTA (k
+                // order, so the result does not depend on timing), and runs the
+                // tile's epilogue.
+                const int ew = warp - C::EPI0;
+                constexpr int SLAB = EPW * 32;  // one warp's partial sums
+                if (qa > 0) {
+                    float *const mine = pb.skpart + ((size_t)blockIdx.x * C::NEPI + ew) * SLAB;
+#pragma unroll
+                    for (int q = 0; q < EPW; q += 4)
+                        *reinterpret_cast<float4 *>(mine + q * 32 + lane * 4) =
+                            make_float4(sum[q], sum[q + 1], sum[q + 2], sum[q + 3]);
+                    __threadfence();
+                    __syncwarp();
+                    if (lane == 0) atomicExch(pb.skflag + (size_t)blockIdx.x * C::NEPI + ew, 1);
+                    last = false;
+                } else {
+                    const int ktot = pb.nseg * pb.kt;
+                    const long long units = (long long)total_tiles * ktot;
+                    const long long tile_end = (long long)(sl.t + 1) * ktot;
+                    for (int c2 = blockIdx.x + 1; c2 < tile_ctas && sk_start(c2, units, tile_ctas) < tile_end && ok;
+                         ++c2) {
+                        const int *f = pb.skflag + (size_t)c2 * C::NEPI + ew;
+                        if (lane == 0) {
+                            const unsigned long long t0 = gtimer();
+                            for (uint32_t n = 0; !ld_acquire(f); ++n) {
+                                __nanosleep(64);
+                                if ((n & 15) == 15) {
+                                    if (ctl->abort) {
+                                        ok = false;
+                                        break;
+                                    }
+                                    if (gtimer() - t0 > WAIT_NS) {
+                                        ctl->abort = 1;
+                                        atomicOr(&g_umma_error, ERR_EPILOGUE);
+                                        ok = false;
+                                        break;
+                                    }
+                                }
+                            }
+                        }
+                        ok = __shfl_sync(0xffffffffu, ok, 0);
+                        if (!ok) break;
+                        __threadfence();
+                        const float *src = pb.skpart + ((size_t)c2 * C::NEPI + ew) * SLAB + lane * 4;
+#pragma unroll
+                        for (int q = 0; q < EPW; q += 4) {
+                            const float4 v = __ldcg(reinterpret_cast<const float4 *>(src + q * 32));
+                            sum[q] += v.x;
+                            sum[q + 1] += v.y;
+                            sum[q + 2] += v.z;
+                            sum[q + 3] += v.w;
+                        }
+                    }
+                    if (!ok) break;
+                }
+            } else if (!BATCHED && pb.ksplit > 1) {
                 // split-K hand-off: publish this slice's sums, count the arrival;
                 // the last slice to arrive adds all slices in slice order
                 const int ew = warp - C::EPI0;
@@ -889,12 +977,14 @@ ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int 
         }
     }
     const int sms = sm_count();
-    const int tile_ctas = total < sms ? total : sms;
+    const bool sk = single && single->streamk;
+    if (sk && (!single->skpart || !single->skflag)) return fail(LN_ERR_INVALID_VALUE, "stream-K without its workspace");
+    const int tile_ctas = sk ? sms : (total < sms ? total : sms);
     int side_ctas = 0;
     PackMulti none{};
     if (side_done) *side_done = false;
     if constexpr (EK == EK_PACK && !BATCHED && C::SIDE_OK) {
-        if (side && single && side->prefix[side->count] > 0 && pack_stream_eligible(*side)) {
+        if (!sk && side && single && side->prefix[side->count] > 0 && pack_stream_eligible(*side)) {
             // time model: a 128 x BN x 64 MMA step per product at the SM's share of
             // the BF16 peak (~0.33 us at BN = 256) against ~60 GB/s of split
             // traffic (32 KiB in, 32 KiB out per pack tile) for each spare SM

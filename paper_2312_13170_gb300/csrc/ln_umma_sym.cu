@@ -8,6 +8,7 @@ namespace ln {
 ln_status umma_contract_sym(const UmmaProblem &p, int terms, cudaStream_t st) {
     long long tiles = (long long)p.mt * (p.mt + 1) / 2;
     if (tiles == 0) return LN_SUCCESS;
+    if (p.streamk && p.ksplit > 1) return fail(LN_ERR_INVALID_VALUE, "stream-K and split-K together");
     if (p.ksplit > 1) {
         if (!p.kpart || !p.kcnt) return fail(LN_ERR_INVALID_VALUE, "split-K without its workspace");
         LN_CUDA_TRY(cudaMemsetAsync(p.kcnt, 0, umma_split_cnt_bytes(tiles, 128), st));

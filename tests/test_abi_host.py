@@ -197,3 +197,5 @@ def test_gramschmidt_validation(L):
     v = ctypes.c_int(0)
     assert L.ln_get_tuning(b"gs_rows", ctypes.byref(v)) == 0 and v.value == 4
     assert L.ln_set_tuning(b"gs_rows", 3) == 1
+    assert L.ln_get_tuning(b"stream_k", ctypes.byref(v)) == 0 and v.value == 0
+    assert L.ln_set_tuning(b"stream_k", 2) == 1
