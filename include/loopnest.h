@@ -139,6 +139,18 @@ ln_status ln_timing_read(const char *family, double *total_ms /*host*/, int *lau
  *              contractions whose output tiles fill less than half the GPU
  *              (slices exchange FP32 partial sums through the workspace; the
  *              last slice of a tile to finish adds them in slice order);
+ *   "pair"     0, 1 or 2 (default 1): CTA pairs for single tensor-core
+ *              contractions with at least two row tiles: clusters of two
+ *              CTAs compute vertically adjacent output tiles with
+ *              tcgen05.mma.cta_group::2, each holding its own rows of A and
+ *              half of the shared column tile of B; 1 pairs 256-wide general
+ *              tiles, 2 every tile width and symmetric outputs (measured
+ *              slower on 128-wide tiles), 0 none; results are bit-identical;
+ *   "stage_beta" 0 or 1 (default 1): the last 256-wide tile of each CTA of
+ *              a general tensor-core contraction with beta != 0 copies its
+ *              block of D (chain) or C (GEMM) into the operand stages once its
+ *              MMAs are done, so the epilogue stores E at once and reads D or
+ *              C from shared memory;
  *   "stream_k" 0 or 1 (default 0): stream-K for single tensor-core
  *              contractions with fewer output tiles than SMs (covariance,
  *              correlation, SYRK/SYR2K and the general contractions that do

@@ -83,6 +83,8 @@ std::atomic<int> g_pack_threads{512};
 std::atomic<int> g_split_k{0};
 std::atomic<int> g_gs_rows{4};
 std::atomic<int> g_stream_k{0};
+std::atomic<int> g_pair{1};
+std::atomic<int> g_stage_beta{1};
 }  // namespace
 
 int tune_chunk_kt() { return g_chunk_kt.load(std::memory_order_relaxed); }
@@ -91,6 +93,8 @@ int tune_pack_threads() { return g_pack_threads.load(std::memory_order_relaxed);
 int tune_split_k() { return g_split_k.load(std::memory_order_relaxed); }
 int tune_gs_rows() { return g_gs_rows.load(std::memory_order_relaxed); }
 int tune_stream_k() { return g_stream_k.load(std::memory_order_relaxed); }
+int tune_pair() { return g_pair.load(std::memory_order_relaxed); }
+int tune_stage_beta() { return g_stage_beta.load(std::memory_order_relaxed); }
 
 bool inject_timeout_requested() {
     const char *v = getenv("LN_FAULT_INJECT");
@@ -988,6 +992,16 @@ ln_status ln_set_tuning(const char *key, int value) {
         g_split_k.store(value);
         return LN_SUCCESS;
     }
+    if (strcmp(key, "stage_beta") == 0) {
+        if (value != 0 && value != 1) return fail(LN_ERR_INVALID_VALUE, "stage_beta must be 0 or 1 (got %d)", value);
+        g_stage_beta.store(value);
+        return LN_SUCCESS;
+    }
+    if (strcmp(key, "pair") == 0) {
+        if (value < 0 || value > 2) return fail(LN_ERR_INVALID_VALUE, "pair must be 0, 1 or 2 (got %d)", value);
+        g_pair.store(value);
+        return LN_SUCCESS;
+    }
     if (strcmp(key, "stream_k") == 0) {
         if (value != 0 && value != 1) return fail(LN_ERR_INVALID_VALUE, "stream_k must be 0 or 1 (got %d)", value);
         g_stream_k.store(value);
@@ -1016,6 +1030,8 @@ ln_status ln_get_tuning(const char *key, int *value) {
     else if (strcmp(key, "split_k") == 0) *value = g_split_k.load();
     else if (strcmp(key, "gs_rows") == 0) *value = g_gs_rows.load();
     else if (strcmp(key, "stream_k") == 0) *value = g_stream_k.load();
+    else if (strcmp(key, "pair") == 0) *value = g_pair.load();
+    else if (strcmp(key, "stage_beta") == 0) *value = g_stage_beta.load();
     else return fail(LN_ERR_INVALID_VALUE, "unknown tuning key '%s'", key);
     return LN_SUCCESS;
 }

@@ -181,6 +181,8 @@ int tune_tile_n();
 int tune_pack_threads();  // threads per CTA of the split-and-pack stream (512 or 1024)
 int tune_split_k();       // 1: split the K range of contractions with few output tiles
 int tune_stream_k();      // 1: stream-K for general contractions with fewer tiles than SMs
+int tune_pair();          // 1: CTA pairs sharing the column operand (UmmaProblem::pair)
+int tune_stage_beta();    // UmmaProblem::stage_beta
 
 // ln_umma.cu: tcgen05 contraction over packed operands
 struct UmmaSeg {
@@ -216,6 +218,16 @@ struct UmmaProblem {
     int streamk;
     float *skpart;
     int *skflag;
+    // CTA pairs (set by umma_contract / umma_contract_sym for single problems
+    // with at least two row tiles): the launch is clusters of two CTAs that
+    // compute vertically adjacent output tiles (row tiles 2p and 2p + 1, the
+    // same column tile) with tcgen05.mma.cta_group::2: the leader issues M = 256
+    // MMAs, each CTA holds its own 128 rows of A and half of the column tile's
+    // B, so each SM stages and reads half as much of B.
+    int pair;
+    // the "stage_beta" knob: a CTA's last 256-wide tile may stage its block of
+    // the beta input (D or C) in the stage memory after the mainloop
+    int stage_beta;
     EpiParams epi;
 };
 // True when LN_FAULT_INJECT=timeout is set in the environment (read per call).
@@ -252,6 +264,12 @@ ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st, const 
                         bool *side_done = nullptr);
 ln_status umma_contract_sym(const UmmaProblem &p, int terms, cudaStream_t st);  // ln_umma_sym.cu
 ln_status umma_read_error_sym(int *value);
+// ln_umma_pair.cu: the CTA-pair launches (tcgen05.mma.cta_group::2) of
+// umma_contract and umma_contract_sym; `total` counts pair tiles
+ln_status umma_contract_pair(int ek, const UmmaProblem &p, int terms, int bn, int total, cudaStream_t st,
+                             const PackMulti *side, bool *side_done);
+ln_status umma_contract_sym_pair(const UmmaProblem &p, int terms, int total, cudaStream_t st);
+ln_status umma_read_error_pair(int *value);
 // d_tile_owner[t] = the problem (in d_probs order) that tile t belongs to.
 ln_status umma_contract_batched(const UmmaProblem *d_probs, const int *d_tile_prefix, const int *d_tile_owner,
                                 int total_tiles, int *d_queue, int terms, cudaStream_t st);

@@ -66,8 +66,11 @@ int umma_streamk(long long tiles, int ktot) {
 size_t umma_streamk_part_bytes(int bn) { return (size_t)sm_count() * 128 * bn * sizeof(float); }
 size_t umma_streamk_flag_bytes() { return (size_t)sm_count() * 8 * sizeof(int); }
 
-ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st, const PackMulti *side, bool *side_done) {
+ln_status umma_contract(const UmmaProblem &p0, int terms, cudaStream_t st, const PackMulti *side, bool *side_done) {
     if (side_done) *side_done = false;
+    UmmaProblem p = p0;
+    p.pair = 0;
+    p.stage_beta = tune_stage_beta();
     long long tiles = p.sym ? (long long)p.mt * (p.mt + 1) / 2 : (long long)p.mt * p.nt;
     if (tiles == 0) return LN_SUCCESS;
     if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many output tiles");
@@ -84,11 +87,19 @@ ln_status umma_contract(const UmmaProblem &p, int terms, cudaStream_t st, const 
         LN_CUDA_TRY(cudaMemsetAsync(p.kcnt, 0, umma_split_cnt_bytes(tiles / p.ksplit, 0), st));
     }
     if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many work items");
+    // CTA pairs over vertically adjacent tiles ("pair" knob 1: 256-wide tiles, where
+    // they measured faster; 2: every width): `total` counts pair tiles
+    const int bn_pair = p.bn > 0 ? p.bn : umma_tile_n(terms, 0, p.epi.M, p.epi.N);
+    if ((tune_pair() == 2 || (tune_pair() == 1 && bn_pair == 256)) && p.ksplit <= 1 && !p.streamk && p.mt >= 2) {
+        p.pair = 1;
+        tiles = ceil_div(p.mt, 2) * p.nt;
+    }
     const int total = (int)tiles;
     const int bn = p.bn > 0 ? p.bn : umma_tile_n(terms, 0, p.epi.M, p.epi.N);
     if (bn != 128 && bn != 256) return fail(LN_ERR_INVALID_VALUE, "tile width %d", bn);
     if (terms > 2 && bn != 128) return fail(LN_ERR_INVALID_VALUE, "three split terms need 128-wide tiles");
     const bool wide = bn == 256;
+    if (p.pair) return umma_contract_pair(ek, p, terms, bn, total, st, side, side_done);
     switch (terms) {
         case 1:
             return wide ? launch_single<1, 256>(ek, p, total, st, side, side_done)
@@ -110,12 +121,14 @@ ln_status umma_read_error_general(int *value) {
 }
 
 ln_status umma_read_error(int *value) {
-    int a = 0, b = 0;
+    int a = 0, b = 0, c = 0;
     ln_status s = umma_read_error_general(&a);
     if (s != LN_SUCCESS) return s;
     s = umma_read_error_sym(&b);
     if (s != LN_SUCCESS) return s;
-    *value = a | b;
+    s = umma_read_error_pair(&c);
+    if (s != LN_SUCCESS) return s;
+    *value = a | b | c;
     return LN_SUCCESS;
 }
 

@@ -62,8 +62,12 @@ enum : int { ERR_PRODUCER = 1, ERR_MMA = 2, ERR_EPILOGUE = 4, ERR_DRAIN = 8 };
 // descriptor into shared memory; the MMA and epilogue roles read the slot and
 // release it (sempty) when they have finished the tile.
 struct SchedSlot {
-    int t, mi, ni, ks;  // work item (stream-K: output tile), row tile, column tile, k slice
+    int t, mi, ni, ks;  // work item (stream-K: output tile; pairs: pair tile), row tile, column tile, k slice
     int qa, qb;         // k tiles [qa, qb) of the flattened nseg * kt range this item covers
+    int ghost;          // pairs: this CTA's tile lies outside the output (or above the diagonal):
+                        // it only copies and releases its share of the pair's stages
+    int dsmem;          // the CTA's last tile: once its MMAs are done the producer copies the tile's
+                        // block of the beta input (D or C) into the freed stage memory (dfull)
     UmmaProblem prob;
 };
 
@@ -95,11 +99,13 @@ __device__ __forceinline__ void slice_range(const UmmaProblem &p, int ks, int &q
 struct Ctl {
     uint64_t full[MAX_STAGES];
     uint64_t empty[MAX_STAGES];
+    uint64_t pfull[MAX_STAGES];  // CTA pairs, leader: the peer's stage is full (relayed by the peer)
     uint64_t tfull[MAX_NACC];
     uint64_t tempty[MAX_NACC];
     uint64_t sfull[SCHED];
     uint64_t sempty[SCHED];
     uint64_t drain;
+    uint64_t dfull;  // the beta-input block of a dsmem tile is in the stage memory
     uint32_t tmem_base;
     volatile int abort;
     SchedSlot slot[SCHED];
@@ -132,6 +138,43 @@ __device__ bool wait_phase(Ctl *ctl, uint64_t *b, uint32_t parity, int who, bool
     }
 }
 
+// wait_phase with cluster-scope acquire, for barriers that the peer CTA of a
+// pair arrives on
+__device__ bool wait_phase_cl(Ctl *ctl, uint64_t *b, uint32_t parity, int who) {
+    auto probe = [&]() {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(saddr(b)), "r"(parity)
+            : "memory");
+        return ok != 0;
+    };
+    if (probe()) return true;
+    const unsigned long long t0 = gtimer();
+    for (uint32_t n = 1;; ++n) {
+        if (probe()) return true;
+        if ((n & 31) == 0) {
+            if (ctl->abort) return false;
+            if (gtimer() - t0 > WAIT_NS) {
+                ctl->abort = 1;
+                atomicOr(&g_umma_error, who);
+                return false;
+            }
+        }
+    }
+}
+
+// Arrival (release, cluster scope) on the mbarrier at bar's offset in CTA
+// `cta` of this cluster.
+__device__ __forceinline__ void mbar_arrive_remote(uint64_t *bar, uint32_t cta) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(saddr(bar)), "r"(cta));
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -147,8 +190,8 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
 }
 
 // Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+__host__ __device__ constexpr uint32_t idesc_bf16(int n, int m = BM) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 template <int BN>
@@ -160,9 +203,51 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t 
         "l"(a), "l"(b), "r"(idesc_bf16(BN)), "r"(acc)
         : "memory");
 }
+// CTA pair, issued by the leader: M = 256 (128 rows in each CTA's shared
+// memory and tensor memory), N = BN with each CTA holding BN / 2 rows of B.
+template <int BN>
+__device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc_bf16(BN, 2 * BM)), "r"(acc)
+        : "memory");
+}
+// completion of the pair's MMAs, signalled on the mbarrier at bar's offset in both CTAs
+__device__ __forceinline__ void umma_commit_pair_mc(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            saddr(bar)),
+        "h"((uint16_t)0x3)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit_pair(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+}
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
                  : "memory");
+}
+// Pair tile T of a CTA pair -> this CTA's (row tile, column tile), and whether
+// that tile is a ghost. General problems: row-tile pairs (2p, 2p + 1) times the
+// nt column tiles. Symmetric problems: row-tile pair p with the column tiles
+// 0 .. min(2p + 1, mt - 1); the tile of row 2p and column 2p + 1 lies above the
+// diagonal.
+__device__ __forceinline__ void pair_tile(const UmmaProblem &p, int T, int rank, int &mi, int &ni, int &ghost) {
+    int pr;
+    if (p.sym) {
+        pr = (int)((sqrtf(4.0f * (float)T + 1.0f) - 1.0f) * 0.5f);
+        while ((pr + 1) * (pr + 2) <= T) ++pr;
+        while (pr * (pr + 1) > T) --pr;
+        ni = T - pr * (pr + 1);
+    } else {
+        pr = T / p.nt;
+        ni = T - pr * p.nt;
+    }
+    mi = 2 * pr + rank;
+    ghost = mi >= p.mt || (p.sym && ni > mi);
 }
 
 // 32 lanes x 16 consecutive columns, without the wait: r is valid only after
@@ -252,7 +337,7 @@ struct Products<3> {  // the six products of order >= 2^-16
 //  TMEM: NACC = 512 / BN accumulator buffers of BN columns.
 // EPW: columns per epilogue warp (128, or 64 for symmetric outputs, whose
 // element-wise epilogue is latency-bound and gains from twice the warps).
-template <int P, int BN, int EPW = 128>
+template <int P, int BN, int EPW = 128, int PAIR = 0>
 struct Cfg {
     static constexpr int NEPI = 4 * BN / EPW;  // epilogue warps: 4 (one per TMEM lane quarter) per EPW columns
     // first epilogue warp: eight epilogue warps make two whole warpgroups
@@ -269,7 +354,9 @@ struct Cfg {
     static constexpr int NACC = TMEM_COLS / BN;
     static constexpr int HALVES = BN / 128;
     static constexpr int A_BYTES = P * PK_TILE_BYTES;
-    static constexpr int B_BYTES = P * HALVES * PK_TILE_BYTES;
+    // CTA pairs: each CTA holds BN / 2 rows of every B term (BN * 64 bytes)
+    static constexpr int BH_BYTES = BN * 64;
+    static constexpr int B_BYTES = PAIR ? P * BH_BYTES : P * HALVES * PK_TILE_BYTES;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int SCRATCH_BYTES = NEPI * 32 * 32 * 4;  // one 32 x 32 FP32 block per epilogue warp
     // 1 KiB of slack lets the kernel align the control block and stages to 1 KiB
@@ -277,6 +364,10 @@ struct Cfg {
     static constexpr int STAGES = STAGES_RAW > MAX_STAGES ? MAX_STAGES : STAGES_RAW;
     static constexpr int SMEM = 1024 + CTL_BYTES + STAGES * STAGE_BYTES + SCRATCH_BYTES;
     static constexpr int NLD = (BN == 128 && EPW == 128) ? 4 : 2;  // tcgen05.ld (x16) in flight per wait
+    // a tile's FP32 block of the beta input fits in the stage memory; staged for
+    // 256-wide tiles only (on 128-wide ones, loading it after the mainloop
+    // measured slower than the epilogue's own loads)
+    static constexpr bool DSMEM_OK = BN == 256 && BM * BN * 4 <= STAGES * STAGE_BYTES;
     static_assert((EPW == 64 || EPW == 128) && NEPI <= 8, "epilogue width");
     static_assert(NACC <= MAX_NACC && STAGES >= 2, "tile configuration does not fit");
     static_assert(!REG_SPLIT || (128 * REG_LO + 32 * NEPI * REG_HI <= REG_LAUNCH * NTHREADS && REG_HI <= 256 &&
@@ -502,6 +593,54 @@ __device__ __forceinline__ bool block_epilogue(const EpiParams &e, float *sc, in
     return true;
 }
 
+// The same block layout for a tile whose beta input sits in shared memory
+// (SchedSlot::dsmem): E alone, then F = alpha * acc + beta * D (EK_EF) or
+// C = alpha * acc + beta * C (EK_GEMM) with D or C read from `ds` (the warp's
+// rows of the staged block, row pitch `pitch` floats). The tile is wholly
+// inside the output and its rows 16-byte aligned (checked when it was staged).
+__device__ __forceinline__ void block_stage(float *sc, const float *v, int lane) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        *reinterpret_cast<float4 *>(sc + lane * 32 + ((k ^ (lane & 7)) << 2)) =
+            make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    __syncwarp();
+}
+
+__device__ __forceinline__ void block_store_e(const EpiParams &e, float *sc, int wrow0, int c0, const float *v,
+                                              int lane) {
+    block_stage(sc, v, lane);
+    const int ch = lane & 7;
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+        const int r = h * 4 + (lane >> 3);
+        *reinterpret_cast<float4 *>(e.E + (long long)(wrow0 + r) * e.ld_ef + c0 + ch * 4) =
+            *reinterpret_cast<const float4 *>(sc + r * 32 + ((ch ^ (r & 7)) << 2));
+    }
+    __syncwarp();
+}
+
+template <int EK>
+__device__ __forceinline__ void block_store_f(const EpiParams &e, float *sc, int wrow0, int c0, const float *v,
+                                              int lane, const float *ds, int pitch) {
+    block_stage(sc, v, lane);
+    const int ch = lane & 7;
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+        const int r = h * 4 + (lane >> 3);
+        const float4 o = *reinterpret_cast<const float4 *>(sc + r * 32 + ((ch ^ (r & 7)) << 2));
+        const float4 d = *reinterpret_cast<const float4 *>(ds + (size_t)r * pitch + ch * 4);
+        float4 f;
+        f.x = fmaf(e.beta, d.x, e.alpha * o.x);
+        f.y = fmaf(e.beta, d.y, e.alpha * o.y);
+        f.z = fmaf(e.beta, d.z, e.alpha * o.z);
+        f.w = fmaf(e.beta, d.w, e.alpha * o.w);
+        float *dst = EK == EK_EF ? e.F + (long long)(wrow0 + r) * e.ld_ef + c0 + ch * 4
+                                 : e.C + (long long)(wrow0 + r) * e.ldc + c0 + ch * 4;
+        *reinterpret_cast<float4 *>(dst) = f;
+    }
+    __syncwarp();
+}
+
 // ---------------------------------------------------------------- the kernel
 // Grid: tile_ctas CTAs take output tiles (static stride tile_ctas, or the
 // queue); CTAs from tile_ctas on (only launched for single problems with the
@@ -510,16 +649,17 @@ __device__ __forceinline__ bool block_epilogue(const EpiParams &e, float *sc, in
 template <int EK>
 constexpr int epi_width() { return EK == EK_SYM ? 64 : 128; }
 
-template <int P, int BN, int BATCHED, int EK>
-__global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_umma(const __grid_constant__ UmmaProblem single,
+template <int P, int BN, int BATCHED, int EK, int PAIR = 0>
+__global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>(), PAIR>::NTHREADS, 1) void k_umma(const __grid_constant__ UmmaProblem single,
                                                                   const UmmaProblem *__restrict__ probs,
                                                                   const int *__restrict__ prefix,
                                                                   const int *__restrict__ owner, int total_tiles,
                                                                   int *queue, const __grid_constant__ PackMulti side,
                                                                   int tile_ctas) {
-    using C = Cfg<P, BN, epi_width<EK>()>;
+    using C = Cfg<P, BN, epi_width<EK>(), PAIR>;
     constexpr int EPW = epi_width<EK>();
     using PR = Products<P>;
+    static_assert(!PAIR || !BATCHED, "CTA pairs take single problems");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment of the stage area is required by the 128-byte swizzle.
     const uint32_t raw = saddr(smem_raw);
@@ -540,32 +680,52 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+    // CTA pairs (PAIR): the leader (rank 0) issues the pair's MMAs; its tensor
+    // memory buffers are released by both CTAs' epilogue warps
+    constexpr bool pair = PAIR != 0;
+    const int rank = pair ? (int)cluster_rank() : 0;
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(&ctl->full[s], 1);
             mbar_init(&ctl->empty[s], 1);
+            mbar_init(&ctl->pfull[s], 1);
         }
         for (int b = 0; b < C::NACC; ++b) {
             mbar_init(&ctl->tfull[b], 1);
-            mbar_init(&ctl->tempty[b], C::NEPI);
+            mbar_init(&ctl->tempty[b], pair ? 2 * C::NEPI : C::NEPI);
         }
         for (int s = 0; s < SCHED; ++s) {
             mbar_init(&ctl->sfull[s], 1);
             mbar_init(&ctl->sempty[s], 1 + C::NEPI);
         }
         mbar_init(&ctl->drain, 1);
+        mbar_init(&ctl->dfull, 1);
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&ctl->tmem_base)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if constexpr (pair) {
+            // allocated collectively by one warp of each CTA of the pair: the same
+            // columns in both CTAs' tensor memory
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             saddr(&ctl->tmem_base)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             saddr(&ctl->tmem_base)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     tc_fence_before();
     __syncthreads();
+    // the peer copies into this CTA's stages and arrives on its barriers only
+    // after both CTAs have initialised theirs
+    if (pair) cluster_sync();
     tc_fence_after();
     const uint32_t tmem = ctl->tmem_base;
     // everything above touched only shared memory and TMEM: with a programmatic
@@ -581,7 +741,9 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             int it = 0, sidx = 0;
-            int next = blockIdx.x;
+            bool dsm_issued = false;
+            int next = pair ? (int)blockIdx.x >> 1 : (int)blockIdx.x;
+            const int stride = pair ? tile_ctas >> 1 : tile_ctas;
             const bool sk = !BATCHED && single.streamk;
             const int sk_ktot = single.nseg * single.kt;
             const long long sk_units = (long long)total_tiles * sk_ktot;
@@ -602,7 +764,7 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
                     t = atomicAdd(queue, 1);
                 } else {
                     t = next;
-                    next += tile_ctas;
+                    next += stride;
                 }
                 if (t >= total_tiles) t = -1;
                 const int s = sidx % SCHED;
@@ -610,7 +772,17 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
                 SchedSlot &sl = ctl->slot[s];
                 TileRef tr{&single, 0, 0};
                 const int ksplit = (!BATCHED && !sk && single.ksplit > 1) ? single.ksplit : 1;
-                if (t >= 0) {
+                sl.ghost = 0;
+                if (t >= 0 && pair) {
+                    pair_tile(single, t, rank, tr.mi, tr.ni, sl.ghost);
+                    sl.prob = single;
+                    sl.mi = tr.mi;
+                    sl.ni = tr.ni;
+                    sl.ks = 0;
+                    slice_range(single, 0, qa, qb);
+                    sl.qa = qa;
+                    sl.qb = qb;
+                } else if (t >= 0) {
                     tr = resolve<BATCHED>(t / ksplit, &single, probs, prefix, owner);
                     sl.prob = *tr.p;  // roles read the problem from shared memory, not from registers
                     sl.mi = tr.mi;
@@ -620,12 +792,23 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
                     sl.qa = qa;
                     sl.qb = qb;
                 }
+                sl.dsmem = 0;
+                if constexpr ((EK == EK_EF || EK == EK_GEMM) && !BATCHED && C::DSMEM_OK) {
+                    // the last tile of a statically scheduled CTA, wholly inside an aligned output
+                    const EpiParams &e = single.epi;
+                    const float *src = EK == EK_EF ? e.D : e.C;
+                    const long long ld = EK == EK_EF ? e.ld_ef : e.ldc;
+                    sl.dsmem = single.stage_beta && t >= 0 && !queue && !sk && ksplit <= 1 && next >= total_tiles &&
+                               !sl.ghost &&
+                               e.beta != 0.0f && tr.mi * BM + BM <= e.M && tr.ni * BN + BN <= e.N && aligned16(src, ld);
+                }
                 sl.t = t;
                 mbar_arrive(&ctl->sfull[s]);
                 ++sidx;
                 if (t < 0) break;
                 const UmmaProblem &pb = *tr.p;
                 if (pb.inject_timeout) break;  // nothing arrives on full[]: the MMA wait runs out
+                const bool ghost = sl.ghost;
                 bool ok = true;
                 {
                     for (int q = qa; q < qb; ++q) {
@@ -636,8 +819,22 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
                             ok = false;
                             break;
                         }
-                        mbar_expect_tx(&ctl->full[st], C::STAGE_BYTES);
                         const uint32_t dst = stage0 + st * C::STAGE_BYTES;
+                        if constexpr (pair) {
+                            // own rows of A; this CTA's BN / 2 rows of every B term
+                            mbar_expect_tx(&ctl->full[st], ghost ? C::B_BYTES : C::STAGE_BYTES);
+                            if (!ghost) bulk_g2s(dst, xb + (size_t)kt * C::A_BYTES, C::A_BYTES, &ctl->full[st]);
+                            const int brt = BN == 256 ? tr.ni * 2 + rank : tr.ni;  // packed 128-row tile of B
+                            const uint32_t boff = BN == 256 ? 0u : (uint32_t)rank * C::BH_BYTES;
+                            const char *yb = pb.seg[sg].Y + ((size_t)brt * pb.y_kt + kt) * C::A_BYTES + boff;
+#pragma unroll
+                            for (int q = 0; q < P; ++q)
+                                bulk_g2s(dst + C::A_BYTES + q * C::BH_BYTES, yb + q * PK_TILE_BYTES, C::BH_BYTES,
+                                         &ctl->full[st]);
+                            ++it;
+                            continue;
+                        }
+                        mbar_expect_tx(&ctl->full[st], C::STAGE_BYTES);
                         bulk_g2s(dst, xb + (size_t)kt * C::A_BYTES, C::A_BYTES, &ctl->full[st]);
                         if (C::HALVES == 1) {
                             const char *yb = pb.seg[sg].Y + ((size_t)tr.ni * pb.y_kt + kt) * C::A_BYTES;
@@ -657,10 +854,28 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
                     }
                 }
                 if (!ok) break;
+                if constexpr ((EK == EK_EF || EK == EK_GEMM) && !BATCHED && C::DSMEM_OK) {
+                    if (sl.dsmem) {
+                        // every stage has been read by the MMAs (its empty phase completed):
+                        // the stage memory now takes the tile's rows of D (or C)
+                        for (int j = (it > C::STAGES ? it - C::STAGES : 0); j < it && ok; ++j)
+                            ok = wait_phase(ctl, &ctl->empty[j % C::STAGES], (j / C::STAGES) & 1, ERR_PRODUCER, true,
+                                            32);
+                        if (!ok) break;
+                        const EpiParams &e = pb.epi;
+                        const float *src = EK == EK_EF ? e.D : e.C;
+                        const long long ld = EK == EK_EF ? e.ld_ef : e.ldc;
+                        const float *row0 = src + (long long)tr.mi * BM * ld + (long long)tr.ni * BN;
+                        mbar_expect_tx(&ctl->dfull, BM * BN * 4);
+                        for (int r = 0; r < BM; ++r) bulk_g2s(stage0 + r * BN * 4, row0 + r * ld, BN * 4, &ctl->dfull);
+                        dsm_issued = true;
+                    }
+                }
             }
             // wait for this CTA's copies still in flight
             for (int j = (it > C::STAGES ? it - C::STAGES : 0); j < it; ++j)
                 wait_phase(ctl, &ctl->full[j % C::STAGES], (j / C::STAGES) & 1, ERR_DRAIN, false, 256);
+            if (dsm_issued) wait_phase(ctl, &ctl->dfull, 0, ERR_DRAIN, false, 256);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
@@ -676,10 +891,28 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
                 const int qa = sl.qa, qb = sl.qb;
                 const int ck = pb.chunk_kt > 0 ? pb.chunk_kt : (qb - qa > 0 ? qb - qa : 1);
                 bool ok = true;
-                // one TMEM accumulator buffer per chunk of ck k tiles
+                if (pair && rank != 0) {
+                    // the peer of a pair issues no MMA: it tells the leader when each
+                    // of its stages is full
+                    for (int q = qa; q < qb; ++q) {
+                        const int st = it % C::STAGES;
+                        if (!wait_phase(ctl, &ctl->full[st], (it / C::STAGES) & 1, ERR_MMA)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_remote(&ctl->pfull[st], 0);
+                        ++it;
+                    }
+                    if (!ok) break;
+                    mbar_arrive(&ctl->sempty[s]);
+                    continue;
+                }
+                // one TMEM accumulator buffer per chunk of ck k tiles (pairs: the
+                // leader computes both CTAs' tiles, ghosts included)
                 for (int q0 = qa; q0 < qb && ok; q0 += ck) {
                     const int b = acc % C::NACC;
-                    if (!wait_phase(ctl, &ctl->tempty[b], ((acc / C::NACC) & 1) ^ 1, ERR_MMA)) {
+                    if (!(pair ? wait_phase_cl(ctl, &ctl->tempty[b], ((acc / C::NACC) & 1) ^ 1, ERR_MMA)
+                               : wait_phase(ctl, &ctl->tempty[b], ((acc / C::NACC) & 1) ^ 1, ERR_MMA))) {
                         ok = false;
                         break;
                     }
@@ -688,7 +921,8 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
                     const int q1 = q0 + ck < qb ? q0 + ck : qb;
                     for (int q = q0; q < q1; ++q) {
                         const int st = it % C::STAGES;
-                        if (!wait_phase(ctl, &ctl->full[st], (it / C::STAGES) & 1, ERR_MMA)) {
+                        if (!wait_phase(ctl, &ctl->full[st], (it / C::STAGES) & 1, ERR_MMA) ||
+                            (pair && !wait_phase_cl(ctl, &ctl->pfull[st], (it / C::STAGES) & 1, ERR_MMA))) {
                             ok = false;
                             break;
                         }
@@ -700,23 +934,38 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
 #pragma unroll
                             for (int ks = 0; ks < PK_K / 16; ++ks) {
                                 const uint64_t ad = sw128_desc(a0 + PR::a(pr) * PK_TILE_BYTES + ks * 32);
-                                const uint64_t bd = sw128_desc(b0 + PR::b(pr) * C::HALVES * PK_TILE_BYTES + ks * 32);
-                                umma_bf16<BN>(d, ad, bd, ((q - q0) | pr | ks) ? 1u : 0u);
+                                if constexpr (pair) {
+                                    const uint64_t bd = sw128_desc(b0 + PR::b(pr) * C::BH_BYTES + ks * 32);
+                                    umma_bf16_pair<BN>(d, ad, bd, ((q - q0) | pr | ks) ? 1u : 0u);
+                                } else {
+                                    const uint64_t bd =
+                                        sw128_desc(b0 + PR::b(pr) * C::HALVES * PK_TILE_BYTES + ks * 32);
+                                    umma_bf16<BN>(d, ad, bd, ((q - q0) | pr | ks) ? 1u : 0u);
+                                }
                             }
                         }
-                        umma_commit(&ctl->empty[st]);
+                        if constexpr (pair) umma_commit_pair_mc(&ctl->empty[st]);
+                        else umma_commit(&ctl->empty[st]);
                         ++it;
                     }
                     if (!ok) break;
-                    umma_commit(&ctl->tfull[b]);
+                    if constexpr (pair) umma_commit_pair_mc(&ctl->tfull[b]);
+                    else umma_commit(&ctl->tfull[b]);
                     ++acc;
                 }
                 if (!ok) break;
                 mbar_arrive(&ctl->sempty[s]);
             }
             // every MMA this thread issued has completed before TMEM is freed
-            umma_commit(&ctl->drain);
-            wait_phase(ctl, &ctl->drain, 0, ERR_DRAIN, false, 256);
+            if constexpr (pair) {
+                if (rank == 0) {
+                    umma_commit_pair(&ctl->drain);
+                    wait_phase(ctl, &ctl->drain, 0, ERR_DRAIN, false, 256);
+                }
+            } else {
+                umma_commit(&ctl->drain);
+                wait_phase(ctl, &ctl->drain, 0, ERR_DRAIN, false, 256);
+            }
         }
     }
     } else {
@@ -733,6 +982,28 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
             const SchedSlot &sl = ctl->slot[s];
             ++sidx;
             if (sl.t < 0) break;
+            if (sl.ghost) {
+                // pairs: nothing of this tile is stored; the leader still computed it
+                // into this CTA's tensor memory, so each chunk is waited for and
+                // released as usual
+                const int gck = sl.prob.chunk_kt > 0 ? sl.prob.chunk_kt : (sl.qb - sl.qa > 0 ? sl.qb - sl.qa : 1);
+                const int gnch = (sl.qb - sl.qa + gck - 1) / gck;
+                for (int c = 0; c < gnch && ok; ++c) {
+                    const int b = acc % C::NACC;
+                    ok = wait_phase(ctl, &ctl->tfull[b], (acc / C::NACC) & 1, ERR_EPILOGUE, true, 128);
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (!ok) break;
+                    tc_fence_after();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_remote(&ctl->tempty[b], 0);
+                    ++acc;
+                }
+                if (!ok) break;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ctl->sempty[s]);
+                continue;
+            }
             const TileRef tr{nullptr, sl.mi, sl.ni};
             const UmmaProblem &pb = sl.prob;
             const int qa = sl.qa, qb = sl.qb;
@@ -796,7 +1067,10 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&ctl->tempty[b]);
+                if (lane == 0) {
+                    if constexpr (pair) mbar_arrive_remote(&ctl->tempty[b], 0);  // the leader's buffer
+                    else mbar_arrive(&ctl->tempty[b]);
+                }
                 ++acc;
             }
             if (!ok) break;
@@ -915,6 +1189,23 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
                     for (int cc = 0; cc < 4; ++cc)
                         store_chunk<P>(tile0, rloc, (g & 1) * 4 + cc, &sum[g * 32 + cc * 8]);
                 }
+            } else if ((EK == EK_EF || EK == EK_GEMM) && sl.dsmem) {
+                // the beta input of this tile arrives in the stage memory (dfull):
+                // E first, which does not need it, then F (or C) from it
+                float *sc = scratch + (warp - C::EPI0) * 1024;
+                const int wrow0 = tr.mi * BM + quarter * 32;
+                if constexpr (EK == EK_EF) {
+#pragma unroll
+                    for (int g = 0; g < EPW / 32; ++g) block_store_e(e, sc, wrow0, col0 + g * 32, &sum[g * 32], lane);
+                }
+                ok = wait_phase(ctl, &ctl->dfull, 0, ERR_EPILOGUE, true, 128);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                const float *ds = reinterpret_cast<const float *>(smem_raw + pad + CTL_BYTES) +
+                                  (size_t)(quarter * 32) * BN + col_base;
+#pragma unroll
+                for (int g = 0; g < EPW / 32; ++g)
+                    block_store_f<EK>(e, sc, wrow0, col0 + g * 32, &sum[g * 32], lane, ds + g * 32, BN);
             } else {
                 float *sc = scratch + (warp - C::EPI0) * 1024;
                 const int wrow0 = tr.mi * BM + quarter * 32;
@@ -936,21 +1227,27 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>()>::NTHREADS, 1) void k_um
 
     tc_fence_before();
     __syncthreads();
+    // neither CTA of a pair leaves while the other may still copy into its
+    // stages or arrive on its barriers
+    if (pair) cluster_sync();
     if (warp == 1) {
         tc_fence_after();
         __syncwarp();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        if constexpr (pair)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
 }
 
 // With `side` (single problems, packing epilogue, Cfg::SIDE_OK), CTAs beyond
 // the tile CTAs pack that operand when enough SMs are free to finish it within
 // the contraction's own time; *side_done reports whether they were launched.
-template <int P, int BN, int BATCHED, int EK>
+template <int P, int BN, int BATCHED, int EK, int PAIR = 0>
 ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int *prefix, const int *owner, int total,
                  int *queue, cudaStream_t st, const PackMulti *side = nullptr, bool *side_done = nullptr) {
-    using C = Cfg<P, BN, epi_width<EK>()>;
-    auto kern = k_umma<P, BN, BATCHED, EK>;
+    using C = Cfg<P, BN, epi_width<EK>(), PAIR>;
+    auto kern = k_umma<P, BN, BATCHED, EK, PAIR>;
     // the shared-memory opt-in is set once per device (so nothing but launches
     // happens while a caller captures a graph)
     static bool attr_set[64] = {false};
@@ -979,7 +1276,36 @@ ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int 
     const int sms = sm_count();
     const bool sk = single && single->streamk;
     if (sk && (!single->skpart || !single->skflag)) return fail(LN_ERR_INVALID_VALUE, "stream-K without its workspace");
-    const int tile_ctas = sk ? sms : (total < sms ? total : sms);
+    constexpr bool pair = PAIR != 0;
+    if (pair && (!single || !single->pair || sk || single->ksplit > 1))
+        return fail(LN_ERR_INVALID_VALUE, "CTA pairs need a single problem without stream-K or split-K");
+    // pairs: `total` counts pair tiles, two CTAs each, at most as many pairs as
+    // the GPU holds at once (both CTAs of a pair share a GPC)
+    int max_pairs = sms / 2;
+    if (pair) {
+        static int cached[64] = {0};
+        if (dev >= 0 && dev < 64 && cached[dev] > 0) {
+            max_pairs = cached[dev];
+        } else {
+            cudaLaunchConfig_t qc{};
+            qc.gridDim = dim3((unsigned)(2 * max_pairs));
+            qc.blockDim = dim3(C::NTHREADS);
+            qc.dynamicSmemBytes = C::SMEM;
+            cudaLaunchAttribute qa[1];
+            qa[0].id = cudaLaunchAttributeClusterDimension;
+            qa[0].val.clusterDim.x = 2;
+            qa[0].val.clusterDim.y = 1;
+            qa[0].val.clusterDim.z = 1;
+            qc.attrs = qa;
+            qc.numAttrs = 1;
+            int n = 0;
+            LN_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n, kern, &qc));
+            if (n <= 0) return fail(LN_ERR_UNSUPPORTED, "no cluster of two CTAs of the tcgen05 kernel fits");
+            max_pairs = n < sms / 2 ? n : sms / 2;
+            if (dev >= 0 && dev < 64) cached[dev] = max_pairs;
+        }
+    }
+    const int tile_ctas = sk ? sms : pair ? 2 * (total < max_pairs ? total : max_pairs) : (total < sms ? total : sms);
     int side_ctas = 0;
     PackMulti none{};
     if (side_done) *side_done = false;
@@ -990,8 +1316,9 @@ ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int 
             // traffic (32 KiB in, 32 KiB out per pack tile) for each spare SM
             const int ktot = single->nseg * single->kt;
             const int kslice = single->ksplit > 1 ? (ktot + single->ksplit - 1) / single->ksplit : ktot;
-            const double mma_us = ceil_div(total, tile_ctas) * (double)kslice * Products<P>::n * 0.33 * (BN / 256.0);
-            const int free_sms = sms - tile_ctas;
+            const double mma_us =
+                ceil_div(total, pair ? tile_ctas / 2 : tile_ctas) * (double)kslice * Products<P>::n * 0.33 * (BN / 256.0);
+            const int free_sms = pair ? 2 * max_pairs - tile_ctas : sms - tile_ctas;
             const double pack_us =
                 free_sms > 0 ? side->prefix[side->count] * 65536.0 / (free_sms * 60e3) : 1e30;
             if (pack_us <= 0.8 * mma_us) side_ctas = free_sms;
@@ -1005,11 +1332,15 @@ ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int 
         cfg.blockDim = dim3(C::NTHREADS);
         cfg.dynamicSmemBytes = C::SMEM;
         cfg.stream = st;
-        cudaLaunchAttribute attr[1];
+        cudaLaunchAttribute attr[2];
         attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         attr[0].val.programmaticStreamSerializationAllowed = 1;
+        attr[1].id = cudaLaunchAttributeClusterDimension;
+        attr[1].val.clusterDim.x = 2;
+        attr[1].val.clusterDim.y = 1;
+        attr[1].val.clusterDim.z = 1;
         cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        cfg.numAttrs = pair ? 2 : 1;
         const cudaError_t le = cudaLaunchKernelEx(&cfg, kern, single ? *single : dummy, probs, prefix, owner, total,
                                                   queue, side_ctas ? *side : none, tile_ctas);
         if (le != cudaSuccess) return fail(LN_ERR_CUDA, "tcgen05 contraction launch: %s", cudaGetErrorString(le));

@@ -1,11 +1,15 @@
 // Instantiations of the tcgen05 contraction kernel (ln_umma_kernel.cuh) for
 // symmetric problems (covariance, correlation, SYRK/SYR2K): lower-triangle
 // square tiles with mirrored stores, single and batched (device tile queue).
+#include <algorithm>
+
 #include "ln_umma_kernel.cuh"
 
 namespace ln {
 
-ln_status umma_contract_sym(const UmmaProblem &p, int terms, cudaStream_t st) {
+ln_status umma_contract_sym(const UmmaProblem &p0, int terms, cudaStream_t st) {
+    UmmaProblem p = p0;
+    p.pair = 0;
     long long tiles = (long long)p.mt * (p.mt + 1) / 2;
     if (tiles == 0) return LN_SUCCESS;
     if (p.streamk && p.ksplit > 1) return fail(LN_ERR_INVALID_VALUE, "stream-K and split-K together");
@@ -13,9 +17,15 @@ ln_status umma_contract_sym(const UmmaProblem &p, int terms, cudaStream_t st) {
         if (!p.kpart || !p.kcnt) return fail(LN_ERR_INVALID_VALUE, "split-K without its workspace");
         LN_CUDA_TRY(cudaMemsetAsync(p.kcnt, 0, umma_split_cnt_bytes(tiles, 128), st));
         tiles *= p.ksplit;
+    } else if (tune_pair() == 2 && !p.streamk && p.mt >= 2) {  // measured slower on 128-wide tiles: opt-in
+        // CTA pairs: row-tile pair q covers the column tiles 0 .. min(2q + 1, mt - 1)
+        p.pair = 1;
+        tiles = 0;
+        for (long long q = 0; q < ceil_div(p.mt, 2); ++q) tiles += std::min<long long>(2 * q + 2, p.mt);
     }
     if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many output tiles");
     const int total = (int)tiles;
+    if (p.pair) return umma_contract_sym_pair(p, terms, total, st);
     switch (terms) {
         case 1: return launch<1, 128, 0, EK_SYM>(&p, nullptr, nullptr, nullptr, total, nullptr, st);
         case 2: return launch<2, 128, 0, EK_SYM>(&p, nullptr, nullptr, nullptr, total, nullptr, st);

@@ -199,3 +199,7 @@ def test_gramschmidt_validation(L):
     assert L.ln_set_tuning(b"gs_rows", 3) == 1
     assert L.ln_get_tuning(b"stream_k", ctypes.byref(v)) == 0 and v.value == 0
     assert L.ln_set_tuning(b"stream_k", 2) == 1
+    assert L.ln_get_tuning(b"pair", ctypes.byref(v)) == 0 and v.value == 1
+    assert L.ln_set_tuning(b"pair", 3) == 1
+    assert L.ln_get_tuning(b"stage_beta", ctypes.byref(v)) == 0 and v.value == 1
+    assert L.ln_set_tuning(b"stage_beta", 2) == 1
