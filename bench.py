@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the CPU baseline sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
+    ap.add_argument("--no-suite", action="store_true",
+                    help="skip the per-workload suite object of the benchmark line (profiling runs)")
     ap.add_argument("--suite", action="store_true", help="measure every workload and form, one JSON line each")
     ap.add_argument("--only", default="",
                     help="suite: comma-separated workloads (gemm,chain,3mm,cov,batched,backward,gramschmidt)")
@@ -167,25 +169,44 @@ def dist_setup():
 
 
 # ---------------------------------------------------------------- CPU (oracle) leg
+def host_cores():
+    """Cores this process may run on (its CPU affinity mask)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def cpu_sample(d, target_s, rows_max=N):
     """Time the FP64 oracle on the first R rows of the chain (E rows depend
-    only on the same rows of A and D); R is calibrated to ~target_s."""
+    only on the same rows of A and D), on every core of this process's
+    affinity mask (R calibrated to ~target_s) and on one core (a smaller
+    sample, ~target_s / 3)."""
     import oracle
 
     oracle.build()
-    cores = oracle.max_threads()
-    r = 4
-    t0 = time.perf_counter()
-    oracle.gemm_chain(d["A"][:r], d["B"], d["C"], d["D"][:r], d["alpha"], d["beta"])
-    dt = max(time.perf_counter() - t0, 1e-4)
-    R = int(min(rows_max, max(r, r * target_s / dt)))
-    t0 = time.perf_counter()
-    E_rows, F_rows = oracle.gemm_chain(d["A"][:R], d["B"], d["C"], d["D"][:R], d["alpha"], d["beta"])
-    dt = time.perf_counter() - t0
-    gflops = 4.0 * R * N * N / dt / 1e9
-    return {"value": gflops, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {R} of {N} rows of E and F (4*{R}*{N}^2 flops), {dt:.2f} s",
-            "seconds": dt}, R, E_rows, F_rows
+    cores = host_cores()
+
+    def calibrated(threads, seconds):
+        oracle.set_threads(threads)
+        r = 4
+        t0 = time.perf_counter()
+        oracle.gemm_chain(d["A"][:r], d["B"], d["C"], d["D"][:r], d["alpha"], d["beta"])
+        dt = max(time.perf_counter() - t0, 1e-4)
+        R = int(min(rows_max, max(r, r * seconds / dt)))
+        t0 = time.perf_counter()
+        E_rows, F_rows = oracle.gemm_chain(d["A"][:R], d["B"], d["C"], d["D"][:R], d["alpha"], d["beta"])
+        return R, time.perf_counter() - t0, E_rows, F_rows
+
+    R, dt, E_rows, F_rows = calibrated(cores, target_s)
+    R1, dt1, _, _ = calibrated(1, target_s / 3.0)
+    oracle.set_threads(cores)
+    base = {"value": 4.0 * R * N * N / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {R} of {N} rows of E and F (4*{R}*{N}^2 flops), {dt:.2f} s on {cores} cores",
+            "seconds": dt,
+            "one_core": {"value": 4.0 * R1 * N * N / dt1 / 1e9, "unit": "GFLOP/s", "cores": 1,
+                         "sample": f"first {R1} of {N} rows, {dt1:.2f} s"}}
+    return base, R, E_rows, F_rows
 
 
 def run_reference(args):
@@ -197,7 +218,8 @@ def run_reference(args):
 
     oracle.build()
     d = inputs.chain_inputs(N, seed=0)
-    cores = oracle.max_threads()
+    cores = host_cores()
+    oracle.set_threads(cores)
     # calibrate a per-step sample of about 1 s
     r = 4
     t0 = time.perf_counter()
@@ -415,6 +437,15 @@ def run_own(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if rank == 0 and not args.no_suite:
+        # every gated workload measured in this same run (after the timed
+        # steps above, so it does not disturb them): plain FP32, tiled FP32 and
+        # the gated 3xBF16 tensor-core form
+        records = []
+        t_suite = time.perf_counter()
+        suite_lines(SUITE_MODES, ALL_WORKLOADS, 5, records.append)
+        line["suite"] = suite_summary(records)
+        line["suite_seconds"] = round(time.perf_counter() - t_suite, 1)
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu, R, E_rows, F_rows = cpu_sample(d, args.cpu_seconds)
         line["cpu_baseline"] = cpu
@@ -429,25 +460,21 @@ def run_own(args):
 
 
 # ---------------------------------------------------------------- suite: every workload, every form
-def run_suite(args):
-    """One JSON line per (workload, operation, form, precision): GFLOP/s, the
-    roofline fraction (roofline time = max(flops / peak of the mode, bytes /
-    HBM bandwidth)), and the relative Frobenius error on sampled outputs
-    against the FP64 oracle, computed in that entry's CPU-baseline leg."""
+def suite_lines(modes, only, reps, sink):
+    """Measures every workload of `only` in every (form, precision) of `modes`
+    and hands one record per entry to sink: GFLOP/s, the roofline fraction
+    (roofline time = max(flops / peak of the mode, bytes / HBM bandwidth)),
+    and the relative Frobenius error on sampled outputs against the FP64
+    oracle, computed in that entry's CPU-baseline leg."""
     import torch
 
-    import __graft_entry__
-
-    __graft_entry__.build()
     import oracle
     from paper_2312_13170_gb300 import api, inputs
 
     oracle.build()
-    torch.cuda.set_device(0)
     bf16_peak, hbm, peak_src = peaks()
     fp32_peak = fp32_simt_peak()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    reps = max(args.steps // 20, 5)
 
     def peak_of(prec):
         return fp32_peak if prec == "fp32" else bf16_peak / {"bf16": 1, "3xbf16": 3, "6xbf16": 6}[prec]
@@ -498,25 +525,61 @@ def run_suite(args):
                 else ("alu" if flops / peak_of(prec) / 1e12 > nbytes / hbm / 1e9 else "hbm"),
                 "peak": {"tflops": peak_of(prec), "hbm_gbs": hbm, "source": peak_src},
                 "rel_err": err, "cpu_baseline": cpu}
-        print(json.dumps(line), flush=True)
+        sink(line)
 
-    modes = [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "bf16"), ("internalized", "3xbf16"),
-             ("internalized", "6xbf16")]
-    if args.modes:
-        modes = [tuple(x.split("/")) for x in args.modes.split(",")]
-    only = set(args.only.split(",")) if args.only else {"gemm", "chain", "3mm", "cov", "batched", "backward",
-                                                        "gramschmidt"}
-    cores = oracle.max_threads()
-
-    # -------------------------------------------------- GEMM 256^3
+    cores = host_cores()
+    oracle.set_threads(cores)
     run_gemm_256(only, modes, api, inputs, oracle, cores, time_it, emit)
     run_chain_2048(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
     run_3mm(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
-    run_cov(only, modes, api, inputs, oracle, cores, time_it, emit, reps, hbm)
+    run_cov(only, modes, api, inputs, oracle, cores, time_it, emit, reps, hbm, sink)
     run_batched(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
     run_backward(only, modes, api, inputs, oracle, cores, time_it, emit, reps)
-    run_gramschmidt(only, modes, api, inputs, oracle, cores, time_it, reps, fp32_peak)
+    run_gramschmidt(only, modes, api, inputs, oracle, cores, time_it, reps, fp32_peak, sink)
+
+
+ALL_WORKLOADS = {"gemm", "chain", "3mm", "cov", "batched", "backward", "gramschmidt"}
+SUITE_MODES = [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16")]
+ALL_MODES = [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "bf16"), ("internalized", "3xbf16"),
+             ("internalized", "6xbf16")]
+
+
+def run_suite(args):
+    """--suite: one JSON line per (workload, operation, form, precision)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    modes = [tuple(x.split("/")) for x in args.modes.split(",")] if args.modes else ALL_MODES
+    only = set(args.only.split(",")) if args.only else ALL_WORKLOADS
+    suite_lines(modes, only, max(args.steps // 20, 5), lambda line: print(json.dumps(line), flush=True))
     return 0
+
+
+def suite_summary(records):
+    """The suite records of the benchmark line, one entry per workload and
+    operation: per form/precision the device time, GFLOP/s, roofline fraction
+    and sampled error, and the internalized 3xBF16 and FP32 speedups over the
+    plain form."""
+    out = {}
+    for r in records:
+        key = f"{r['op']}: {r['workload']}"
+        e = out.setdefault(key, {})
+        ent = {"ms": round(r["ms_median"], 5), "rel_err": r.get("rel_err")}
+        if "gflops" in r:
+            ent["gflops"] = round(r["gflops"], 1)
+        for k in ("roofline_frac", "hbm_gbs", "fp32_frac", "bound"):
+            if k in r:
+                ent[k] = round(r[k], 4) if isinstance(r[k], float) else r[k]
+        e[f"{r['form']}/{r['precision']}"] = ent
+    for e in out.values():
+        plain = e.get("plain/fp32") or e.get("plain/fp64")
+        for mode in ("internalized/3xbf16", "internalized/fp32", "internalized/fp64"):
+            if plain and mode in e and e[mode]["ms"] > 0:
+                e["speedup_" + mode.split("/")[1] + "_vs_plain"] = round(plain["ms"] / e[mode]["ms"], 2)
+    return out
 
 
 def run_gemm_256(only, modes, api, inputs, oracle, cores, time_it, emit):
@@ -607,7 +670,7 @@ def run_3mm(only, modes, api, inputs, oracle, cores, time_it, emit, reps):
                  cpu_b)
 
 
-def run_cov(only, modes, api, inputs, oracle, cores, time_it, emit, reps, hbm):
+def run_cov(only, modes, api, inputs, oracle, cores, time_it, emit, reps, hbm, sink):
     import torch
 
     if "cov" not in only:
@@ -632,7 +695,7 @@ def run_cov(only, modes, api, inputs, oracle, cores, time_it, emit, reps, hbm):
                 "precision": "fp64", "ms_median": ms[0], "ms_mean": ms[1],
                 "hbm_gbs": 2 * 4 * ns * m / (ms[0] / 1e3) / 1e9,
                 "roofline_frac": (2 * 4 * ns * m / (hbm * 1e9) * 1e3) / ms[0], "bound": "hbm", "rel_err": err}
-        print(json.dumps(line), flush=True)
+        sink(line)
     for form, prec in modes:
         if form == "plain":
             reps_here = 2
@@ -753,7 +816,7 @@ def main():
     return run_own(args)
 
 
-def run_gramschmidt(only, modes, api, inputs, oracle, cores, time_it, reps, fp32_peak):
+def run_gramschmidt(only, modes, api, inputs, oracle, cores, time_it, reps, fp32_peak, sink):
     """Polybench Gram-Schmidt QR at the paper's size (1024 x 1024, U[-1,1]),
     the FP32 forms among `modes`. Flops as the loop nest counts them: per
     column k, 2m for the norm, m for the scaling and 4m per later column."""
@@ -791,7 +854,7 @@ def run_gramschmidt(only, modes, api, inputs, oracle, cores, time_it, reps, fp32
                 "fp32_frac": gflops / 1e3 / fp32_peak,
                 "rel_err": errR, "rel_err_Q": errQ, "kappa": kappa, "Q_bound": max(1e-5, kappa * 2.0 ** -24),
                 "cpu_baseline": cpu}
-        print(json.dumps(line), flush=True)
+        sink(line)
 
 
 if __name__ == "__main__":

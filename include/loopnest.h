@@ -260,16 +260,20 @@ ln_status ln_correlation(int nsamples, int nfeat, const float *X, int ldx, float
  * enter the allocator). The paper has no counterpart to this entry point; it
  * computes exactly what ln_covariance computes with LN_FORM_INTERNALIZED and
  * LN_PREC_FP32, but takes no workspace: its scratch (the FP64 column
- * statistics and per-block partial sums) is one fixed 8 MiB device array in
- * the library, held on every GPU that loads the library until the process
- * exits. Sizes whose scratch exceeds 8 MiB -- about
- * 40*nfeat + 8*nfeat*ceil(nsamples/r) bytes, r the rows per reduction block
- * (256, 128 or 64, smaller for narrow inputs) -- give LN_ERR_INVALID_VALUE
- * with a message; nothing is launched then. The first call on each device
- * looks up the array's device address (cudaGetSymbolAddress) and must come
- * before any CUDA graph capture on that device. All calls share the array, so
- * calls whose kernels may overlap on the GPU (unordered streams) race; calls
- * in one stream are safe. X, cov and stream as in ln_covariance.
+ * means, their FP32 centring pair and per-block partial sums) is one fixed
+ * 8 MiB device array in the library, held on every GPU that loads the library
+ * until the process exits. The scratch of an nsamples x nfeat call is at most
+ * 16*nfeat + 8*nfeat*ceil(nsamples/r) + 1024 bytes, r the rows per reduction
+ * block (256, 128 or 64: the largest that still gives about 600 blocks of 128
+ * columns); sizes whose scratch exceeds 8 MiB, and sizes outside [0, 2^22],
+ * give LN_ERR_INVALID_VALUE with a message and launch nothing.
+ * The array's device address is looked up (cudaGetSymbolAddress, under a
+ * lock) on every call made outside stream capture and remembered per device;
+ * a call during capture uses the remembered address, so the first call on a
+ * device -- and the first after a cudaDeviceReset, which can move the array --
+ * must come before any capture (else LN_ERR_UNSUPPORTED). All calls share the
+ * array, so calls whose kernels may overlap on the GPU (unordered streams)
+ * race; calls in one stream are safe. X, cov and stream as in ln_covariance.
  */
 ln_status ln_covariance_noalloc(int nsamples, int nfeat, const float *X, int ldx, float *cov, int ldcov,
                                 void *stream);

@@ -101,6 +101,12 @@ bool inject_timeout_requested() {
     return v && strcmp(v, "timeout") == 0;
 }
 
+ln_status check_dims(std::initializer_list<long long> dims) {
+    for (long long d : dims)
+        if (d < 0 || d > MAX_DIM) return fail(LN_ERR_INVALID_VALUE, "size %lld out of range [0, %lld]", d, MAX_DIM);
+    return LN_SUCCESS;
+}
+
 int sm_count() {
     static int cache[64] = {0};
     int dev = 0;
@@ -286,13 +292,6 @@ bool overlap(Span a, Span b) {
     return x < y + b.bytes && y < x + a.bytes;
 }
 
-constexpr long long MAX_DIM = 1 << 22;
-
-ln_status check_dims(std::initializer_list<long long> dims) {
-    for (long long d : dims)
-        if (d < 0 || d > MAX_DIM) return fail(LN_ERR_INVALID_VALUE, "size %lld out of range [0, %lld]", d, MAX_DIM);
-    return LN_SUCCESS;
-}
 
 ln_status check_form(ln_form form, ln_precision prec) {
     if (form != LN_FORM_PLAIN && form != LN_FORM_INTERNALIZED)

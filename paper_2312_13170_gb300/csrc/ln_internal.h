@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <initializer_list>
+
 #include "loopnest.h"
 
 namespace ln {
@@ -22,6 +24,11 @@ void clear_error();
 
 // Check for a launch error right after <<<>>>.
 ln_status check_launch(const char *what);
+
+// Every size argument of the C ABI lies in [0, MAX_DIM]; LN_ERR_INVALID_VALUE
+// with a message otherwise.
+constexpr long long MAX_DIM = 1 << 22;
+ln_status check_dims(std::initializer_list<long long> dims);
 
 // Launch accounting (ln_launch_count / ln_timing_*): construct one of these
 // right before a kernel launch; it counts the launch and, while timing is

@@ -1,5 +1,5 @@
 // ln_covariance_noalloc: the covariance of ln_covariance (internalized form,
-// exact-FP32 tiled contraction over FP64 column statistics) for callers that
+// exact-FP32 tiled contraction centred by FP64 column means) for callers that
 // cannot allocate device memory -- for example code running where cudaMalloc
 // is forbidden or would break an allocation budget, such as inside a custom
 // allocator, a memory-capped sandbox or a real-time loop that must not call
@@ -8,15 +8,21 @@
 //
 // The array is a file-scope __device__ variable, so every GPU that loads the
 // library holds it (8 MiB) until the process exits. Host code cannot use the
-// array's name as a device address; the first call on each device looks the
-// address up with cudaGetSymbolAddress (with that device current) and keeps it.
-// That first call should therefore happen before any CUDA graph capture.
+// array's name as a device address: a call outside stream capture looks the
+// address up with cudaGetSymbolAddress (with the call's device current) and
+// remembers it per device; a call during capture uses the remembered address,
+// so a device's first call must come before any capture on it, and after a
+// cudaDeviceReset the first call must again come outside capture (the reset
+// can move the array).
 //
 // All calls on a device share the one array: calls whose kernels overlap on
 // the GPU (different streams without ordering) race on it. Each call writes
 // every scratch value it reads before reading it, so nothing left by an
 // earlier call needs clearing.
+#include <mutex>
+
 #include "ln_internal.h"
+#include "ln_stats.h"
 
 namespace ln {
 
@@ -26,11 +32,14 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH
 
 namespace {
 
+std::mutex g_scratch_mu;
 void *g_scratch_addr[64] = {nullptr};
 
-// Byte offsets of the scratch pieces for an n x m problem (each 256-aligned).
+// Byte offsets of the scratch pieces for an n x m problem (each 256-aligned):
+// the FP64 column means, the FP32 centring pair (hi, lo) and the per-block
+// partial sums of the mean pass.
 struct NoallocLayout {
-    size_t mean, ss, hi, lo, rs, partials, total;
+    size_t mean, hi, lo, partials, total;
 };
 
 NoallocLayout noalloc_layout(int n, int m) {
@@ -42,13 +51,31 @@ NoallocLayout noalloc_layout(int n, int m) {
         return at;
     };
     L.mean = take(sizeof(double) * (size_t)m);
-    L.ss = take(sizeof(double) * (size_t)m);
     L.hi = take(sizeof(float) * (size_t)m);
     L.lo = take(sizeof(float) * (size_t)m);
-    L.rs = take(sizeof(float) * (size_t)m);
     L.partials = take(col_stats_partials_bytes(n, m));
     L.total = off;
     return L;
+}
+
+// The array's device address on the current device (see the file comment).
+ln_status scratch_address(cudaStream_t st, char **out) {
+    int dev = 0;
+    LN_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(LN_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    LN_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (cs == cudaStreamCaptureStatusNone) {
+        void *p = nullptr;
+        LN_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_scratch_addr[dev] = p;
+    } else if (!g_scratch_addr[dev]) {
+        return fail(LN_ERR_UNSUPPORTED,
+                    "ln_covariance_noalloc: the first call on a device must come before stream capture");
+    }
+    *out = static_cast<char *>(g_scratch_addr[dev]);
+    return LN_SUCCESS;
 }
 
 }  // namespace
@@ -60,7 +87,8 @@ using namespace ln;
 extern "C" ln_status ln_covariance_noalloc(int nsamples, int nfeat, const float *X, int ldx, float *cov, int ldcov,
                                            void *stream) {
     clear_error();
-    if (nsamples < 0 || nfeat < 0) return fail(LN_ERR_INVALID_VALUE, "negative size");
+    ln_status s = check_dims({nsamples, nfeat});
+    if (s != LN_SUCCESS) return s;
     if (nfeat == 0) return LN_SUCCESS;
     if (nsamples < 2) return fail(LN_ERR_INVALID_VALUE, "covariance needs nsamples >= 2 (got %d)", nsamples);
     if (!X || !cov) return fail(LN_ERR_INVALID_VALUE, "NULL X or output");
@@ -73,27 +101,21 @@ extern "C" ln_status ln_covariance_noalloc(int nsamples, int nfeat, const float 
     if (L.total > NOALLOC_SCRATCH_BYTES)
         return fail(LN_ERR_INVALID_VALUE,
                     "ln_covariance_noalloc needs %zu bytes of scratch for %d x %d, more than its fixed %zu bytes "
-                    "(about 40*nfeat + 8*nfeat*ceil(nsamples/r) bytes, r = 64 to 256 rows per reduction block); "
-                    "use ln_covariance with a workspace",
+                    "(at most 16*nfeat + 8*nfeat*ceil(nsamples/r) + 1024 bytes, r = 256, 128 or 64 rows per "
+                    "reduction block); use ln_covariance with a workspace",
                     L.total, nsamples, nfeat, NOALLOC_SCRATCH_BYTES);
-    int dev = 0;
-    LN_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(LN_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        LN_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_scratch_addr[dev] = p;
-    }
-    char *base = static_cast<char *>(g_scratch_addr[dev]);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *base = nullptr;
+    s = scratch_address(st, &base);
+    if (s != LN_SUCCESS) return s;
     double *mean = reinterpret_cast<double *>(base + L.mean);
-    double *ss = reinterpret_cast<double *>(base + L.ss);
     float *hi = reinterpret_cast<float *>(base + L.hi);
     float *lo = reinterpret_cast<float *>(base + L.lo);
-    float *rs = reinterpret_cast<float *>(base + L.rs);
     double *partials = reinterpret_cast<double *>(base + L.partials);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
 
-    ln_status s = col_stats(nsamples, nfeat, X, ldx, mean, ss, hi, lo, rs, partials, st);
+    // the mean pass of ln_covariance's internalized form: the same partial sums
+    // and reduction, so the centring pair and the result are the same
+    s = col_mean(nsamples, nfeat, X, ldx, mean, hi, lo, partials, st);
     if (s != LN_SUCCESS) return s;
     EpiParams e{};
     e.mode = EPI_SYM;

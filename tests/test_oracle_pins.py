@@ -389,3 +389,25 @@ def test_cov_rows_matches_full():
     rows = [0, 7, 19, 3]
     assert np.array_equal(oracle.cov_rows(X, rows), oracle.covariance(X)[rows])
     assert np.array_equal(oracle.cov_rows(X, rows, corr=True), oracle.correlation(X)[rows])
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (2, 3), (5, 4), (8, 2)])
+def test_col_stats_exact_fraction(n, m):
+    """oracle.col_stats (mean, ss) against exact rational arithmetic: entries are
+    multiples of 1/8, so every sum is exact in FP64 and the mean is the exact
+    quotient rounded once; ss = sum (x - mean)^2 is within a few ulps of the
+    exact value. A swapped (ss, mean) return, a dropped centring or a divisor
+    in ss fails."""
+    rng = np.random.default_rng(n * 10 + m)
+    X = (rng.integers(-80, 80, size=(n, m)) / 8.0).astype(np.float32)
+    X[:, 0] += 100.0  # one column far from zero: centring matters
+    mean, ss = oracle.col_stats(X)
+    for j in range(m):
+        col = [Fraction(float(v)) for v in X[:, j]]
+        mu = sum(col) / n
+        s2 = sum((x - mu) ** 2 for x in col)
+        assert mean[j] == float(mu)
+        assert abs(Fraction(float(ss[j])) - s2) <= Fraction(1, 10 ** 12) * max(s2, Fraction(1, 64)), (j, ss[j], s2)
+    # the same statistics as the definition computed by NumPy in FP64
+    X64 = X.astype(np.float64)
+    assert np.allclose(ss, ((X64 - X64.mean(axis=0)) ** 2).sum(axis=0), rtol=1e-12, atol=1e-12)
