@@ -146,6 +146,11 @@ ln_status ln_timing_read(const char *family, double *total_ms /*host*/, int *lau
  *              half of the shared column tile of B; 1 pairs 256-wide general
  *              tiles, 2 every tile width and symmetric outputs (measured
  *              slower on 128-wide tiles), 0 none; results are bit-identical;
+ *   "simt_exact" 0 or 1 (default 1): the FP32 tiled form launches its EXACT
+ *              instance (no bounds predicates, 16-byte epilogue accesses) when
+ *              M, N are multiples of its tile width, K of 8, and every operand
+ *              and output row is 16-byte aligned; 0 always takes the general
+ *              instance; results are bit-identical;
  *   "stage_beta" 0 or 1 (default 1): the last 256-wide tile of each CTA of
  *              a general tensor-core contraction with beta != 0 copies its
  *              block of D (chain) or C (GEMM) into the operand stages once its

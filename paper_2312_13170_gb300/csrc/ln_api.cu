@@ -85,6 +85,7 @@ std::atomic<int> g_gs_rows{4};
 std::atomic<int> g_stream_k{0};
 std::atomic<int> g_pair{1};
 std::atomic<int> g_stage_beta{1};
+std::atomic<int> g_simt_exact{1};
 }  // namespace
 
 int tune_chunk_kt() { return g_chunk_kt.load(std::memory_order_relaxed); }
@@ -95,6 +96,7 @@ int tune_gs_rows() { return g_gs_rows.load(std::memory_order_relaxed); }
 int tune_stream_k() { return g_stream_k.load(std::memory_order_relaxed); }
 int tune_pair() { return g_pair.load(std::memory_order_relaxed); }
 int tune_stage_beta() { return g_stage_beta.load(std::memory_order_relaxed); }
+int tune_simt_exact() { return g_simt_exact.load(std::memory_order_relaxed); }
 
 bool inject_timeout_requested() {
     const char *v = getenv("LN_FAULT_INJECT");
@@ -760,7 +762,9 @@ ln_status run_batch(bool two, ln_fill fill, int count, const ln_sym_desc *h, con
     if (form == LN_FORM_PLAIN) return plain_sym_batched(two, count, d, bp.max_n, fill, alpha, beta, st);
     if (!tensor_prec(prec)) {
         LN_TRY(simt_sym_batched_prefix(count, d, bp.tile_prefix, st));
-        return simt_sym_batched(two, count, d, bp.tile_prefix, (int)bp.total_tiles, fill, alpha, beta, st);
+        const long long tiles = simt_sym_batched_tiles(count, h);
+        if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "batch too large");
+        return simt_sym_batched(two, count, d, bp.tile_prefix, (int)tiles, fill, alpha, beta, st);
     }
     const int P = prec_terms(prec);
     LN_TRY(sym_batched_plan(two, count, d, fill, alpha, beta, bp.probs, bp.tile_prefix, bp.tile_owner, bp.pack_off,
@@ -991,6 +995,11 @@ ln_status ln_set_tuning(const char *key, int value) {
         g_split_k.store(value);
         return LN_SUCCESS;
     }
+    if (strcmp(key, "simt_exact") == 0) {
+        if (value != 0 && value != 1) return fail(LN_ERR_INVALID_VALUE, "simt_exact must be 0 or 1 (got %d)", value);
+        g_simt_exact.store(value);
+        return LN_SUCCESS;
+    }
     if (strcmp(key, "stage_beta") == 0) {
         if (value != 0 && value != 1) return fail(LN_ERR_INVALID_VALUE, "stage_beta must be 0 or 1 (got %d)", value);
         g_stage_beta.store(value);
@@ -1031,6 +1040,7 @@ ln_status ln_get_tuning(const char *key, int *value) {
     else if (strcmp(key, "stream_k") == 0) *value = g_stream_k.load();
     else if (strcmp(key, "pair") == 0) *value = g_pair.load();
     else if (strcmp(key, "stage_beta") == 0) *value = g_stage_beta.load();
+    else if (strcmp(key, "simt_exact") == 0) *value = g_simt_exact.load();
     else return fail(LN_ERR_INVALID_VALUE, "unknown tuning key '%s'", key);
     return LN_SUCCESS;
 }

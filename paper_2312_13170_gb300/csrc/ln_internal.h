@@ -297,5 +297,7 @@ ln_status plain_sym_batched(int is_syr2k, int count, const ln_sym_desc *d_descs,
 ln_status simt_sym_batched(int is_syr2k, int count, const ln_sym_desc *d_descs, const int *d_tile_prefix,
                            int total_tiles, int fill, float alpha, float beta, cudaStream_t st);
 ln_status simt_sym_batched_prefix(int count, const ln_sym_desc *d_descs, int *d_tile_prefix, cudaStream_t st);
+// Lower-triangle tiles of the FP32 tiled batched kernel (its own tile width).
+long long simt_sym_batched_tiles(int count, const ln_sym_desc *h);
 
 }  // namespace ln

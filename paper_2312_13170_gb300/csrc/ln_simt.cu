@@ -1,200 +1,365 @@
 // Internalized FP32 form: the work-group tiling of loop internalization
-// (paper Sec. VI-C, Listing 6) mapped to a CTA. Each CTA owns a 128 x 128
-// output tile; the inner k loop is tiled by 8, and each k-tile of both
-// operands is prefetched from global memory (coalesced 128-bit loads where
-// the layout allows) into shared memory, double-buffered so that one barrier
-// per k-tile separates the prefetch of the next tile from the use of the
-// current one. Each thread accumulates an 8 x 8 register block in exact FP32
-// FFMA and stores it once (Sec. VI-B).
+// (paper Sec. VI-C, Listing 6) mapped to a CTA. Each CTA owns a TB x TB output
+// tile (TB = 128, or 64 for problems whose 128-wide tiles would leave most SMs
+// idle); the inner k loop is tiled by TK (16 at TB = 128, 8 at 64), and each
+// k-tile of both operands is copied from global memory into shared memory by
+// 16-byte cp.async copies (4-byte ones, or zero fill, at ragged or unaligned
+// edges) into a ring of NST stages (3 at TB = 128, 4 at 64), so that NST - 1
+// k-tiles are in flight while one is consumed and a single barrier per k-tile
+// orders the ring. Each thread accumulates an 8 x 8
+// (TB = 128) or 4 x 4 (TB = 64) register block in exact FP32 FFMA and stores it
+// once (Sec. VI-B).
+//
+// Constant propagation (the analogue of the paper's host-device constant
+// propagation, Sec. VII): when the host sees that the problem divides into
+// whole tiles and k-tiles and that every operand row is 16-byte aligned, it
+// launches the EXACT instance, in which those facts are compile-time
+// constants: no bounds predicates in the copies or the epilogue, and 16-byte
+// epilogue accesses.
+#include <type_traits>
+
+#include "ln_async.cuh"
 #include "ln_epilogue.cuh"
 #include "ln_internal.h"
 
 namespace ln {
 
+int tune_simt_exact();  // ln_api.cu: the "simt_exact" knob
+
 namespace {
 
-constexpr int TB = 128;  // output tile edge
-constexpr int TK = 8;    // k-tile depth
-constexpr int PADW = TB + 4;
+constexpr int PADT = 4;   // row padding of k-major tiles ([TK][TB + PADT])
+template <int TB>
+constexpr int tk_of() { return TB == 128 ? 16 : 8; }  // k-tile depth
+template <int TB>
+constexpr int nst_of() { return TB == 128 ? 3 : 4; }  // ring stages
 
-struct TileCtx {
-    const float *A, *B;
-    long long lda, ldb;
-    int M, N, K;
-    int i0, j0;
-    bool a_vec, b_vec;  // 16-byte loads legal (aligned base, ld % 4 == 0)
-    const float *a_hi, *a_lo, *b_hi, *b_lo;
+// Shared-memory extent (floats) of one operand tile: k-major ([TK][TB + PADT],
+// rows of the operand's contiguous index) or k-contiguous ([TB][TK + 4]: 48-byte
+// rows), both filled by 16-byte copies. k-major tiles are read 4 consecutive
+// rows (columns) at a time; k-contiguous ones 4 consecutive k at a time, by
+// lanes whose rows are one address per half-warp (A: rows follow ty) or
+// consecutive (B: columns tx + 16 q), so that no read has bank conflicts.
+template <int TB, int KMAJ>
+struct TileShape {
+    static constexpr int TK = tk_of<TB>();
+    static constexpr bool KMAJOR = KMAJ;  // 1: element (k, x) at [k][x]; 0: at [x][k]
+    static constexpr int LD = KMAJOR ? TB + PADT : TK + 4;
+    static constexpr int FLOATS = KMAJOR ? TK * LD : TB * LD;
+    static constexpr bool V16 = true;
 };
 
-// Four consecutive elements of row `row` starting at column `col` of a
-// row-major (rows x cols) matrix, zero outside the matrix.
-__device__ __forceinline__ float4 load4(const float *p, long long ld, int row, int col, int rows, int cols, bool vec) {
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (row >= rows) return v;
-    const float *q = p + (long long)row * ld + col;
-    if (vec && col + 3 < cols) return __ldg(reinterpret_cast<const float4 *>(q));
-    if (col + 0 < cols) v.x = __ldg(q + 0);
-    if (col + 1 < cols) v.y = __ldg(q + 1);
-    if (col + 2 < cols) v.z = __ldg(q + 2);
-    if (col + 3 < cols) v.w = __ldg(q + 3);
-    return v;
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool ok) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
 }
-
-template <int AT, int BT>
-__device__ __forceinline__ void fetch(const TileCtx &c, int k0, int tid, float4 &ra, float4 &rb) {
-    if (AT == 0) {  // A[i][k]: 128 rows x 8 k, two float4 per row
-        ra = load4(c.A, c.lda, c.i0 + (tid >> 1), k0 + (tid & 1) * 4, c.M, c.K, c.a_vec);
-        if (c.a_hi) {
-            int i = c.i0 + (tid >> 1);
-            if (i < c.M) {
-                float h = c.a_hi[i], l = c.a_lo[i];
-                int kk = k0 + (tid & 1) * 4;
-                if (kk + 0 < c.K) ra.x = (ra.x - h) - l;
-                if (kk + 1 < c.K) ra.y = (ra.y - h) - l;
-                if (kk + 2 < c.K) ra.z = (ra.z - h) - l;
-                if (kk + 3 < c.K) ra.w = (ra.w - h) - l;
-            }
-        }
-    } else {  // A[k][i]: 8 k-rows x 128 i
-        int kk = k0 + (tid >> 5), i = c.i0 + (tid & 31) * 4;
-        ra = load4(c.A, c.lda, kk, i, c.K, c.M, c.a_vec);
-        if (c.a_hi && kk < c.K) {
-            if (i + 0 < c.M) ra.x = (ra.x - c.a_hi[i + 0]) - c.a_lo[i + 0];
-            if (i + 1 < c.M) ra.y = (ra.y - c.a_hi[i + 1]) - c.a_lo[i + 1];
-            if (i + 2 < c.M) ra.z = (ra.z - c.a_hi[i + 2]) - c.a_lo[i + 2];
-            if (i + 3 < c.M) ra.w = (ra.w - c.a_hi[i + 3]) - c.a_lo[i + 3];
-        }
-    }
-    if (BT == 0) {  // B[k][j]: 8 k-rows x 128 j
-        int kk = k0 + (tid >> 5), j = c.j0 + (tid & 31) * 4;
-        rb = load4(c.B, c.ldb, kk, j, c.K, c.N, c.b_vec);
-        if (c.b_hi && kk < c.K) {
-            if (j + 0 < c.N) rb.x = (rb.x - c.b_hi[j + 0]) - c.b_lo[j + 0];
-            if (j + 1 < c.N) rb.y = (rb.y - c.b_hi[j + 1]) - c.b_lo[j + 1];
-            if (j + 2 < c.N) rb.z = (rb.z - c.b_hi[j + 2]) - c.b_lo[j + 2];
-            if (j + 3 < c.N) rb.w = (rb.w - c.b_hi[j + 3]) - c.b_lo[j + 3];
-        }
-    } else {  // B[j][k]: 128 rows x 8 k
-        rb = load4(c.B, c.ldb, c.j0 + (tid >> 1), k0 + (tid & 1) * 4, c.N, c.K, c.b_vec);
-        if (c.b_hi) {
-            int j = c.j0 + (tid >> 1);
-            if (j < c.N) {
-                float h = c.b_hi[j], l = c.b_lo[j];
-                int kk = k0 + (tid & 1) * 4;
-                if (kk + 0 < c.K) rb.x = (rb.x - h) - l;
-                if (kk + 1 < c.K) rb.y = (rb.y - h) - l;
-                if (kk + 2 < c.K) rb.z = (rb.z - h) - l;
-                if (kk + 3 < c.K) rb.w = (rb.w - h) - l;
-            }
-        }
-    }
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src, bool ok) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0) : "memory");
 }
-
-template <int AT, int BT>
-__device__ __forceinline__ void stash(float (*As)[PADW], float (*Bs)[PADW], int tid, const float4 &ra,
-                                      const float4 &rb) {
-    if (AT == 0) {
-        int i = tid >> 1, k = (tid & 1) * 4;
-        As[k + 0][i] = ra.x;
-        As[k + 1][i] = ra.y;
-        As[k + 2][i] = ra.z;
-        As[k + 3][i] = ra.w;
-    } else {
-        *reinterpret_cast<float4 *>(&As[tid >> 5][(tid & 31) * 4]) = ra;
-    }
-    if (BT == 0) {
-        *reinterpret_cast<float4 *>(&Bs[tid >> 5][(tid & 31) * 4]) = rb;
-    } else {
-        int j = tid >> 1, k = (tid & 1) * 4;
-        Bs[k + 0][j] = rb.x;
-        Bs[k + 1][j] = rb.y;
-        Bs[k + 2][j] = rb.z;
-        Bs[k + 3][j] = rb.w;
-    }
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 __device__ __forceinline__ bool vec_ok(const float *p, long long ld) {
     return ((reinterpret_cast<uintptr_t>(p) & 15) == 0) && ((ld & 3) == 0);
 }
 
-// One 128 x 128 output tile at (i0, j0) over nseg segments of K.
-template <int AT, int BT>
-__device__ void simt_tile(int M, int N, int K, const SimtOperands &op, const EpiParams &epi, int i0, int j0) {
-    __shared__ __align__(16) float As[2][TK][PADW];
-    __shared__ __align__(16) float Bs[2][TK][PADW];
-    const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
-    float acc[8][8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc[r][q] = 0.0f;
-
-    const int kt = (K + TK - 1) / TK;
-    const int total = kt * op.nseg;
-    TileCtx c;
-    c.M = M;
-    c.N = N;
-    c.K = K;
-    c.i0 = i0;
-    c.j0 = j0;
-    c.a_hi = op.a_off_hi;
-    c.a_lo = op.a_off_lo;
-    c.b_hi = op.b_off_hi;
-    c.b_lo = op.b_off_lo;
-
-    float4 ra, rb;
-    if (total > 0) {
-        c.A = op.A[0];
-        c.B = op.B[0];
-        c.lda = op.lda[0];
-        c.ldb = op.ldb[0];
-        c.a_vec = vec_ok(c.A, c.lda);
-        c.b_vec = vec_ok(c.B, c.ldb);
-        fetch<AT, BT>(c, 0, tid, ra, rb);
-        stash<AT, BT>(As[0], Bs[0], tid, ra, rb);
+// Copies the 16-byte chunk (r, c .. c + 3) of a row-major rows x cols matrix
+// (leading dimension ld) to shared address dst; elements outside the matrix
+// are zero. vec: 16-byte copies are legal for whole chunks.
+// V16: the shared-memory destination takes 16-byte copies; else four 4-byte
+// ones at dst, dst + dstep, dst + 2 dstep, dst + 3 dstep (bytes).
+template <bool EXACT, bool V16>
+__device__ __forceinline__ void copy_chunk(uint32_t dst, uint32_t dstep, const float *p, long long ld, int r, int c,
+                                           int rows, int cols, bool vec) {
+    if (V16 && EXACT) {
+        cp_async16(dst, p + (long long)r * ld + c, true);
+        return;
     }
-    __syncthreads();
-    for (int it = 0; it < total; ++it) {
-        const int buf = it & 1;
-        const bool more = it + 1 < total;
-        if (more) {
-            const bool seg1 = (it + 1) >= kt;
-            c.A = seg1 ? op.A[1] : op.A[0];
-            c.B = seg1 ? op.B[1] : op.B[0];
-            c.lda = seg1 ? op.lda[1] : op.lda[0];
-            c.ldb = seg1 ? op.ldb[1] : op.ldb[0];
-            c.a_vec = vec_ok(c.A, c.lda);
-            c.b_vec = vec_ok(c.B, c.ldb);
-            fetch<AT, BT>(c, ((it + 1) % kt) * TK, tid, ra, rb);
+    const bool inr = EXACT || r < rows;
+    const float *q = p + (long long)r * ld + c;
+    if (V16) {
+        if (!inr || c >= cols) {
+            cp_async16(dst, p, false);
+            return;
         }
-#pragma unroll
-        for (int kk = 0; kk < TK; ++kk) {
-            float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
-            float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
-            float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
-            float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
-            float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-            for (int r = 0; r < 8; ++r)
-#pragma unroll
-                for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(a[r], b[q], acc[r][q]);
+        if (vec && c + 3 < cols) {
+            cp_async16(dst, q, true);
+            return;
         }
-        if (more) stash<AT, BT>(As[buf ^ 1], Bs[buf ^ 1], tid, ra, rb);
-        __syncthreads();
     }
-    // per row: issue the row's eight epilogue loads, then its stores
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        const int i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
-        float2 g[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) g[q] = epi_load(epi, i, j0 + (q < 4 ? tx * 4 + q : 64 + tx * 4 + (q - 4)));
-#pragma unroll
-        for (int q = 0; q < 8; ++q) epi_apply(epi, i, j0 + (q < 4 ? tx * 4 + q : 64 + tx * 4 + (q - 4)), acc[r][q], g[q]);
+    for (int e = 0; e < 4; ++e) {
+        const bool ok = inr && (EXACT || c + e < cols);
+        cp_async4(dst + dstep * e, ok ? q + e : p, ok);
     }
 }
+
+// Operand roles: op A is M x K (AT = 0: A[i][k], AT = 1: A[k][i]); op B is
+// K x N (BT = 0: B[k][j], BT = 1: B[j][k]). In shared memory A is k-major when
+// AT = 1 (its rows are k), B k-major when BT = 0.
+template <int AT, int BT, int TB, bool EXACT>
+struct Simt {
+    using SA = TileShape<TB, AT>;      // A k-major iff AT == 1
+    using SB = TileShape<TB, 1 - BT>;  // B k-major iff BT == 0
+    static constexpr int TK = tk_of<TB>();
+    static constexpr int NST = nst_of<TB>();
+    static constexpr int STAGE = SA::FLOATS + SB::FLOATS;
+    static constexpr int SMEM = NST * STAGE * 4;  // dynamic shared memory (bytes)
+    // k values per read of a k-contiguous tile: 4 (16-byte reads), or 2 when both
+    // operands are k-contiguous, so that the held values fit two CTAs per SM
+    static constexpr int KG = (AT == 0 && BT == 1) ? 2 : 4;
+    static constexpr int R = TB / 16;  // rows (and columns) per thread: 8 or 4
+    static constexpr int CHUNKS = TK * TB / 4;  // 16-byte chunks per operand per k-tile
+
+    struct Ctx {
+        const float *A, *B;
+        long long lda, ldb;
+        bool avec, bvec;
+    };
+
+    __device__ static Ctx seg_ctx(const SimtOperands &op, int sg) {
+        // selects, not a runtime index into the parameter block (which would
+        // copy it to local memory)
+        Ctx c;
+        c.A = sg ? op.A[1] : op.A[0];
+        c.B = sg ? op.B[1] : op.B[0];
+        c.lda = sg ? op.lda[1] : op.lda[0];
+        c.ldb = sg ? op.ldb[1] : op.ldb[0];
+        c.avec = vec_ok(c.A, c.lda);
+        c.bvec = vec_ok(c.B, c.ldb);
+        return c;
+    }
+
+    // chunk `id` of an operand tile: (row, col) in the operand's storage and the
+    // shared-memory float offset it goes to (its four elements are consecutive
+    // in both)
+    __device__ static void chunk_a(int id, int i0, int k0, int &r, int &c, int &off) {
+        if (AT) {  // A[k][i]: rows k, cols i
+            const int k = id / (TB / 4), x = (id % (TB / 4)) * 4;
+            r = k0 + k;
+            c = i0 + x;
+            off = k * SA::LD + x;
+        } else {  // A[i][k]: rows i, cols k
+            const int x = id / (TK / 4), k = (id % (TK / 4)) * 4;
+            r = i0 + x;
+            c = k0 + k;
+            off = x * SA::LD + k;
+        }
+    }
+    __device__ static void chunk_b(int id, int j0, int k0, int &r, int &c, int &off) {
+        if (BT == 0) {  // B[k][j]: rows k, cols j
+            const int k = id / (TB / 4), x = (id % (TB / 4)) * 4;
+            r = k0 + k;
+            c = j0 + x;
+            off = k * SB::LD + x;
+        } else {  // B[j][k]: rows j, cols k
+            const int x = id / (TK / 4), k = (id % (TK / 4)) * 4;
+            r = j0 + x;
+            c = k0 + k;
+            off = x * SB::LD + k;
+        }
+    }
+
+    // Issue the copies of flattened k-tile q (segment q / kt) into stage `buf`.
+    __device__ static void issue(float *sm, int buf, int q, int kt, const SimtOperands &op, int M, int N, int K,
+                                 int i0, int j0, int tid) {
+        const Ctx c = seg_ctx(op, q / kt);
+        const int k0 = (q % kt) * TK;
+        float *sa = sm + buf * STAGE, *sb = sa + SA::FLOATS;
+        for (int id = tid; id < 2 * CHUNKS; id += 256) {
+            int r, col, off;
+            if (id < CHUNKS) {
+                chunk_a(id, i0, k0, r, col, off);
+                copy_chunk<EXACT, SA::V16>(saddr(sa + off), 4, c.A, c.lda, r, col, AT ? K : M, AT ? M : K, c.avec);
+            } else {
+                chunk_b(id - CHUNKS, j0, k0, r, col, off);
+                copy_chunk<EXACT, SB::V16>(saddr(sb + off), 4, c.B, c.ldb, r, col, BT ? N : K, BT ? K : N, c.bvec);
+            }
+        }
+    }
+
+    // Centring (covariance: v = (x - hi) - lo per column of the data matrix)
+    // of the chunks this thread copied into stage `buf`. Only the k-major
+    // layouts carry offsets (the data matrix is A[k][i] and B[k][j]); a thread's
+    // chunks keep their columns from k-tile to k-tile, so their offsets were
+    // read once into ha/la (A) and hb/lb (B). Elements outside the matrix stay 0.
+    __device__ static void centre(float *sm, int buf, int q, int kt, int K, int i0, int j0, int tid, int M, int N,
+                                  const float4 &ha, const float4 &la, const float4 &hb, const float4 &lb, bool offa,
+                                  bool offb) {
+        const int k0 = (q % kt) * TK;
+        float *sa = sm + buf * STAGE, *sb = sa + SA::FLOATS;
+        for (int id = tid; id < 2 * CHUNKS; id += 256) {
+            const bool isa = id < CHUNKS;
+            if (isa ? !offa : !offb) continue;
+            int r, col, off;
+            if (isa) chunk_a(id, i0, k0, r, col, off);
+            else chunk_b(id - CHUNKS, j0, k0, r, col, off);
+            if (r >= K) continue;
+            float *v = (isa ? sa : sb) + off;
+            const float4 h = isa ? ha : hb, l = isa ? la : lb;
+            const int cols = isa ? M : N;
+            if (col + 0 < cols) v[0] = (v[0] - h.x) - l.x;
+            if (col + 1 < cols) v[1] = (v[1] - h.y) - l.y;
+            if (col + 2 < cols) v[2] = (v[2] - h.z) - l.z;
+            if (col + 3 < cols) v[3] = (v[3] - h.w) - l.w;
+        }
+    }
+
+    // this thread's centring offsets of chunk `id`'s four columns (zero outside)
+    __device__ static float4 offsets4(const float *off, int x0, int n) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!off) return v;
+        if (x0 + 0 < n) v.x = off[x0 + 0];
+        if (x0 + 1 < n) v.y = off[x0 + 1];
+        if (x0 + 2 < n) v.z = off[x0 + 2];
+        if (x0 + 3 < n) v.w = off[x0 + 3];
+        return v;
+    }
+
+    __device__ static float comp(const float4 &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+    __device__ static float comp(const float2 &v, int i) { return i == 0 ? v.x : v.y; }
+
+    // output row of this thread's accumulator row r, and column of its column q
+    __device__ static int row_of(int r, int ty) { return (r / 4) * (TB / 2) + ty * 4 + r % 4; }
+    __device__ static int col_of(int q, int tx) { return BT ? tx + 16 * q : (q / 4) * (TB / 2) + tx * 4 + q % 4; }
+
+    __device__ static void tile(int M, int N, int K, const SimtOperands &op, const EpiParams &epi, int i0, int j0) {
+        extern __shared__ __align__(16) float sm[];
+        const int tid = threadIdx.x;
+        const int tx = tid & 15, ty = tid >> 4;
+        float acc[R][R];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int q = 0; q < R; ++q) acc[r][q] = 0.0f;
+        const int kt = (K + TK - 1) / TK;
+        const int nkt = kt * op.nseg;
+        // centring offsets: only the k-major layouts (covariance's A[k][i], B[k][j]) take them
+        const bool offa = AT == 1 && op.a_off_hi, offb = BT == 0 && op.b_off_hi;
+        float4 ha{}, la{}, hb{}, lb{};
+        if (offa || offb) {
+            // this thread's chunks (ids tid, tid + 256, ... over A then B) keep their
+            // columns x = (id % (TB / 4)) * 4 in every k-tile
+            for (int id = tid; id < 2 * CHUNKS; id += 256) {
+                const int x = (id < CHUNKS ? i0 : j0) + ((id % CHUNKS) % (TB / 4)) * 4;
+                if (id < CHUNKS && offa) ha = offsets4(op.a_off_hi, x, M), la = offsets4(op.a_off_lo, x, M);
+                if (id >= CHUNKS && offb) hb = offsets4(op.b_off_hi, x, N), lb = offsets4(op.b_off_lo, x, N);
+            }
+        }
+
+#pragma unroll
+        for (int s = 0; s < NST - 1; ++s) {
+            if (s < nkt) issue(sm, s, s, kt, op, M, N, K, i0, j0, tid);
+            cp_commit();
+        }
+        for (int it = 0; it < nkt; ++it) {
+            const int buf = it % NST;
+            if constexpr (NST == 4) cp_wait<2>();  // this thread's copies of k-tile it have landed
+            else cp_wait<1>();
+            if (offa || offb) centre(sm, buf, it, kt, K, i0, j0, tid, M, N, ha, la, hb, lb, offa, offb);
+            __syncthreads();  // every thread's copies of k-tile it; stage (it - 1) % NST is free
+            if (it + NST - 1 < nkt) issue(sm, (it + NST - 1) % NST, it + NST - 1, kt, op, M, N, K, i0, j0, tid);
+            cp_commit();
+            const float *sa = sm + buf * STAGE, *sb = sa + SA::FLOATS;
+#pragma unroll
+            for (int kq = 0; kq < TK; kq += KG) {
+                // k-contiguous tiles: KG consecutive k of a row (column) per read
+                using VK = typename std::conditional<KG == 4, float4, float2>::type;
+                VK a4[AT ? 1 : R], b4[BT ? R : 1];
+                if (!AT) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) a4[r] = *reinterpret_cast<const VK *>(sa + row_of(r, ty) * SA::LD + kq);
+                }
+                if (BT) {
+#pragma unroll
+                    for (int q = 0; q < R; ++q) b4[q] = *reinterpret_cast<const VK *>(sb + col_of(q, tx) * SB::LD + kq);
+                }
+#pragma unroll
+                for (int k4 = 0; k4 < KG; ++k4) {
+                    const int kk = kq + k4;
+                    float a[R], b[R];
+                    if (AT) {  // k-major: four consecutive rows per 16-byte read
+#pragma unroll
+                        for (int h = 0; h < R / 4; ++h) {
+                            const float4 v = *reinterpret_cast<const float4 *>(sa + kk * SA::LD + row_of(4 * h, ty));
+                            a[4 * h] = v.x, a[4 * h + 1] = v.y, a[4 * h + 2] = v.z, a[4 * h + 3] = v.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < R; ++r) a[r] = comp(a4[r], k4);
+                    }
+                    if (BT == 0) {
+#pragma unroll
+                        for (int h = 0; h < R / 4; ++h) {
+                            const float4 v = *reinterpret_cast<const float4 *>(sb + kk * SB::LD + col_of(4 * h, tx));
+                            b[4 * h] = v.x, b[4 * h + 1] = v.y, b[4 * h + 2] = v.z, b[4 * h + 3] = v.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < R; ++q) b[q] = comp(b4[q], k4);
+                    }
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+#pragma unroll
+                        for (int q = 0; q < R; ++q) acc[r][q] = fmaf(a[r], b[q], acc[r][q]);
+                }
+            }
+        }
+        cp_wait<0>();
+        epilogue(epi, i0, j0, tx, ty, acc);
+        static_assert(NST == 3 || NST == 4, "ring depth");
+    }
+
+    // Row r of this thread's block is output row i0 + row_of(r), column q is
+    // j0 + col_of(q): four consecutive columns per group unless B is k-contiguous.
+    __device__ static void epilogue(const EpiParams &epi, int i0, int j0, int tx, int ty, float (&acc)[R][R]) {
+        if (EXACT && BT == 0 && (epi.mode == EPI_GEMM || epi.mode == EPI_STORE || epi.mode == EPI_EF)) {
+            // whole tile inside the output, rows 16-byte aligned: four columns per access
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int i = i0 + row_of(r, ty);
+#pragma unroll
+                for (int h = 0; h < R / 4; ++h) {
+                    const int j = j0 + col_of(4 * h, tx);
+                    const float4 v = make_float4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
+                    if (epi.mode == EPI_EF) {
+                        const long long o = (long long)i * epi.ld_ef + j;
+                        *reinterpret_cast<float4 *>(epi.E + o) = v;
+                        float4 f = make_float4(epi.alpha * v.x, epi.alpha * v.y, epi.alpha * v.z, epi.alpha * v.w);
+                        if (epi.beta != 0.0f) {
+                            const float4 d = *reinterpret_cast<const float4 *>(epi.D + o);
+                            f.x = fmaf(epi.beta, d.x, f.x), f.y = fmaf(epi.beta, d.y, f.y);
+                            f.z = fmaf(epi.beta, d.z, f.z), f.w = fmaf(epi.beta, d.w, f.w);
+                        }
+                        *reinterpret_cast<float4 *>(epi.F + o) = f;
+                    } else {
+                        float *c = epi.C + (long long)i * epi.ldc + j;
+                        float4 f = make_float4(epi.alpha * v.x, epi.alpha * v.y, epi.alpha * v.z, epi.alpha * v.w);
+                        if (epi.mode == EPI_GEMM && epi.beta != 0.0f) {
+                            const float4 d = *reinterpret_cast<const float4 *>(c);
+                            f.x = fmaf(epi.beta, d.x, f.x), f.y = fmaf(epi.beta, d.y, f.y);
+                            f.z = fmaf(epi.beta, d.z, f.z), f.w = fmaf(epi.beta, d.w, f.w);
+                        }
+                        *reinterpret_cast<float4 *>(c) = f;
+                    }
+                }
+            }
+            return;
+        }
+        // per row: issue the row's epilogue loads, then its stores
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = i0 + row_of(r, ty);
+            float2 g[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) g[q] = epi_load(epi, i, j0 + col_of(q, tx));
+#pragma unroll
+            for (int q = 0; q < R; ++q) epi_apply(epi, i, j0 + col_of(q, tx), acc[r][q], g[q]);
+        }
+    }
+};
 
 __device__ __forceinline__ void tri_tile(int t, int &ti, int &tj) {
     int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
@@ -204,8 +369,12 @@ __device__ __forceinline__ void tri_tile(int t, int &ti, int &tj) {
     tj = t - r * (r + 1) / 2;
 }
 
-template <int AT, int BT>
-__global__ __launch_bounds__(256, 2) void k_simt(int M, int N, int K, SimtOperands op, EpiParams epi, int sym) {
+// Two CTAs of 256 threads per SM (at most 128 registers a thread).
+template <int AT, int BT, int TB>
+constexpr int simt_min_blocks() { return 2; }
+
+template <int AT, int BT, int TB, bool EXACT>
+__global__ __launch_bounds__(256, simt_min_blocks<AT, BT, TB>()) void k_simt(int M, int N, int K, SimtOperands op, EpiParams epi, int sym) {
     int ti, tj;
     if (sym) {
         tri_tile(blockIdx.x, ti, tj);
@@ -213,11 +382,12 @@ __global__ __launch_bounds__(256, 2) void k_simt(int M, int N, int K, SimtOperan
         ti = blockIdx.y;
         tj = blockIdx.x;
     }
-    simt_tile<AT, BT>(M, N, K, op, epi, ti * TB, tj * TB);
+    Simt<AT, BT, TB, EXACT>::tile(M, N, K, op, epi, ti * TB, tj * TB);
 }
 
 // Batched SYRK/SYR2K: a flat grid over every instance's lower-triangle tiles.
-__global__ __launch_bounds__(256, 2) void k_simt_sym_batched(int is_syr2k, const ln_sym_desc *__restrict__ descs,
+constexpr int TB_BATCH = 128;
+__global__ __launch_bounds__(256, simt_min_blocks<0, 1, TB_BATCH>()) void k_simt_sym_batched(int is_syr2k, const ln_sym_desc *__restrict__ descs,
                                                           const int *__restrict__ prefix, int count, int fill,
                                                           float alpha, float beta) {
     int t = blockIdx.x;
@@ -251,7 +421,7 @@ __global__ __launch_bounds__(256, 2) void k_simt_sym_batched(int is_syr2k, const
     e.ldc = d.ldc;
     e.fill = fill;
     e.sym_kind = SYM_AXPBY;
-    simt_tile<0, 1>(d.n, d.n, d.k, op, e, ti * TB, tj * TB);
+    Simt<0, 1, TB_BATCH, false>::tile(d.n, d.n, d.k, op, e, ti * TB_BATCH, tj * TB_BATCH);
 }
 
 __global__ void k_sym_prefix(int count, const ln_sym_desc *__restrict__ descs, int *prefix) {
@@ -259,29 +429,103 @@ __global__ void k_sym_prefix(int count, const ln_sym_desc *__restrict__ descs, i
     int acc = 0;
     for (int i = 0; i < count; ++i) {
         prefix[i] = acc;
-        int t = (descs[i].n + TB - 1) / TB;
+        int t = (descs[i].n + TB_BATCH - 1) / TB_BATCH;
         acc += t * (t + 1) / 2;
     }
     prefix[count] = acc;
+}
+
+bool host_vec(const void *p, long long ld) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0 && (ld & 3) == 0; }
+
+// The facts the EXACT instance takes as constants, checked on the host.
+bool exact_ok(int M, int N, int K, int TB, const SimtOperands &op, const EpiParams &e) {
+    const int tk = TB == 128 ? tk_of<128>() : tk_of<64>();
+    if (M % TB || N % TB || K % tk || K == 0) return false;
+    for (int s = 0; s < op.nseg; ++s)
+        if (!host_vec(op.A[s], op.lda[s]) || !host_vec(op.B[s], op.ldb[s])) return false;
+    switch (e.mode) {
+        case EPI_GEMM:
+        case EPI_STORE: return host_vec(e.C, e.ldc);
+        case EPI_EF: return host_vec(e.E, e.ld_ef) && host_vec(e.F, e.ld_ef) && (e.beta == 0.0f || host_vec(e.D, e.ld_ef));
+        default: return true;  // symmetric outputs keep the element-wise epilogue
+    }
+}
+
+// The dynamic shared-memory opt-in of a kernel, once per device (so that
+// nothing but launches happens while a caller captures a graph).
+template <class F>
+ln_status smem_optin(F kern, int bytes, bool (&done)[64]) {
+    int dev = 0;
+    LN_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !done[dev]) {
+        LN_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        if (dev >= 0 && dev < 64) done[dev] = true;
+    }
+    return LN_SUCCESS;
+}
+
+template <int AT, int BT, int TB, bool EXACT>
+ln_status launch_one(dim3 grid, int M, int N, int K, const SimtOperands &op, const EpiParams &epi, int sym,
+                     cudaStream_t st) {
+    static bool done[64] = {false};
+    auto kern = k_simt<AT, BT, TB, EXACT>;
+    constexpr int smem = Simt<AT, BT, TB, EXACT>::SMEM;
+    ln_status s = smem_optin(kern, smem, done);
+    if (s != LN_SUCCESS) return s;
+    kern<<<grid, 256, smem, st>>>(M, N, K, op, epi, sym);
+    return LN_SUCCESS;
+}
+
+template <int AT, int BT, int TB>
+ln_status launch_simt(dim3 grid, int M, int N, int K, const SimtOperands &op, const EpiParams &epi, int sym,
+                      bool exact, cudaStream_t st) {
+    return exact ? launch_one<AT, BT, TB, true>(grid, M, N, K, op, epi, sym, st)
+                 : launch_one<AT, BT, TB, false>(grid, M, N, K, op, epi, sym, st);
+}
+
+template <int TB>
+ln_status launch_simt_tb(dim3 grid, int M, int N, int K, const SimtOperands &op, const EpiParams &epi, int sym,
+                         bool exact, cudaStream_t st) {
+    if (op.a_t == 0 && op.b_t == 0) return launch_simt<0, 0, TB>(grid, M, N, K, op, epi, sym, exact, st);
+    if (op.a_t == 0 && op.b_t == 1) return launch_simt<0, 1, TB>(grid, M, N, K, op, epi, sym, exact, st);
+    if (op.a_t == 1 && op.b_t == 0) return launch_simt<1, 0, TB>(grid, M, N, K, op, epi, sym, exact, st);
+    return launch_simt<1, 1, TB>(grid, M, N, K, op, epi, sym, exact, st);
 }
 
 }  // namespace
 
 ln_status simt_contract(int M, int N, int K, const SimtOperands &op, const EpiParams &epi, cudaStream_t st) {
     const bool sym = epi.mode == EPI_SYM;
+    // 64-wide tiles when 128-wide ones would fill at most half the SMs
+    auto tiles_of = [&](int tb) {
+        const long long t = ceil_div(M, tb);
+        return sym ? t * (t + 1) / 2 : t * ceil_div(N, tb);
+    };
+    const int TB = 2 * tiles_of(128) <= sm_count() ? 64 : 128;
     dim3 grid;
     if (sym) {
-        long long t = ceil_div(M, TB);
-        grid = dim3((unsigned)(t * (t + 1) / 2));
+        grid = dim3((unsigned)tiles_of(TB));
     } else {
         grid = dim3((unsigned)ceil_div(N, TB), (unsigned)ceil_div(M, TB));
     }
-    LaunchScope ls_(FAM_SIMT, st);
-    if (op.a_t == 0 && op.b_t == 0) k_simt<0, 0><<<grid, 256, 0, st>>>(M, N, K, op, epi, sym);
-    else if (op.a_t == 0 && op.b_t == 1) k_simt<0, 1><<<grid, 256, 0, st>>>(M, N, K, op, epi, sym);
-    else if (op.a_t == 1 && op.b_t == 0) k_simt<1, 0><<<grid, 256, 0, st>>>(M, N, K, op, epi, sym);
-    else k_simt<1, 1><<<grid, 256, 0, st>>>(M, N, K, op, epi, sym);
+    const bool exact = tune_simt_exact() && exact_ok(M, N, K, TB, op, epi);
+    ln_status s;
+    {
+        LaunchScope ls_(FAM_SIMT, st);
+        s = TB == 64 ? launch_simt_tb<64>(grid, M, N, K, op, epi, sym, exact, st)
+                     : launch_simt_tb<128>(grid, M, N, K, op, epi, sym, exact, st);
+    }
+    if (s != LN_SUCCESS) return s;
     return check_launch("fp32 tiled contraction");
+}
+
+long long simt_sym_batched_tiles(int count, const ln_sym_desc *h) {
+    long long total = 0;
+    for (int i = 0; i < count; ++i) {
+        const long long t = ceil_div(h[i].n, TB_BATCH);
+        total += t * (t + 1) / 2;
+    }
+    return total;
 }
 
 ln_status simt_sym_batched_prefix(int count, const ln_sym_desc *d_descs, int *d_tile_prefix, cudaStream_t st) {
@@ -291,8 +535,15 @@ ln_status simt_sym_batched_prefix(int count, const ln_sym_desc *d_descs, int *d_
 
 ln_status simt_sym_batched(int is_syr2k, int count, const ln_sym_desc *d_descs, const int *d_tile_prefix,
                            int total_tiles, int fill, float alpha, float beta, cudaStream_t st) {
-    { LaunchScope ls_(FAM_SIMT, st); k_simt_sym_batched<<<(unsigned)total_tiles, 256, 0, st>>>(is_syr2k, d_descs, d_tile_prefix, count, fill, alpha,
-                                                              beta); }
+    static bool done[64] = {false};
+    constexpr int smem = Simt<0, 1, TB_BATCH, false>::SMEM;
+    ln_status s = smem_optin(k_simt_sym_batched, smem, done);
+    if (s != LN_SUCCESS) return s;
+    {
+        LaunchScope ls_(FAM_SIMT, st);
+        k_simt_sym_batched<<<(unsigned)total_tiles, 256, smem, st>>>(is_syr2k, d_descs, d_tile_prefix, count, fill,
+                                                                    alpha, beta);
+    }
     return check_launch("fp32 tiled batched syrk/syr2k");
 }
 
