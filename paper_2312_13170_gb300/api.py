@@ -392,6 +392,11 @@ class SymBatch:
         self.ws, self.nb = _workspace(nb, dev)
 
     def run(self, stream=None):
+        if self.count:
+            # the batch's class for the autotuner: count and mean instance sizes
+            ns = [d.n for d in self.h_descs[:self.count]]
+            ks = [d.k for d in self.h_descs[:self.count]]
+            _autotune(self.fn[3:], (self.count, sum(ns) // self.count, max(sum(ks) // self.count, 1)), self.prec)
         _check(getattr(lib(), self.fn)(self.fill, self.count, ctypes.byref(self.h_descs), _ptr(self.d_descs),
                                        self.alpha, self.beta, _ptr(self.ws), self.nb, self.form, self.prec,
                                        _stream(stream)), self.fn)

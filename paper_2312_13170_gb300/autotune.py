@@ -1,4 +1,5 @@
-"""Autotuner for the tensor-core engine's knobs (tile width, accumulation chunk).
+"""Autotuner for the engine knobs (tile width, accumulation chunk, CTA pairs,
+staged beta input, stream-K; the FP32 tiled form's EXACT instance).
 
 The runtime analogue of the compiler's tiling decision in loop
 internalization (paper Sec. VI-C: the pass tiles the loop by the work-group
@@ -11,8 +12,13 @@ call (``LN_AUTOTUNE=cached``) and may search on a miss (``LN_AUTOTUNE=search``);
 
 Knobs (see ``ln_set_tuning`` in include/loopnest.h): ``tile_n`` in {0 (automatic), 128, 256}
 for general contractions, ``chunk_kt`` in {1, 2} (k tiles accumulated in
-tensor memory before promotion to FP32 registers). Only configurations that
-keep the library's accuracy gate are offered.
+tensor memory before promotion to FP32 registers), ``pair`` in {0, 1} (CTA
+pairs with tcgen05.mma.cta_group::2), ``stage_beta`` in {0, 1}, ``stream_k``
+in {0, 1}, and for the FP32 tiled form ``simt_exact`` in {0, 1}. Batched
+SYRK/SYR2K are tuned over ``chunk_kt`` (their 128 x 128 symmetric tiles and
+stage count are fixed by the kernel's shared-memory plan). Only
+configurations that keep the library's accuracy gate are offered; every one
+gives a result within the gate, most bit-identical.
 
 Cache: ``LN_AUTOTUNE_CACHE`` or ``~/.cache/libloopnest/autotune.json``.
 """
@@ -23,19 +29,36 @@ import math
 import os
 import threading
 
+import numpy as np
+
 # tile_n 0 is the library's automatic width (256, or 128 for problems whose
 # 256-wide tiles would fill at most half the SMs)
+DEFAULT = {"tile_n": 0, "chunk_kt": 2, "pair": 1, "stage_beta": 1, "stream_k": 0, "simt_exact": 1}
+
+
+def _c(**kw):
+    return dict(DEFAULT, **kw)
+
+
+_GENERAL = [_c(), _c(tile_n=256), _c(tile_n=128), _c(chunk_kt=1), _c(pair=0), _c(stage_beta=0), _c(stream_k=1)]
+_SYM = [_c(), _c(chunk_kt=1), _c(stream_k=1)]
 CANDIDATES = {
-    "gemm": [{"tile_n": 0, "chunk_kt": 2}, {"tile_n": 256, "chunk_kt": 2}, {"tile_n": 128, "chunk_kt": 2},
-             {"tile_n": 0, "chunk_kt": 1}],
-    "gemm_chain": [{"tile_n": 0, "chunk_kt": 2}, {"tile_n": 256, "chunk_kt": 2}, {"tile_n": 128, "chunk_kt": 2},
-                   {"tile_n": 0, "chunk_kt": 1}],
-    "covariance": [{"tile_n": 0, "chunk_kt": 2}, {"tile_n": 0, "chunk_kt": 1}],
-    "correlation": [{"tile_n": 0, "chunk_kt": 2}, {"tile_n": 0, "chunk_kt": 1}],
-    "syrk": [{"tile_n": 0, "chunk_kt": 2}, {"tile_n": 0, "chunk_kt": 1}],
-    "syr2k": [{"tile_n": 0, "chunk_kt": 2}, {"tile_n": 0, "chunk_kt": 1}],
+    "gemm": _GENERAL,
+    "gemm_chain": _GENERAL,
+    "three_mm": [_c(), _c(tile_n=128), _c(chunk_kt=1), _c(pair=0), _c(stream_k=1)],
+    "covariance": _SYM,
+    "correlation": _SYM,
+    "syrk": _SYM,
+    "syr2k": _SYM,
+    "syrk_batched": [_c(), _c(chunk_kt=1)],
+    "syr2k_batched": [_c(), _c(chunk_kt=1)],
 }
-DEFAULT = {"tile_n": 0, "chunk_kt": 2}
+# the FP32 tiled form (every operation): its EXACT instance or the general one
+FP32_CANDIDATES = [_c(), _c(simt_exact=0)]
+
+
+def candidates(op, prec):
+    return FP32_CANDIDATES if prec == "fp32" else CANDIDATES[op]
 _lock = threading.Lock()
 _cache = None
 _state = threading.local()  # set while a search runs, so its own calls are not re-tuned
@@ -106,7 +129,7 @@ def _device_name():
 def _apply_config(cfg):
     from . import api
 
-    for k in ("tile_n", "chunk_kt"):
+    for k in DEFAULT:
         api.set_tuning(k, int(cfg.get(k, DEFAULT[k])))
 
 
@@ -140,6 +163,22 @@ def _runner(op, shape, prec):
         if op == "syrk":
             return lambda: api.syrk(A, C, 1.0, 0.0, prec=prec)
         return lambda: api.syr2k(A, B, C, 1.0, 0.0, prec=prec)
+    if op == "three_mm":
+        ni, nj, nk, nl, nm = shape
+        rng = np.random.default_rng(0)
+        A, B, C, D = (t(rng.uniform(-1, 1, size=s).astype(np.float32))
+                      for s in ((ni, nk), (nk, nj), (nj, nm), (nm, nl)))
+        return lambda: api.three_mm(A, B, C, D, prec=prec)
+    if op in ("syrk_batched", "syr2k_batched"):
+        # a batch of `count` instances of the class's mean sizes
+        count, n, k = shape
+        rng = np.random.default_rng(0)
+        As = [t(rng.uniform(-1, 1, size=(n, k)).astype(np.float32)) for _ in range(count)]
+        Bs = [t(rng.uniform(-1, 1, size=(n, k)).astype(np.float32)) for _ in range(count)] \
+            if op == "syr2k_batched" else None
+        Cs = [t(np.zeros((n, n), np.float32)) for _ in range(count)]
+        batch = api.SymBatch(As, Cs, Bs, 1.0, 0.0, prec=prec)
+        return batch.run
     raise ValueError(f"no tuner for {op}")
 
 
@@ -161,7 +200,7 @@ def tune(op, shape, prec="3xbf16", reps=5, save_result=True):
 
     _state.active = True
     try:
-        best, times = select(CANDIDATES[op], timer, reps)
+        best, times = select(candidates(op, prec), timer, reps)
     finally:
         _state.active = False
         _apply_config(DEFAULT)
@@ -175,7 +214,7 @@ def tune(op, shape, prec="3xbf16", reps=5, save_result=True):
 def apply(op, shape, prec):
     """Apply the tuned configuration for this call (per LN_AUTOTUNE)."""
     m = mode()
-    if m == "off" or prec == "fp32" or getattr(_state, "active", False):
+    if m == "off" or getattr(_state, "active", False):
         return
     k = key(_device_name(), op, prec, shape)
     entry = load().get(k)

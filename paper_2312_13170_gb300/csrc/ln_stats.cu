@@ -341,18 +341,38 @@ __global__ __launch_bounds__(256) void k_corr_cols(int n, int m, const float *__
 
 // d_j = sum_r Z dZ and the column mean of dXc = (dZ - Z d) rs, which is
 // rs_j (sum dZ - d_j sum Z) / n (the adjoint of the centring subtracts it).
-__global__ void k_corr_cols_final(int n, int m, int nch, const double *__restrict__ partials,
-                                  const float *__restrict__ rs, float *d, float *cmean) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
+// Column sums of the three partial-sum sets: a CTA takes 32 columns (lane =
+// column, coalesced), its 8 warps take every 8th row chunk, and the warps'
+// sums are added in warp order (deterministic).
+__global__ __launch_bounds__(256) void k_corr_cols_final(int n, int m, int nch, const double *__restrict__ partials,
+                                                         const float *__restrict__ rs, float *d, float *cmean) {
+    __shared__ double red[3][8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + lane;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int ch = 0; ch < nch; ++ch) {
-        s0 += partials[(long long)ch * m + j];
-        s1 += partials[((long long)nch + ch) * m + j];
-        s2 += partials[(2LL * nch + ch) * m + j];
+    if (j < m) {
+#pragma unroll 4
+        for (int ch = w; ch < nch; ch += 8) {
+            s0 += partials[(long long)ch * m + j];
+            s1 += partials[((long long)nch + ch) * m + j];
+            s2 += partials[(2LL * nch + ch) * m + j];
+        }
     }
-    d[j] = (float)s0;
-    cmean[j] = (float)((double)rs[j] * (s1 - s0 * s2) / (double)n);
+    red[0][w][lane] = s0;
+    red[1][w][lane] = s1;
+    red[2][w][lane] = s2;
+    __syncthreads();
+    if (w == 0 && j < m) {
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            t0 += red[0][g][lane];
+            t1 += red[1][g][lane];
+            t2 += red[2][g][lane];
+        }
+        d[j] = (float)t0;
+        cmean[j] = (float)((double)rs[j] * (t1 - t0 * t2) / (double)n);
+    }
 }
 
 // dX = (dZ - Z * d) * rs - cmean
@@ -503,7 +523,7 @@ ln_status corr_bwd_finish(int n, int m, const float *Z, long long ldz, const flo
     }
     {
         LaunchScope ls_(FAM_STATS, st);
-        k_corr_cols_final<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(n, m, nch, partials, rs, d, cmean);
+        k_corr_cols_final<<<(unsigned)ceil_div(m, 32), 256, 0, st>>>(n, m, nch, partials, rs, d, cmean);
     }
     {
         LaunchScope ls_(FAM_STATS, st);

@@ -38,9 +38,16 @@ def test_cache_roundtrip(tmp_path, monkeypatch):
 
 
 def test_candidates_respect_knob_domains():
-    for op, cands in autotune.CANDIDATES.items():
+    domains = {"tile_n": (0, 128, 256), "chunk_kt": (1, 2), "pair": (0, 1, 2), "stage_beta": (0, 1),
+               "stream_k": (0, 1), "simt_exact": (0, 1)}
+    for op, cands in list(autotune.CANDIDATES.items()) + [("fp32", autotune.FP32_CANDIDATES)]:
+        assert cands[0] == autotune.DEFAULT, op  # the library defaults are always a candidate
         for c in cands:
-            assert c["tile_n"] in (0, 128, 256) and c["chunk_kt"] in (1, 2), (op, c)
+            assert set(c) == set(domains), (op, c)
+            for k, v in c.items():
+                assert v in domains[k], (op, c)
+    assert autotune.candidates("gemm", "fp32") is autotune.FP32_CANDIDATES
+    assert autotune.candidates("syrk_batched", "3xbf16") is autotune.CANDIDATES["syrk_batched"]
 
 
 @pytest.mark.gpu
@@ -58,7 +65,7 @@ def test_tuning_pass_and_cached_use(tmp_path, monkeypatch):
     shape = (300, 260, 200, 280)
     best = autotune.tune("gemm_chain", shape, "3xbf16", reps=3)
     assert best in autotune.CANDIDATES["gemm_chain"]
-    assert api.get_tuning("tile_n") == 0 and api.get_tuning("chunk_kt") == 2  # defaults restored
+    assert all(api.get_tuning(k) == v for k, v in autotune.DEFAULT.items())  # defaults restored
     monkeypatch.setenv("LN_AUTOTUNE", "cached")
     d = inputs.chain_inputs(*shape, seed=3)
     t = {k: torch.from_numpy(d[k]).cuda() for k in "ABCD"}
@@ -68,13 +75,13 @@ def test_tuning_pass_and_cached_use(tmp_path, monkeypatch):
     assert inputs.rel_fro(F.cpu().numpy(), F_ref) <= 1e-5
     # every knob setting keeps the gate
     for cfg in autotune.CANDIDATES["gemm_chain"]:
-        api.set_tuning("tile_n", cfg["tile_n"])
-        api.set_tuning("chunk_kt", cfg["chunk_kt"])
+        for k, v in cfg.items():
+            api.set_tuning(k, v)
         E, F = api.gemm_chain(t["A"], t["B"], t["C"], t["D"], d["alpha"], d["beta"], prec="3xbf16")
         torch.cuda.synchronize()
         assert inputs.rel_fro(F.cpu().numpy(), F_ref) <= 1e-5, cfg
-    api.set_tuning("tile_n", 0)
-    api.set_tuning("chunk_kt", 2)
+    for k, v in autotune.DEFAULT.items():
+        api.set_tuning(k, v)
 
 
 @pytest.mark.gpu
@@ -109,3 +116,32 @@ def test_knob_settings_keep_parity(tile_n, chunk_kt):
     finally:
         api.set_tuning("tile_n", 0)
         api.set_tuning("chunk_kt", 2)
+
+
+@pytest.mark.gpu
+def test_tuning_batched_and_fp32(tmp_path, monkeypatch):
+    """The batched path and the FP32 tiled form are tuned and cached too; the
+    chosen configuration is applied before the call and keeps the gate."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    import oracle
+
+    __graft_entry__.build()
+    from paper_2312_13170_gb300 import api
+
+    monkeypatch.setenv("LN_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    best = autotune.tune("syrk_batched", (6, 200, 90), "3xbf16", reps=2)
+    assert best in autotune.CANDIDATES["syrk_batched"]
+    best = autotune.tune("gemm", (256, 256, 256), "fp32", reps=2)
+    assert best in autotune.FP32_CANDIDATES
+    monkeypatch.setenv("LN_AUTOTUNE", "cached")
+    g = inputs.gemm_inputs(256, 256, 256, seed=4)
+    C = torch.from_numpy(g["C"]).cuda()
+    api.gemm(torch.from_numpy(g["A"]).cuda(), torch.from_numpy(g["B"]).cuda(), C, g["alpha"], g["beta"],
+             form="internalized", prec="fp32")
+    assert api.get_tuning("simt_exact") == best["simt_exact"]
+    assert inputs.rel_fro(C.cpu().numpy(), oracle.gemm(g["A"], g["B"], g["C"], g["alpha"], g["beta"])) <= 1e-5
+    for k, v in autotune.DEFAULT.items():
+        api.set_tuning(k, v)
