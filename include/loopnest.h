@@ -60,7 +60,10 @@ typedef enum {
     LN_SUCCESS = 0,
     LN_ERR_INVALID_VALUE = 1, /* bad size, leading dimension, enum or NULL pointer */
     LN_ERR_ALIASING = 2,      /* an output range overlaps an input range */
-    LN_ERR_MISALIGNED = 3,    /* a pointer does not meet a stated alignment */
+    LN_ERR_MISALIGNED = 3,    /* the workspace pointer is not 256-byte aligned; data
+                                 pointers of any alignment are accepted (unaligned
+                                 rows take the slower copy paths), so no other
+                                 argument returns this code */
     LN_ERR_UNSUPPORTED = 4,   /* form/precision combination not available */
     LN_ERR_CUDA = 5,          /* a CUDA runtime call or launch failed */
     LN_ERR_TIMEOUT = 6,       /* a bounded device wait ran out (ln_stream_check) */
@@ -156,13 +159,16 @@ ln_status ln_timing_read(const char *family, double *total_ms /*host*/, int *lau
  *              block of D (chain) or C (GEMM) into the operand stages once its
  *              MMAs are done, so the epilogue stores E at once and reads D or
  *              C from shared memory;
- *   "stream_k" 0 or 1 (default 0): stream-K for single tensor-core
+ *   "stream_k" 0, 1 or 2 (default 2): stream-K for single tensor-core
  *              contractions with fewer output tiles than SMs (covariance,
  *              correlation, SYRK/SYR2K and the general contractions that do
  *              not run beside another one): the tiles' k ranges are split
  *              evenly over one CTA per SM; a tile spread over several CTAs
  *              gets their FP32 partial sums through the workspace, added in
- *              k order by the CTA that holds its first k tile;
+ *              k order by the CTA that holds its first k tile; 1 applies it
+ *              to every such contraction with at least 4 k tiles per SM,
+ *              2 only to those that also fill at most half the SMs and have
+ *              at least 32 k tiles of 64 (where it measured faster), 0 never;
  *   "gs_rows"  2 or 4 (default 4): rows of the matrix each thread holds in
  *              registers in the internalized Gram-Schmidt panel kernel when
  *              512 < m <= 1024 (512 or 256 threads per panel CTA).
@@ -259,6 +265,25 @@ ln_status ln_correlation(int nsamples, int nfeat, const float *X, int ldx, float
                          void *stream);
 
 /*
+ * Forward calls that also keep the adjoint's saved state: the same result as
+ * ln_covariance / ln_correlation (bit for bit: the same kernels in the same
+ * order), and `stats` (device, 8-byte aligned, 2*nfeat doubles, not
+ * overlapping X or the output) receives the FP64 column means then the sums
+ * of squared deviations from them, as ln_col_stats computes them -- the
+ * `stats` that ln_covariance_bwd / ln_correlation_bwd take. The statistics
+ * are written straight into `stats`, so a forward-backward pair runs the
+ * statistics passes once. The covariance's internalized form adds the second
+ * (squared deviations) pass that ln_covariance skips. Workspace: as
+ * ln_covariance_workspace_size. NULL stats gives LN_ERR_INVALID_VALUE.
+ */
+ln_status ln_covariance_fwd(int nsamples, int nfeat, const float *X, int ldx, float *cov, int ldcov, double *stats,
+                            void *workspace, size_t workspace_bytes, ln_form form, ln_precision prec,
+                            void *stream);
+ln_status ln_correlation_fwd(int nsamples, int nfeat, const float *X, int ldx, float *corr, int ldcorr,
+                             double *stats, void *workspace, size_t workspace_bytes, ln_form form,
+                             ln_precision prec, void *stream);
+
+/*
  * Covariance for callers that cannot allocate device memory (code that runs
  * where cudaMalloc is not allowed or would exceed a fixed memory budget, such
  * as inside an allocator, a memory-capped sandbox or a loop that must never
@@ -273,10 +298,10 @@ ln_status ln_correlation(int nsamples, int nfeat, const float *X, int ldx, float
  * columns); sizes whose scratch exceeds 8 MiB, and sizes outside [0, 2^22],
  * give LN_ERR_INVALID_VALUE with a message and launch nothing.
  * The array's device address is looked up (cudaGetSymbolAddress, under a
- * lock) on every call made outside stream capture and remembered per device;
- * a call during capture uses the remembered address, so the first call on a
- * device -- and the first after a cudaDeviceReset, which can move the array --
- * must come before any capture (else LN_ERR_UNSUPPORTED). All calls share the
+ * lock) on each call and remembered per device (a cudaDeviceReset can move
+ * the array; the next lookup finds it); where the stream's state does not
+ * allow the lookup, the remembered address is used, and with none remembered
+ * the call gives LN_ERR_UNSUPPORTED and launches nothing. All calls share the
  * array, so calls whose kernels may overlap on the GPU (unordered streams)
  * race; calls in one stream are safe. X, cov and stream as in ln_covariance.
  */
@@ -390,7 +415,8 @@ ln_status ln_3mm_bwd(int ni, int nj, int nk, int nl, int nm, const float *A, con
  * diagonal: dZ = Z (W' + W'^T); dXc_j = (dZ_j - Z_j (Z_j . dZ_j)) / s_j;
  * dX = dXc - 1 (1^T dXc) / nsamples.
  * `stats` (nullable) holds 2*nfeat doubles, mean then ss, from a forward call
- * (ln_col_stats); when NULL they are recomputed from X. The centred matrix is
+ * (ln_covariance_fwd, ln_correlation_fwd or ln_col_stats), read in place;
+ * when NULL they are recomputed from X. The centred matrix is
  * always recomputed from X rather than stored.
  */
 ln_status ln_gemm_chain_bwd_workspace_size(int ni, int nj, int nk, int nl, ln_form form, ln_precision prec,

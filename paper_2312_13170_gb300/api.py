@@ -73,6 +73,8 @@ _SIGS = {
     "ln_covariance_workspace_size": (_I, [_I, _I, _I, _I, _P]),
     "ln_covariance": (_I, [_I, _I, _P, _I, _P, _I, _P, _SZ, _I, _I, _P]),
     "ln_correlation": (_I, [_I, _I, _P, _I, _P, _I, _P, _SZ, _I, _I, _P]),
+    "ln_covariance_fwd": (_I, [_I, _I, _P, _I, _P, _I, _P, _P, _SZ, _I, _I, _P]),
+    "ln_correlation_fwd": (_I, [_I, _I, _P, _I, _P, _I, _P, _P, _SZ, _I, _I, _P]),
     "ln_covariance_noalloc": (_I, [_I, _I, _P, _I, _P, _I, _P]),
     "ln_syrk_workspace_size": (_I, [_I, _I, _I, _I, _P]),
     "ln_syrk": (_I, [_I, _I, _I, _F, _P, _I, _F, _P, _I, _P, _SZ, _I, _I, _P]),
@@ -316,14 +318,19 @@ def col_stats(X, form="internalized", stream=None):
     return mean, ss
 
 
-def _covlike(fn, X, form, prec, stream, out):
+def _covlike(fn, X, form, prec, stream, out, stats=None):
     _f32(X, "X")
     n, m = X.shape
     fm, pr = _enum(FORMS, form, "form"), _enum(PRECS, prec, "precision")
     out = torch.empty((m, m), dtype=torch.float32, device=X.device) if out is None else out
-    _autotune("covariance" if fn == "ln_covariance" else "correlation", (n, m), prec)
+    _autotune("covariance" if fn.startswith("ln_covariance") else "correlation", (n, m), prec)
     ws, nb = _workspace(_ws_query("ln_covariance_workspace_size", n, m, fm, pr), X.device)
-    _check(getattr(lib(), fn)(n, m, _ptr(X), _ld(X), _ptr(out), _ld(out), _ptr(ws), nb, fm, pr, _stream(stream)), fn)
+    if stats is None:
+        _check(getattr(lib(), fn)(n, m, _ptr(X), _ld(X), _ptr(out), _ld(out), _ptr(ws), nb, fm, pr, _stream(stream)),
+               fn)
+    else:
+        _check(getattr(lib(), fn)(n, m, _ptr(X), _ld(X), _ptr(out), _ld(out), _ptr(stats), _ptr(ws), nb, fm, pr,
+                                  _stream(stream)), fn)
     return out
 
 
@@ -333,6 +340,20 @@ def covariance(X, form="internalized", prec="3xbf16", stream=None, out=None):
 
 def correlation(X, form="internalized", prec="3xbf16", stream=None, out=None):
     return _covlike("ln_correlation", X, form, prec, stream, out)
+
+
+def covariance_fwd(X, form="internalized", prec="3xbf16", stream=None, out=None):
+    """(cov, stats): the covariance and the FP64 [mean; ss] (2*nfeat) that
+    covariance_bwd takes, from one call."""
+    stats = torch.empty(2 * X.shape[1], dtype=torch.float64, device=X.device)
+    return _covlike("ln_covariance_fwd", X, form, prec, stream, out, stats), stats
+
+
+def correlation_fwd(X, form="internalized", prec="3xbf16", stream=None, out=None):
+    """(corr, stats): the correlation and the FP64 [mean; ss] (2*nfeat) that
+    correlation_bwd takes, from one call."""
+    stats = torch.empty(2 * X.shape[1], dtype=torch.float64, device=X.device)
+    return _covlike("ln_correlation_fwd", X, form, prec, stream, out, stats), stats
 
 
 def syrk(A, C, alpha=1.0, beta=0.0, fill="full", form="internalized", prec="3xbf16", stream=None):
@@ -490,15 +511,15 @@ class GemmChainFn(torch.autograd.Function):
         return dA, dB, dC, None, None
 
 
-def _cov_forward(ctx, X, fwd, form, prec, keep_stats):
+def _cov_forward(ctx, X, fwd, fwd_stats, form, prec, keep_stats):
     Xc = X.contiguous()
-    stats = None
-    if keep_stats:
-        mean, ss = col_stats(Xc, form)
-        stats = torch.cat([mean, ss])
-    ctx.save_for_backward(Xc, stats if stats is not None else torch.empty(0, device=X.device))
+    if keep_stats:  # one call: the result and the statistics the adjoint reads
+        out, stats = fwd_stats(Xc, form, prec)
+    else:
+        out, stats = fwd(Xc, form, prec), torch.empty(0, device=X.device)
+    ctx.save_for_backward(Xc, stats)
     ctx.cfg = (form, prec, keep_stats)
-    return fwd(Xc, form, prec)
+    return out
 
 
 def _cov_backward(ctx, gR, bwd):
@@ -513,7 +534,7 @@ class CovarianceFn(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, X, form="internalized", prec="3xbf16", keep_stats=True):
-        return _cov_forward(ctx, X, covariance, form, prec, keep_stats)
+        return _cov_forward(ctx, X, covariance, covariance_fwd, form, prec, keep_stats)
 
     @staticmethod
     def backward(ctx, gR):
@@ -525,7 +546,7 @@ class CorrelationFn(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, X, form="internalized", prec="3xbf16", keep_stats=True):
-        return _cov_forward(ctx, X, correlation, form, prec, keep_stats)
+        return _cov_forward(ctx, X, correlation, correlation_fwd, form, prec, keep_stats)
 
     @staticmethod
     def backward(ctx, gR):

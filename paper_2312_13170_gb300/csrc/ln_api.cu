@@ -82,7 +82,7 @@ std::atomic<int> g_tile_n{0};
 std::atomic<int> g_pack_threads{512};
 std::atomic<int> g_split_k{0};
 std::atomic<int> g_gs_rows{4};
-std::atomic<int> g_stream_k{0};
+std::atomic<int> g_stream_k{2};
 std::atomic<int> g_pair{1};
 std::atomic<int> g_stage_beta{1};
 std::atomic<int> g_simt_exact{1};
@@ -511,8 +511,10 @@ void plan_cov(Ws &w, int n, int m, ln_form form, ln_precision prec, CovPlan &p) 
     }
 }
 
-ln_status run_cov(bool corr, int n, int m, const float *X, int ldx, float *out, int ldo, void *ws, size_t wsb,
-                  ln_form form, ln_precision prec, cudaStream_t st) {
+// stats (nullable): 2*m doubles, mean then ss, written for the adjoint; the
+// statistics passes then write there instead of into the workspace.
+ln_status run_cov(bool corr, int n, int m, const float *X, int ldx, float *out, int ldo, double *stats, void *ws,
+                  size_t wsb, ln_form form, ln_precision prec, cudaStream_t st) {
     LN_TRY(check_dims({n, m}));
     LN_TRY(check_form(form, prec));
     if (m == 0) return LN_SUCCESS;
@@ -520,12 +522,22 @@ ln_status run_cov(bool corr, int n, int m, const float *X, int ldx, float *out, 
     if (!X || !out) return fail(LN_ERR_INVALID_VALUE, "NULL X or output");
     if (ldx < m || ldo < m) return fail(LN_ERR_INVALID_VALUE, "leading dimension smaller than nfeat");
     if (overlap(mspan(out, m, m, ldo), mspan(X, n, m, ldx))) return fail(LN_ERR_ALIASING, "output overlaps X");
+    if (stats) {
+        const Span ss{stats, sizeof(double) * 2 * (size_t)m};
+        if (overlap(ss, mspan(out, m, m, ldo)) || overlap(ss, mspan(X, n, m, ldx)))
+            return fail(LN_ERR_ALIASING, "statistics overlap X or the output");
+        if (reinterpret_cast<uintptr_t>(stats) & 7) return fail(LN_ERR_INVALID_VALUE, "statistics not 8-byte aligned");
+    }
     Ws count(nullptr);
     CovPlan p;
     plan_cov(count, n, m, form, prec, p);
     LN_TRY(check_ws(ws, wsb, count.off));
     Ws w(ws);
     plan_cov(w, n, m, form, prec, p);
+    if (stats) {
+        p.mean = stats;
+        p.ss = stats + m;
+    }
 
     EpiParams e{};
     e.mode = EPI_SYM;
@@ -543,8 +555,9 @@ ln_status run_cov(bool corr, int n, int m, const float *X, int ldx, float *out, 
         return plain_cov(n, m, X, ldx, p.mean, e, st);
     }
     LN_TRY(zero_streamk_flags(p.split, st));
-    // covariance centres with the means only; correlation also needs the second pass (1/s)
-    if (corr) LN_TRY(col_stats(n, m, X, ldx, p.mean, p.ss, p.hi, p.lo, p.rs, p.partials, st));
+    // covariance centres with the means only; correlation, and a call that
+    // returns the statistics, also need the second pass
+    if (corr || stats) LN_TRY(col_stats(n, m, X, ldx, p.mean, p.ss, p.hi, p.lo, p.rs, p.partials, st));
     else LN_TRY(col_mean(n, m, X, ldx, p.mean, p.hi, p.lo, p.partials, st));
     if (!tensor_prec(prec)) {
         SimtOperands op{};
@@ -898,14 +911,6 @@ void plan_cov_bwd(Ws &w, bool corr, int n, int m, ln_form form, ln_precision pre
     }
 }
 
-__global__ void k_copy_stats(int m, const double *src, double *mean, double *ss) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < m) {
-        mean[j] = src[j];
-        ss[j] = src[m + j];
-    }
-}
-
 ln_status run_cov_bwd(bool corr, int n, int m, const float *X, int ldx, const float *W, int ldw, const double *stats,
                       float *dX, int lddx, void *ws, size_t wsb, ln_form form, ln_precision prec, cudaStream_t st) {
     LN_TRY(check_dims({n, m}));
@@ -926,12 +931,7 @@ ln_status run_cov_bwd(bool corr, int n, int m, const float *X, int ldx, const fl
     plan_cov_bwd(w, corr, n, m, form, prec, p);
 
     if (stats) {
-        {
-            LaunchScope ls(FAM_STATS, st);
-            k_copy_stats<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(m, stats, p.mean, p.ss);
-        }
-        LN_TRY(check_launch("copy statistics"));
-        LN_TRY(stats_derive(m, p.mean, p.ss, p.hi, p.lo, p.rs, st));
+        LN_TRY(stats_derive(m, stats, stats + m, p.hi, p.lo, p.rs, st));
     } else if (form == LN_FORM_PLAIN) {
         LN_TRY(plain_col_stats(n, m, X, ldx, p.mean, p.ss, st));
         LN_TRY(stats_derive(m, p.mean, p.ss, p.hi, p.lo, p.rs, st));
@@ -1011,7 +1011,7 @@ ln_status ln_set_tuning(const char *key, int value) {
         return LN_SUCCESS;
     }
     if (strcmp(key, "stream_k") == 0) {
-        if (value != 0 && value != 1) return fail(LN_ERR_INVALID_VALUE, "stream_k must be 0 or 1 (got %d)", value);
+        if (value < 0 || value > 2) return fail(LN_ERR_INVALID_VALUE, "stream_k must be 0, 1 or 2 (got %d)", value);
         g_stream_k.store(value);
         return LN_SUCCESS;
     }
@@ -1501,13 +1501,27 @@ ln_status ln_covariance_workspace_size(int nsamples, int nfeat, ln_form form, ln
 ln_status ln_covariance(int nsamples, int nfeat, const float *X, int ldx, float *cov, int ldcov, void *ws, size_t wsb,
                         ln_form form, ln_precision prec, void *stream) {
     clear_error();
-    return run_cov(false, nsamples, nfeat, X, ldx, cov, ldcov, ws, wsb, form, prec, S(stream));
+    return run_cov(false, nsamples, nfeat, X, ldx, cov, ldcov, nullptr, ws, wsb, form, prec, S(stream));
 }
 
 ln_status ln_correlation(int nsamples, int nfeat, const float *X, int ldx, float *corr, int ldcorr, void *ws,
                          size_t wsb, ln_form form, ln_precision prec, void *stream) {
     clear_error();
-    return run_cov(true, nsamples, nfeat, X, ldx, corr, ldcorr, ws, wsb, form, prec, S(stream));
+    return run_cov(true, nsamples, nfeat, X, ldx, corr, ldcorr, nullptr, ws, wsb, form, prec, S(stream));
+}
+
+ln_status ln_covariance_fwd(int nsamples, int nfeat, const float *X, int ldx, float *cov, int ldcov, double *stats,
+                            void *ws, size_t wsb, ln_form form, ln_precision prec, void *stream) {
+    clear_error();
+    if (!stats) return fail(LN_ERR_INVALID_VALUE, "NULL statistics");
+    return run_cov(false, nsamples, nfeat, X, ldx, cov, ldcov, stats, ws, wsb, form, prec, S(stream));
+}
+
+ln_status ln_correlation_fwd(int nsamples, int nfeat, const float *X, int ldx, float *corr, int ldcorr,
+                             double *stats, void *ws, size_t wsb, ln_form form, ln_precision prec, void *stream) {
+    clear_error();
+    if (!stats) return fail(LN_ERR_INVALID_VALUE, "NULL statistics");
+    return run_cov(true, nsamples, nfeat, X, ldx, corr, ldcorr, stats, ws, wsb, form, prec, S(stream));
 }
 
 // ------------------------------------------------------------------ SYRK / SYR2K

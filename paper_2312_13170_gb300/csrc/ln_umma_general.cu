@@ -58,7 +58,11 @@ size_t umma_split_cnt_bytes(long long tiles, int) { return (size_t)tiles * 8 * s
 
 int umma_streamk(long long tiles, int ktot) {
     const int sms = sm_count();
-    if (!tune_stream_k() || tiles <= 0 || tiles >= sms) return 0;
+    const int knob = tune_stream_k();
+    if (!knob || tiles <= 0 || tiles >= sms) return 0;
+    // automatic (2): only deep contractions that fill at most half the SMs,
+    // where the idle SMs outweigh the partial-sum hand-off
+    if (knob == 2 && (2 * tiles > sms || ktot < 32)) return 0;
     return tiles * ktot >= 4LL * sms ? 1 : 0;
 }
 

@@ -121,6 +121,14 @@ def test_sym_validation(L):
 def test_cov_validation(L):
     assert L.ln_covariance(1, 8, P(FAKE_A), 8, P(FAKE_C), 8, None, 0, 0, 0, None) == 1
     assert L.ln_correlation(16, 8, P(FAKE_A), 8, P(FAKE_A + 64), 8, None, 0, 0, 0, None) == 2
+    # the statistics-returning forms: NULL, overlapping X or the output, misaligned
+    assert L.ln_covariance_fwd(16, 8, P(FAKE_A), 8, P(FAKE_C), 8, None, None, 0, 1, 2, None) == 1
+    assert "statistics" in last(L)
+    assert L.ln_correlation_fwd(16, 8, P(FAKE_A), 8, P(FAKE_C), 8, P(FAKE_A + 8), None, 0, 1, 2, None) == 2
+    assert L.ln_correlation_fwd(16, 8, P(FAKE_A), 8, P(FAKE_C), 8, P(FAKE_C + 64), None, 0, 1, 2, None) == 2
+    assert L.ln_covariance_fwd(16, 8, P(FAKE_A), 8, P(FAKE_C), 8, P(FAKE_B + 4), None, 0, 1, 2, None) == 1
+    # a valid call without a workspace stops at the workspace check, before any launch
+    assert L.ln_covariance_fwd(16, 8, P(FAKE_A), 8, P(FAKE_C), 8, P(FAKE_B), None, 0, 1, 2, None) == 7
 
 
 def test_batched_validation(L):
@@ -197,8 +205,8 @@ def test_gramschmidt_validation(L):
     v = ctypes.c_int(0)
     assert L.ln_get_tuning(b"gs_rows", ctypes.byref(v)) == 0 and v.value == 4
     assert L.ln_set_tuning(b"gs_rows", 3) == 1
-    assert L.ln_get_tuning(b"stream_k", ctypes.byref(v)) == 0 and v.value == 0
-    assert L.ln_set_tuning(b"stream_k", 2) == 1
+    assert L.ln_get_tuning(b"stream_k", ctypes.byref(v)) == 0 and v.value == 2
+    assert L.ln_set_tuning(b"stream_k", 3) == 1
     assert L.ln_get_tuning(b"pair", ctypes.byref(v)) == 0 and v.value == 1
     assert L.ln_set_tuning(b"pair", 3) == 1
     assert L.ln_get_tuning(b"stage_beta", ctypes.byref(v)) == 0 and v.value == 1

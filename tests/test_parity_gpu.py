@@ -290,6 +290,29 @@ def test_cov_corr_bwd(api, form, prec, corr):
     assert inputs.rel_fro(host(dX2), ref) <= GATE
 
 
+@pytest.mark.parametrize("form,prec", [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16")])
+@pytest.mark.parametrize("corr", [False, True])
+def test_cov_corr_fwd_keeps_stats(api, form, prec, corr):
+    """ln_covariance_fwd / ln_correlation_fwd: the result bit for bit that of
+    the plain call, the statistics bit for bit those of ln_col_stats, and the
+    adjoint reading them equal to the one that recomputes them."""
+    d = inputs.backward_inputs(333, 140, 8, seed=9)
+    X, W = dev(d["X"]), dev(d["W"][:140, :140].copy())
+    fwd, plain = (api.correlation_fwd, api.correlation) if corr else (api.covariance_fwd, api.covariance)
+    out, stats = fwd(X, form=form, prec=prec)
+    ref = plain(X, form=form, prec=prec)
+    mean, ss = api.col_stats(X, form=form)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    assert torch.equal(stats, torch.cat([mean, ss]))
+    assert inputs.rel_fro(host(out), (oracle.correlation if corr else oracle.covariance)(d["X"])) <= GATE
+    bwd = api.correlation_bwd if corr else api.covariance_bwd
+    dX1 = bwd(X, W, stats=stats, form=form, prec=prec)
+    dX0 = bwd(X, W, form=form, prec=prec)
+    torch.cuda.synchronize()
+    assert torch.equal(dX1, dX0)
+
+
 def test_autograd_functions(api):
     d = inputs.backward_inputs(256, 48, 40, seed=6)
     X = dev(d["X"]).requires_grad_(True)

@@ -30,7 +30,7 @@ def api():
     from paper_2312_13170_gb300 import api as a
 
     yield a
-    a.set_tuning("stream_k", 0)
+    a.set_tuning("stream_k", 2)
 
 
 def dev(x):
@@ -49,7 +49,7 @@ def both(api, fn):
         api.set_tuning("stream_k", on)
         out.append(fn())
         api.stream_check()
-    api.set_tuning("stream_k", 0)
+    api.set_tuning("stream_k", 2)
     return out
 
 
@@ -154,6 +154,44 @@ def test_cov_corr_streamk(api):
         assert np.array_equal(c, c.T) and np.all(np.diag(r) == 1.0)
 
 
+def test_streamk_automatic_policy(api):
+    """The default (2) takes stream-K only for deep contractions filling at
+    most half the SMs: the correlation of a 4096 x 1024 matrix (36 tiles of 64
+    k tiles; its workspace grows by the partial-sum area) but not the
+    8192 x 2048 covariance (136 tiles). Results: oracle gate, and integer SYRK
+    of the same shape bit for bit against stream-K off."""
+    import ctypes
+
+    assert api.get_tuning("stream_k") == 2
+
+    def ws(n, m):
+        b = ctypes.c_size_t()
+        assert api.lib().ln_covariance_workspace_size(n, m, 1, 2, ctypes.byref(b)) == 0
+        return b.value
+
+    sizes = {}
+    for v in (0, 2):
+        api.set_tuning("stream_k", v)
+        sizes[v] = (ws(4096, 1024), ws(8192, 2048))
+    assert sizes[2][0] > sizes[0][0] and sizes[2][1] == sizes[0][1]
+    X = inputs.cov_inputs(4096, 1024, seed=37)["X"]
+    got = host(api.correlation(dev(X), prec="3xbf16"))
+    api.stream_check()
+    assert inputs.rel_fro(got, oracle.correlation(X)) <= GATE
+    A = inputs.int_matrix((1024, 4096), seed=38)
+    C0 = inputs.int_matrix((1024, 1024), seed=39)
+    ref = oracle.syrk(A, C0, 2.0, 1.0, 0)
+    outs = []
+    for v in (2, 0):
+        api.set_tuning("stream_k", v)
+        C = dev(C0)
+        api.syrk(dev(A), C, 2.0, 1.0, prec="3xbf16")
+        outs.append(host(C))
+        api.stream_check()
+    api.set_tuning("stream_k", 2)
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], ref.astype(np.float32))
+
+
 def test_streamk_graph_replay(api):
     """The stream-K flags are cleared inside the captured call: replays agree bit for bit."""
     api.set_tuning("stream_k", 1)
@@ -174,7 +212,7 @@ def test_streamk_graph_replay(api):
         graph.replay()
         outs.append(host(C))
     api.stream_check()
-    api.set_tuning("stream_k", 0)
+    api.set_tuning("stream_k", 2)
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
     ref = oracle.gemm(g["A"], g["B"], g["C"], g["alpha"], 0.0)
     assert inputs.rel_fro(outs[0], ref) <= GATE
