@@ -63,6 +63,7 @@ METRIC = "GFLOP/s & roofline fraction, internalized vs plain kernels, at <=1e-5 
 FLOPS = 4.0 * N ** 3          # two N^3 multiply-adds per step
 FLOPS_PER_UMMA = 2.0 * N ** 3
 PRODUCTS = 3                   # MMA products per multiply-add in the 3xBF16 split
+TF32_RATIO = 1.1 / 2.25        # nominal dense TF32 / BF16 tensor throughput
 
 
 def parse():
@@ -476,7 +477,14 @@ def suite_lines(modes, only, reps, sink):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def peak_of(prec):
-        return fp32_peak if prec == "fp32" else bf16_peak / {"bf16": 1, "3xbf16": 3, "6xbf16": 6}[prec]
+        """Peak of a mode: FP32 from unit counts; the measured BF16 peak divided
+        by the products; TF32 modes from the BF16 peak scaled by the nominal
+        dense TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s)."""
+        if prec == "fp32":
+            return fp32_peak
+        if prec in ("tf32", "3xtf32"):
+            return bf16_peak * TF32_RATIO / (3 if prec == "3xtf32" else 1)
+        return bf16_peak / {"bf16": 1, "3xbf16": 3, "6xbf16": 6}[prec]
 
     def time_it(fn, n=reps, graph=True):
         """Median and mean device time of fn over n repetitions, L2 flushed
@@ -540,7 +548,7 @@ def suite_lines(modes, only, reps, sink):
 ALL_WORKLOADS = {"gemm", "chain", "3mm", "cov", "batched", "backward", "gramschmidt"}
 SUITE_MODES = [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16")]
 ALL_MODES = [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "bf16"), ("internalized", "3xbf16"),
-             ("internalized", "6xbf16")]
+             ("internalized", "6xbf16"), ("internalized", "tf32"), ("internalized", "3xtf32")]
 
 
 def run_suite(args):

@@ -78,14 +78,20 @@ typedef enum { LN_FORM_PLAIN = 0, LN_FORM_INTERNALIZED = 1 } ln_form;
  * only): BF16 = one product of BF16-rounded operands; 3XBF16 = each operand
  * split x = hi + lo into two BF16 terms, products hi*hi + hi*lo + lo*hi;
  * 6XBF16 = three BF16 terms (hi + mid + lo), the six products whose order is
- * at least 2^-16. FP32, 3XBF16 and 6XBF16 meet a 1e-5 relative Frobenius error
- * against exact arithmetic on the shipped workloads; BF16 does not.
+ * at least 2^-16. TF32 = one product of TF32-rounded operands (10-bit
+ * mantissa, round to nearest, ties away from zero); 3XTF32 = x = hi + lo in
+ * two TF32 terms, products hi*hi + hi*lo + lo*hi, on the tensor cores' TF32
+ * path (half the BF16 rate per product). FP32, 3XBF16, 6XBF16 and 3XTF32
+ * meet a 1e-5 relative Frobenius error against exact arithmetic on the shipped
+ * workloads; BF16 and TF32 do not.
  */
 typedef enum {
     LN_PREC_FP32 = 0,
     LN_PREC_BF16 = 1,
     LN_PREC_3XBF16 = 2,
-    LN_PREC_6XBF16 = 3
+    LN_PREC_6XBF16 = 3,
+    LN_PREC_TF32 = 4,
+    LN_PREC_3XTF32 = 5
 } ln_precision;
 
 /* Triangle of a symmetric output (SYRK/SYR2K): LOWER/UPPER read and write only

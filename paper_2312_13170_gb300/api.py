@@ -6,7 +6,7 @@ workspace) and the current CUDA stream. There is no CPU fallback: if the
 shared library has not been built, every call raises.
 
 Names follow the C ABI (ln_gemm -> gemm, ...). `form` is "plain" or
-"internalized"; `prec` is "fp32", "bf16", "3xbf16" or "6xbf16".
+"internalized"; `prec` is "fp32", "bf16", "3xbf16", "6xbf16", "tf32" or "3xtf32".
 """
 from __future__ import annotations
 
@@ -19,10 +19,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libloopnest.so")
 
 FORMS = {"plain": 0, "internalized": 1}
-PRECS = {"fp32": 0, "bf16": 1, "3xbf16": 2, "6xbf16": 3}
+PRECS = {"fp32": 0, "bf16": 1, "3xbf16": 2, "6xbf16": 3, "tf32": 4, "3xtf32": 5}
 FILLS = {"full": 0, "lower": 1, "upper": 2}
 # MMA products per multiply-add of each precision (for effective-peak accounting)
-PRODUCTS = {"fp32": 1, "bf16": 1, "3xbf16": 3, "6xbf16": 6}
+PRODUCTS = {"fp32": 1, "bf16": 1, "3xbf16": 3, "6xbf16": 6, "tf32": 1, "3xtf32": 3}
 
 STATUS = {
     0: "LN_SUCCESS", 1: "LN_ERR_INVALID_VALUE", 2: "LN_ERR_ALIASING", 3: "LN_ERR_MISALIGNED",

@@ -298,7 +298,7 @@ bool overlap(Span a, Span b) {
 ln_status check_form(ln_form form, ln_precision prec) {
     if (form != LN_FORM_PLAIN && form != LN_FORM_INTERNALIZED)
         return fail(LN_ERR_INVALID_VALUE, "unknown form %d", (int)form);
-    if (prec < LN_PREC_FP32 || prec > LN_PREC_6XBF16) return fail(LN_ERR_INVALID_VALUE, "unknown precision %d", (int)prec);
+    if (prec < LN_PREC_FP32 || prec > LN_PREC_3XTF32) return fail(LN_ERR_INVALID_VALUE, "unknown precision %d", (int)prec);
     if (form == LN_FORM_PLAIN && prec != LN_PREC_FP32)
         return fail(LN_ERR_UNSUPPORTED, "the plain form computes in FP32 only (precision %d requested)", (int)prec);
     return LN_SUCCESS;
@@ -384,6 +384,7 @@ ln_status run_contract(int M, int N, int K, Operand a, Operand b, const EpiParam
     const int P = prec_terms(prec);
     PackSrc ps[2] = {{a.p, a.ld, a.t ? 1 : 0, M, K, nullptr, nullptr, cp.px, cp.mt, cp.kt},
                      {b.p, b.ld, b.t ? 0 : 1, N, K, nullptr, nullptr, cp.py, cp.yrt, cp.kt}};
+    for (PackSrc &q : ps) q.tf32 = is_tf32(prec);
     LN_TRY(zero_streamk_flags(cp.split, st));
     LN_TRY(pack_operands(ps, 2, P, st));
     UmmaProblem pb{};
@@ -396,6 +397,7 @@ ln_status run_contract(int M, int N, int K, Operand a, Operand b, const EpiParam
     pb.nt = cp.nt;
     pb.sym = 0;
     pb.chunk_kt = tune_chunk_kt();
+    pb.tf32 = is_tf32(prec);
     pb.inject_timeout = inject_timeout_requested();
     apply_split(pb, cp.split);
     pb.bn = cp.bn;
@@ -574,6 +576,7 @@ ln_status run_cov(bool corr, int n, int m, const float *X, int ldx, float *out, 
     }
     const int P = prec_terms(prec);
     PackSrc ps{X, ldx, 1, m, n, p.hi, p.lo, p.pack, p.mt, p.kt};
+    ps.tf32 = is_tf32(prec);
     LN_TRY(pack_operand(ps, P, st));
     UmmaProblem pb{};
     pb.seg[0] = {p.pack, p.pack};
@@ -583,6 +586,7 @@ ln_status run_cov(bool corr, int n, int m, const float *X, int ldx, float *out, 
     pb.mt = pb.nt = p.mt;
     pb.sym = 1;
     pb.chunk_kt = tune_chunk_kt();
+    pb.tf32 = is_tf32(prec);
     apply_split(pb, p.split);
     pb.epi = e;
     return umma_contract(pb, P, st);
@@ -654,6 +658,7 @@ ln_status run_sym(bool two, ln_fill fill, int n, int k, float alpha, const float
     const int P = prec_terms(prec);
     PackSrc ps[2] = {{A, lda, 0, n, k, nullptr, nullptr, p.pa, p.mt, p.kt},
                      {B, ldb, 0, n, k, nullptr, nullptr, p.pb, p.mt, p.kt}};
+    for (PackSrc &q : ps) q.tf32 = is_tf32(prec);
     LN_TRY(zero_streamk_flags(p.split, st));
     LN_TRY(pack_operands(ps, two ? 2 : 1, P, st));
     UmmaProblem pb{};
@@ -670,6 +675,7 @@ ln_status run_sym(bool two, ln_fill fill, int n, int k, float alpha, const float
     pb.mt = pb.nt = p.mt;
     pb.sym = 1;
     pb.chunk_kt = tune_chunk_kt();
+    pb.tf32 = is_tf32(prec);
     apply_split(pb, p.split);
     pb.epi = e;
     return umma_contract(pb, P, st);
@@ -779,12 +785,13 @@ ln_status run_batch(bool two, ln_fill fill, int count, const ln_sym_desc *h, con
         if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "batch too large");
         return simt_sym_batched(two, count, d, bp.tile_prefix, (int)tiles, fill, alpha, beta, st);
     }
-    const int P = prec_terms(prec);
+    const int P = prec_terms(prec), tf = is_tf32(prec) ? 1 : 0;
     LN_TRY(sym_batched_plan(two, count, d, fill, alpha, beta, bp.probs, bp.tile_prefix, bp.tile_owner, bp.pack_off,
-                            bp.pack_prefix, bp.order, bp.pack, P, st));
+                            bp.pack_prefix, bp.order, bp.pack, P, tf, st));
     LN_TRY(sym_batched_pack(two, count, d, bp.pack_off, bp.pack_prefix, bp.order, (int)bp.total_pack_tiles, bp.pack,
-                            P, st));
-    return umma_contract_batched(bp.probs, bp.tile_prefix, bp.tile_owner, (int)bp.total_tiles, bp.queue, P, st);
+                            P, tf, st));
+    return umma_contract_batched(bp.probs, bp.tile_prefix, bp.tile_owner, (int)bp.total_tiles, bp.queue,
+                                 mma_terms(prec), st);
 }
 
 // ------------------------------------------------------------------ backward
@@ -1183,6 +1190,7 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
     PackSrc ps[3] = {{A, nk, 0, ni, nk, nullptr, nullptr, p.pa, p.g1.mt, p.g1.kt},
                      {B, nj, 1, nj, nk, nullptr, nullptr, p.pb, p.g1.yrt, p.g1.kt},
                      {C, nl, 1, nl, nj, nullptr, nullptr, p.pc, p.g2.yrt, p.g2.kt}};
+    for (PackSrc &q : ps) q.tf32 = is_tf32(prec);
     // C is packed by the first contraction's spare CTAs when it has fewer
     // output tiles than SMs (and no stream-K, which gives every SM mainloop
     // work), else here with A and B
@@ -1200,6 +1208,7 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
     g1.mt = p.g1.mt;
     g1.nt = p.g1.nt;
     g1.chunk_kt = tune_chunk_kt();
+    g1.tf32 = is_tf32(prec);
     g1.inject_timeout = inject_timeout_requested();
     g1.epi.mode = EPI_PACK;
     g1.epi.M = ni;
@@ -1220,6 +1229,7 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
     g2.mt = p.g2.mt;
     g2.nt = p.g2.nt;
     g2.chunk_kt = tune_chunk_kt();
+    g2.tf32 = is_tf32(prec);
     g2.inject_timeout = g1.inject_timeout;
     apply_split(g2, p.s2);
     g2.bn = p.g2.bn;
@@ -1282,6 +1292,7 @@ ln_status ln_3mm(int ni, int nj, int nk, int nl, int nm, const float *A, const f
                      {B, nj, 1, nj, nk, nullptr, nullptr, p.pb, p.gE.yrt, p.gE.kt},
                      {D, nl, 1, nl, nm, nullptr, nullptr, p.pd, p.gF.mt, p.gF.kt},
                      {C, nm, 0, nj, nm, nullptr, nullptr, p.pc, p.gF.yrt, p.gF.kt}};
+    for (PackSrc &q : ps) q.tf32 = is_tf32(prec);
     PackMulti side;
     const bool try_side = p.gE.bn == 256 && !p.sE.streamk && make_pack_multi(ps + 2, 2, side) &&
                           pack_stream_eligible(side);
@@ -1297,6 +1308,7 @@ ln_status ln_3mm(int ni, int nj, int nk, int nl, int nm, const float *A, const f
     gE.mt = p.gE.mt;
     gE.nt = p.gE.nt;
     gE.chunk_kt = tune_chunk_kt();
+    gE.tf32 = is_tf32(prec);
     gE.inject_timeout = inject_timeout_requested();
     apply_split(gE, p.sE);
     gE.bn = p.gE.bn;
@@ -1313,6 +1325,7 @@ ln_status ln_3mm(int ni, int nj, int nk, int nl, int nm, const float *A, const f
     gF.mt = p.gF.mt;
     gF.nt = p.gF.nt;
     gF.chunk_kt = tune_chunk_kt();
+    gF.tf32 = is_tf32(prec);
     gF.inject_timeout = gE.inject_timeout;
     apply_split(gF, p.sF);
     gF.bn = p.gF.bn;
@@ -1354,6 +1367,7 @@ ln_status ln_3mm(int ni, int nj, int nk, int nl, int nm, const float *A, const f
     gG.mt = p.gG.mt;
     gG.nt = p.gG.nt;
     gG.chunk_kt = tune_chunk_kt();
+    gG.tf32 = is_tf32(prec);
     gG.inject_timeout = gE.inject_timeout;
     apply_split(gG, p.sG);
     gG.bn = p.gG.bn;

@@ -88,6 +88,12 @@ struct EpiParams {
 //   chunk position c ^ (r % 8) of that row (128 bytes per row).
 // Rows >= rows and k >= K are zero. Because the layout in global memory is the
 // layout in shared memory, one bulk copy moves a tile (no tensor map needed).
+// TF32 operands (PackSrc::tf32) keep the same 128 x 64 blocks, each holding two
+// 32-K tiles of T TF32 terms (P = 2T 16 KiB pieces per block): piece h * T +
+// term of block (rt, kt) is 32-K tile 2 kt + h, element (r, k) in 16-byte chunk
+// (k mod 32) / 4 of row r at chunk position c ^ (r % 8). So the tiles of a
+// TF32 operand are, in order, exactly those of a BF16 operand with 32-K tiles:
+// tile (rt, j, term) at ((rt * 2KT + j) * T + term) * 16384.
 constexpr int PK_ROWS = 128;
 constexpr int PK_K = 64;
 constexpr int PK_TILE_BYTES = PK_ROWS * PK_K * 2;
@@ -95,14 +101,21 @@ constexpr int PK_TILE_BYTES = PK_ROWS * PK_K * 2;
 inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// 16 KiB pieces per 128 x 64 block of a packed operand (BF16: the split terms;
+// TF32: twice the terms, the block holding two 32-K tiles)
 inline int prec_terms(ln_precision p) {
     switch (p) {
         case LN_PREC_BF16: return 1;
         case LN_PREC_3XBF16: return 2;
         case LN_PREC_6XBF16: return 3;
+        case LN_PREC_TF32: return 2;
+        case LN_PREC_3XTF32: return 4;
         default: return 0;
     }
 }
+inline bool is_tf32(ln_precision p) { return p == LN_PREC_TF32 || p == LN_PREC_3XTF32; }
+// split terms the tensor-core products take (the kernel's P)
+inline int mma_terms(ln_precision p) { return is_tf32(p) ? prec_terms(p) / 2 : prec_terms(p); }
 
 // bytes of a packed operand with `rt` row tiles and `kt` k tiles
 inline size_t packed_bytes(long long rt, long long kt, int terms) {
@@ -117,6 +130,7 @@ struct PackSrc {
     const float *off_hi, *off_lo;  // optional per-row centring, v = (x - hi) - lo
     char *dst;       // packed destination
     int rt, kt;      // tile counts of the destination (>= ceil(rows/128), ceil(K/64))
+    int tf32;        // TF32 terms (the TF32 block layout above) instead of BF16
 };
 
 // Up to four operands packed by one launch: a flat tile index space, operand i
@@ -231,10 +245,17 @@ struct UmmaProblem {
     // same column tile) with tcgen05.mma.cta_group::2: the leader issues M = 256
     // MMAs, each CTA holds its own 128 rows of A and half of the column tile's
     // B, so each SM stages and reads half as much of B.
-    int pair;
+    short pair;
     // the "stage_beta" knob: a CTA's last 256-wide tile may stage its block of
     // the beta input (D or C) in the stage memory after the mainloop
-    int stage_beta;
+    short stage_beta;
+    // TF32 operands: tcgen05.mma kind::tf32, 32-K tiles. The host sets it with
+    // k-tile counts in 64-K blocks; umma_contract doubles them (and halves the
+    // term count) before the launch. A packing epilogue writes TF32 blocks.
+    // (pair and stage_beta are short so that the problem keeps the size and
+    // layout the epilogue registers were tuned with: a larger struct moved
+    // registers into spills in the E/F epilogue)
+    int tf32;
     EpiParams epi;
 };
 // True when LN_FAULT_INJECT=timeout is set in the environment (read per call).
@@ -277,7 +298,8 @@ ln_status umma_contract_pair(int ek, const UmmaProblem &p, int terms, int bn, in
                              const PackMulti *side, bool *side_done);
 ln_status umma_contract_sym_pair(const UmmaProblem &p, int terms, int total, cudaStream_t st);
 ln_status umma_read_error_pair(int *value);
-// d_tile_owner[t] = the problem (in d_probs order) that tile t belongs to.
+// d_tile_owner[t] = the problem (in d_probs order) that tile t belongs to;
+// terms = the split terms of the products (mma_terms).
 ln_status umma_contract_batched(const UmmaProblem *d_probs, const int *d_tile_prefix, const int *d_tile_owner,
                                 int total_tiles, int *d_queue, int terms, cudaStream_t st);
 ln_status umma_read_error(int *value);
@@ -286,12 +308,14 @@ ln_status umma_read_error(int *value);
 // work, assigns each its packed-operand offsets, and writes its contraction
 // descriptor and tile prefix sums (rank order); the pack kernel then packs
 // every instance's operands in one launch.
+// terms: 16 KiB pieces per packed block (prec_terms); tf32: TF32 operands
+// (the plan then writes problems with 32-K tile counts and the tf32 flag)
 ln_status sym_batched_plan(int is_syr2k, int count, const ln_sym_desc *d_descs, int fill, float alpha, float beta,
                            UmmaProblem *d_probs, int *d_tile_prefix, int *d_tile_owner, long long *d_pack_off,
-                           int *d_pack_prefix, int *d_order, char *pack_base, int terms, cudaStream_t st);
+                           int *d_pack_prefix, int *d_order, char *pack_base, int terms, int tf32, cudaStream_t st);
 ln_status sym_batched_pack(int is_syr2k, int count, const ln_sym_desc *d_descs, const long long *d_pack_off,
                            const int *d_pack_prefix, const int *d_order, int total_pack_tiles, char *pack_base,
-                           int terms, cudaStream_t st);
+                           int terms, int tf32, cudaStream_t st);
 ln_status plain_sym_batched(int is_syr2k, int count, const ln_sym_desc *d_descs, int max_n, int fill, float alpha,
                             float beta, cudaStream_t st);
 ln_status simt_sym_batched(int is_syr2k, int count, const ln_sym_desc *d_descs, const int *d_tile_prefix,

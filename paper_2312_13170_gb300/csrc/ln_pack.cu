@@ -58,7 +58,7 @@ __device__ __forceinline__ void pack_tile(const PackSrc &p, int kt, int rt, floa
                 for (int q = 0; q < 8; ++q)
                     if (gk + q < p.K) v[pass][q] = (v[pass][q] - h) - l;
             }
-            store_chunk<P>(tile0, r, c, v[pass]);
+            store_chunk_any<P>(tile0, r, c, v[pass], p.tf32);
         }
     } else {
         // element (r, k) = S[k*ld + r]: stage the 64 x 128 block through shared
@@ -115,7 +115,7 @@ __device__ __forceinline__ void pack_tile(const PackSrc &p, int kt, int rt, floa
             float v[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) v[q] = s[c * 8 + q][r];
-            store_chunk<P>(tile0, r, c, v);
+            store_chunk_any<P>(tile0, r, c, v, p.tf32);
         }
     }
 }
@@ -161,7 +161,7 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_batch_plan(int is_syr2k, int c
                                                              int fill, float alpha, float beta, UmmaProblem *probs,
                                                              int *tile_prefix, int *tile_owner, long long *pack_off,
                                                              int *pack_prefix, char *pack_base, int terms,
-                                                             int chunk_kt_for_kernel) {
+                                                             int chunk_kt_for_kernel, int tf32) {
     __shared__ float w[RANK_MAX];
     __shared__ long long sb[PLAN_THREADS];
     __shared__ int st[PLAN_THREADS], sp[PLAN_THREADS];
@@ -219,11 +219,12 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_batch_plan(int is_syr2k, int c
         const int kt = (d.k + PK_K - 1) / PK_K;
         const long long one = (long long)mt * kt * terms * PK_TILE_BYTES;
         UmmaProblem p{};
-        p.kt = kt;
-        p.x_kt = p.y_kt = kt;
+        p.kt = tf32 ? 2 * kt : kt;  // the kernel's k tiles: 32-K tiles for TF32
+        p.x_kt = p.y_kt = p.kt;
         p.mt = p.nt = mt;
         p.sym = 1;
         p.chunk_kt = chunk_kt_for_kernel;
+        p.tf32 = tf32;
         const char *pa = pack_base + off_b;
         const char *pb = is_syr2k ? pa + one : pa;
         pack_off[2 * r] = off_b;
@@ -269,7 +270,7 @@ template <int P>
 __global__ __launch_bounds__(256) void k_pack_batched(int is_syr2k, int count, const ln_sym_desc *__restrict__ descs,
                                                       const long long *__restrict__ pack_off,
                                                       const int *__restrict__ pack_prefix,
-                                                      const int *__restrict__ order, char *pack_base) {
+                                                      const int *__restrict__ order, char *pack_base, int tf32) {
     __shared__ float s[1][PK_ROWS + 1];
     const int t = blockIdx.x;
     int lo = 0, hi = count - 1;
@@ -295,6 +296,7 @@ __global__ __launch_bounds__(256) void k_pack_batched(int is_syr2k, int count, c
     p.dst = pack_base + pack_off[2 * lo + operand];
     p.rt = mt;
     p.kt = kt;
+    p.tf32 = tf32;
     pack_tile<0, P>(p, rem % kt, rem / kt, s);
 }
 
@@ -314,9 +316,11 @@ ln_status pack_operand(const PackSrc &p, int terms, cudaStream_t st) {
     LN_PACK_CASE(0, 1);
     else LN_PACK_CASE(0, 2);
     else LN_PACK_CASE(0, 3);
+    else LN_PACK_CASE(0, 4);
     else LN_PACK_CASE(1, 1);
     else LN_PACK_CASE(1, 2);
     else LN_PACK_CASE(1, 3);
+    else LN_PACK_CASE(1, 4);
     else return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
 #undef LN_PACK_CASE
     return check_launch("split-and-pack");
@@ -351,11 +355,12 @@ bool pack_stream_eligible(const PackMulti &m) {
 namespace {
 
 // 4 input stages and 3 output buffers where they fit in 227 KiB (1 and 2
-// terms), else 3 and 2
+// pieces per block), else 3 and 2
 constexpr int stream_stages(int terms) { return terms >= 3 ? 3 : PS_MAX_STAGES; }
 constexpr int stream_outs(int terms) { return terms >= 3 ? 2 : 3; }
 static_assert(pack_stream_smem(stream_stages(2), stream_outs(2), 2) <= 227 * 1024, "pack stream smem");
 static_assert(pack_stream_smem(stream_stages(3), stream_outs(3), 3) <= 227 * 1024, "pack stream smem");
+static_assert(pack_stream_smem(stream_stages(4), stream_outs(4), 4) <= 227 * 1024, "pack stream smem");
 
 template <int P, int NT>
 ln_status launch_pack_stream(const PackMulti &m, cudaStream_t st) {
@@ -406,6 +411,7 @@ ln_status pack_operands(const PackSrc *ps, int count, int terms, cudaStream_t st
             case 1: return launch_pack_stream<1>(m, st);
             case 2: return launch_pack_stream<2>(m, st);
             case 3: return launch_pack_stream<3>(m, st);
+            case 4: return launch_pack_stream<4>(m, st);
             default: return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
         }
     }
@@ -414,6 +420,7 @@ ln_status pack_operands(const PackSrc *ps, int count, int terms, cudaStream_t st
         case 1: k_pack_multi<1><<<(unsigned)tiles, 256, 0, st>>>(m); break;
         case 2: k_pack_multi<2><<<(unsigned)tiles, 256, 0, st>>>(m); break;
         case 3: k_pack_multi<3><<<(unsigned)tiles, 256, 0, st>>>(m); break;
+        case 4: k_pack_multi<4><<<(unsigned)tiles, 256, 0, st>>>(m); break;
         default: return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
     }
     return check_launch("split-and-pack (multi)");
@@ -421,33 +428,33 @@ ln_status pack_operands(const PackSrc *ps, int count, int terms, cudaStream_t st
 
 ln_status sym_batched_plan(int is_syr2k, int count, const ln_sym_desc *d_descs, int fill, float alpha, float beta,
                            UmmaProblem *d_probs, int *d_tile_prefix, int *d_tile_owner, long long *d_pack_off,
-                           int *d_pack_prefix, int *d_order, char *pack_base, int terms, cudaStream_t st) {
+                           int *d_pack_prefix, int *d_order, char *pack_base, int terms, int tf32,
+                           cudaStream_t st) {
     LaunchScope ls_(FAM_PACK, st);
     k_batch_plan<<<1, PLAN_THREADS, 0, st>>>(is_syr2k, count, d_descs, d_order, fill, alpha, beta, d_probs,
                                              d_tile_prefix, d_tile_owner, d_pack_off, d_pack_prefix, pack_base, terms,
-                                             tune_chunk_kt());
+                                             tune_chunk_kt(), tf32);
     return check_launch("batched plan");
 }
 
 ln_status sym_batched_pack(int is_syr2k, int count, const ln_sym_desc *d_descs, const long long *d_pack_off,
                            const int *d_pack_prefix, const int *d_order, int total_pack_tiles, char *pack_base,
-                           int terms, cudaStream_t st) {
+                           int terms, int tf32, cudaStream_t st) {
     if (total_pack_tiles == 0) return LN_SUCCESS;
-    switch (terms) {
-        case 1:
-            { LaunchScope ls_(FAM_PACK, st); k_pack_batched<1><<<total_pack_tiles, 256, 0, st>>>(is_syr2k, count, d_descs, d_pack_off, d_pack_prefix,
-                                                                d_order, pack_base); }
-            break;
-        case 2:
-            { LaunchScope ls_(FAM_PACK, st); k_pack_batched<2><<<total_pack_tiles, 256, 0, st>>>(is_syr2k, count, d_descs, d_pack_off, d_pack_prefix,
-                                                                d_order, pack_base); }
-            break;
-        case 3:
-            { LaunchScope ls_(FAM_PACK, st); k_pack_batched<3><<<total_pack_tiles, 256, 0, st>>>(is_syr2k, count, d_descs, d_pack_off, d_pack_prefix,
-                                                                d_order, pack_base); }
-            break;
-        default: return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
+    if (terms < 1 || terms > 4) return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
+#define LN_PACK_BATCHED(P)                                                                                   \
+    k_pack_batched<P><<<total_pack_tiles, 256, 0, st>>>(is_syr2k, count, d_descs, d_pack_off, d_pack_prefix, \
+                                                        d_order, pack_base, tf32)
+    {
+        LaunchScope ls_(FAM_PACK, st);
+        switch (terms) {
+            case 1: LN_PACK_BATCHED(1); break;
+            case 2: LN_PACK_BATCHED(2); break;
+            case 3: LN_PACK_BATCHED(3); break;
+            default: LN_PACK_BATCHED(4); break;
+        }
     }
+#undef LN_PACK_BATCHED
     return check_launch("batched split-and-pack");
 }
 

@@ -133,7 +133,7 @@ __device__ __forceinline__ void ps_split(const PsTile &tl, const float *stage, c
                 for (int q = 0; q < 8; ++q)
                     if (c * 8 + q < tl.nk) v[q] = (v[q] - h) - l;
             }
-            store_chunk<P>(out, r, c, v);
+            store_chunk_any<P>(out, r, c, v, p.tf32);
         }
     } else {
         // warp w builds chunk c = w % 8 of 32 consecutive rows per pass: each
@@ -151,7 +151,7 @@ __device__ __forceinline__ void ps_split(const PsTile &tl, const float *stage, c
                 for (int q = 0; q < 8; ++q)
                     if (c * 8 + q < tl.nk) v[q] = (v[q] - h) - l;
             }
-            store_chunk<P>(out, r, c, v);
+            store_chunk_any<P>(out, r, c, v, p.tf32);
         }
     }
 }

@@ -30,7 +30,7 @@ int epi_kind(const EpiParams &e) {
 }  // namespace
 
 int umma_tile_n(int terms, int sym, long long M, long long N) {
-    if (sym || terms > 2) return 128;
+    if (sym || terms == 3) return 128;  // terms: BF16 split terms, or pieces per TF32 block (2, 4)
     const int knob = tune_tile_n();
     if (knob == 128 || knob == 256) return knob;
     const long long wide_tiles = ceil_div(M, 128) * ceil_div(N, 256);
@@ -75,6 +75,18 @@ ln_status umma_contract(const UmmaProblem &p0, int terms, cudaStream_t st, const
     UmmaProblem p = p0;
     p.pair = 0;
     p.stage_beta = tune_stage_beta();
+    if (p.tf32) {
+        // TF32 operands: `terms` counts the 16 KiB pieces of a 128 x 64 block
+        // (two per TF32 term) and the k-tile counts are in such blocks; the
+        // kernel takes the TF32 terms and 32-K tiles. The spare CTAs' pack
+        // stream writes BF16 blocks only, so the caller packs a side operand.
+        if (terms != 2 && terms != 4) return fail(LN_ERR_INVALID_VALUE, "TF32 operand with %d pieces", terms);
+        terms /= 2;
+        p.kt *= 2;
+        p.x_kt *= 2;
+        p.y_kt *= 2;
+        side = nullptr;
+    }
     long long tiles = p.sym ? (long long)p.mt * (p.mt + 1) / 2 : (long long)p.mt * p.nt;
     if (tiles == 0) return LN_SUCCESS;
     if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many output tiles");

@@ -214,6 +214,36 @@ __device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t a, uint
         "l"(a), "l"(b), "r"(idesc_bf16(BN, 2 * BM)), "r"(acc)
         : "memory");
 }
+// TF32 operands (kind::tf32, K = 8 per instruction: the same 32 bytes of each
+// 128-byte row as a BF16 K = 16 step, so the descriptors advance alike). The
+// instruction descriptor differs from the BF16 one only in the A and B format
+// fields (TF32 = 2). The MMA of either kind is one predicated pair of
+// instructions, so the issue loop has no branch on the operand type.
+__host__ __device__ constexpr uint32_t idesc_tf32(int n, int m = BM) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+template <int BN>
+__device__ __forceinline__ void umma_any(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc, uint32_t tf32) {
+    asm volatile(
+        "{\n\t.reg .pred p, t;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "setp.ne.b32 t, %5, 0;\n\t"
+        "@t tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %6, p;\n\t"
+        "@!t tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc_bf16(BN)), "r"(acc), "r"(tf32), "r"(idesc_tf32(BN))
+        : "memory");
+}
+template <int BN>
+__device__ __forceinline__ void umma_any_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc, uint32_t tf32) {
+    asm volatile(
+        "{\n\t.reg .pred p, t;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "setp.ne.b32 t, %5, 0;\n\t"
+        "@t tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %6, p;\n\t"
+        "@!t tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc_bf16(BN, 2 * BM)), "r"(acc), "r"(tf32), "r"(idesc_tf32(BN, 2 * BM))
+        : "memory");
+}
 // completion of the pair's MMAs, signalled on the mbarrier at bar's offset in both CTAs
 __device__ __forceinline__ void umma_commit_pair_mc(uint64_t *bar) {
     asm volatile(
@@ -890,6 +920,7 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>(), PAIR>::NTHREADS, 1) voi
                 const UmmaProblem &pb = sl.prob;
                 const int qa = sl.qa, qb = sl.qb;
                 const int ck = pb.chunk_kt > 0 ? pb.chunk_kt : (qb - qa > 0 ? qb - qa : 1);
+                const uint32_t tf32 = pb.tf32 ? 1u : 0u;
                 bool ok = true;
                 if (pair && rank != 0) {
                     // the peer of a pair issues no MMA: it tells the leader when each
@@ -934,13 +965,14 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>(), PAIR>::NTHREADS, 1) voi
 #pragma unroll
                             for (int ks = 0; ks < PK_K / 16; ++ks) {
                                 const uint64_t ad = sw128_desc(a0 + PR::a(pr) * PK_TILE_BYTES + ks * 32);
+                                const uint32_t acc_in = ((q - q0) | pr | ks) ? 1u : 0u;
                                 if constexpr (pair) {
                                     const uint64_t bd = sw128_desc(b0 + PR::b(pr) * C::BH_BYTES + ks * 32);
-                                    umma_bf16_pair<BN>(d, ad, bd, ((q - q0) | pr | ks) ? 1u : 0u);
+                                    umma_any_pair<BN>(d, ad, bd, acc_in, tf32);
                                 } else {
                                     const uint64_t bd =
                                         sw128_desc(b0 + PR::b(pr) * C::HALVES * PK_TILE_BYTES + ks * 32);
-                                    umma_bf16<BN>(d, ad, bd, ((q - q0) | pr | ks) ? 1u : 0u);
+                                    umma_any<BN>(d, ad, bd, acc_in, tf32);
                                 }
                             }
                         }
@@ -1183,11 +1215,18 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>(), PAIR>::NTHREADS, 1) voi
                 // row rloc of M tile mi; column j of the result is k = j of the packed operand
 #pragma unroll
                 for (int g = 0; g < EPW / 32; ++g) {
-                    const int kt = (col0 + g * 32) / PK_K;
-                    char *tile0 = e.pack + (size_t)((long long)tr.mi * e.pack_kt + kt) * P * PK_TILE_BYTES;
+                    const int kt = (col0 + g * 32) / PK_K;  // 128 x 64 block of the packed operand
+                    if (pb.tf32) {  // blocks of 2P pieces: P TF32 terms of two 32-K tiles
+                        char *blk = e.pack + (size_t)((long long)tr.mi * e.pack_kt + kt) * 2 * P * PK_TILE_BYTES;
 #pragma unroll
-                    for (int cc = 0; cc < 4; ++cc)
-                        store_chunk<P>(tile0, rloc, (g & 1) * 4 + cc, &sum[g * 32 + cc * 8]);
+                        for (int cc = 0; cc < 4; ++cc)
+                            store_chunk_tf32<P>(blk, rloc, (g & 1) * 4 + cc, &sum[g * 32 + cc * 8]);
+                    } else {
+                        char *tile0 = e.pack + (size_t)((long long)tr.mi * e.pack_kt + kt) * P * PK_TILE_BYTES;
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc)
+                            store_chunk<P>(tile0, rloc, (g & 1) * 4 + cc, &sum[g * 32 + cc * 8]);
+                    }
                 }
             } else if ((EK == EK_EF || EK == EK_GEMM) && sl.dsmem) {
                 // the beta input of this tile arrives in the stage memory (dfull):

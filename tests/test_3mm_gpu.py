@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 GATE = 1e-5
 MODES = [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "bf16"), ("internalized", "3xbf16"),
-         ("internalized", "6xbf16")]
+         ("internalized", "6xbf16"), ("internalized", "tf32"), ("internalized", "3xtf32")]
 
 
 @pytest.fixture(scope="module")
@@ -52,12 +52,12 @@ def test_3mm(api, form, prec, ni, nj, nk, nl, nm):
     ref = oracle.three_mm(A, B, C, D)
     G = api.three_mm(dev(A), dev(B), dev(C), dev(D), form=form, prec=prec)
     api.stream_check()
-    assert inputs.rel_fro(host(G), ref) <= (3e-2 if prec == "bf16" else GATE)
+    assert inputs.rel_fro(host(G), ref) <= (3e-2 if prec in ("bf16", "tf32") else GATE)
 
 
-@pytest.mark.parametrize("form,prec", [m for m in MODES if m[1] != "bf16"])
+@pytest.mark.parametrize("form,prec", [m for m in MODES if m[1] not in ("bf16", "tf32")])
 def test_3mm_integer_bitexact(api, form, prec):
-    # |E|, |F| <= 15 * 16 < 256 (one BF16 term), |G| <= 200 * 240^2 < 2^24
+    # |E|, |F| <= 15 * 16 < 256 (one BF16 term, one TF32 term), |G| <= 200 * 240^2 < 2^24
     ni, nj, nk, nl, nm = 150, 200, 15, 130, 15
     A, B, C, D = (inputs.int_matrix(s, seed=90 + i) for i, s in enumerate([(ni, nk), (nk, nj), (nj, nm), (nm, nl)]))
     ref = oracle.three_mm(A, B, C, D)
@@ -81,7 +81,7 @@ def test_3mm_empty_inner_and_host_operands(api):
 
 
 @pytest.mark.parametrize("form,prec", [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16"),
-                                       ("internalized", "6xbf16")])
+                                       ("internalized", "6xbf16"), ("internalized", "3xtf32")])
 @pytest.mark.parametrize("ni,nj,nk,nl,nm", [(70, 129, 65, 90, 33), (1024, 1024, 1024, 1024, 1024)])
 def test_3mm_bwd(api, form, prec, ni, nj, nk, nl, nm):
     if form == "plain" and ni > 512:

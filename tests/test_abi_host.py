@@ -67,8 +67,11 @@ def test_gemm_validation(L):
     # C overlapping A -> aliasing (the alias contract of the transformation)
     s = L.ln_gemm(64, 64, 64, 1.0, P(FAKE_A), 64, P(FAKE_B), 64, 0.0, P(FAKE_A + 256), 64, None, 0, 0, 0, None)
     assert s == 2 and "overlap" in last(L)
-    # plain form supports only FP32
+    # plain form supports only FP32 (the TF32 modes too are tensor-core only)
     assert L.ln_gemm(4, 4, 4, 1.0, P(FAKE_A), 4, P(FAKE_B), 4, 0.0, P(FAKE_C), 4, None, 0, 0, 2, None) == 4
+    assert L.ln_gemm(4, 4, 4, 1.0, P(FAKE_A), 4, P(FAKE_B), 4, 0.0, P(FAKE_C), 4, None, 0, 0, 5, None) == 4
+    # precision codes end at LN_PREC_3XTF32 = 5
+    assert L.ln_gemm(4, 4, 4, 1.0, P(FAKE_A), 4, P(FAKE_B), 4, 0.0, P(FAKE_C), 4, None, 0, 1, 6, None) == 1
     # unknown enum
     assert L.ln_gemm(4, 4, 4, 1.0, P(FAKE_A), 4, P(FAKE_B), 4, 0.0, P(FAKE_C), 4, None, 0, 7, 0, None) == 1
     # tensor-core path without a workspace
@@ -109,6 +112,9 @@ def _workspace_queries_256(L):
     assert n.value == 4 * 2048 * 2048
     assert L.ln_covariance_workspace_size(8192, 2048, 1, 2, ctypes.byref(n)) == 0 and n.value > 0
     assert L.ln_syr2k_workspace_size(100, 50, 1, 2, ctypes.byref(n)) == 0 and n.value == 2 * 2 * 16384
+    # TF32 terms take 4 bytes: one TF32 term packs into as many bytes as two BF16 terms
+    assert L.ln_syr2k_workspace_size(100, 50, 1, 4, ctypes.byref(n)) == 0 and n.value == 2 * 2 * 16384
+    assert L.ln_syr2k_workspace_size(100, 50, 1, 5, ctypes.byref(n)) == 0 and n.value == 2 * 4 * 16384
 
 
 def test_sym_validation(L):

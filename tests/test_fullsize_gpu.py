@@ -40,7 +40,8 @@ def host(t):
 ROWS = np.random.default_rng(123).choice(2048, size=12, replace=False)
 
 
-@pytest.mark.parametrize("form,prec", [("internalized", "3xbf16"), ("internalized", "fp32"), ("plain", "fp32")])
+@pytest.mark.parametrize("form,prec", [("internalized", "3xbf16"), ("internalized", "3xtf32"), ("internalized", "fp32"),
+                                       ("plain", "fp32")])
 def test_chain_2048(api, form, prec):
     d = inputs.chain_inputs(2048, seed=0)
     E, F = api.gemm_chain(dev(d["A"]), dev(d["B"]), dev(d["C"]), dev(d["D"]), d["alpha"], d["beta"],
@@ -52,7 +53,7 @@ def test_chain_2048(api, form, prec):
     assert inputs.rel_fro(host(F)[ROWS], F_ref) <= GATE
 
 
-@pytest.mark.parametrize("form,prec", [("internalized", "3xbf16"), ("internalized", "fp32")])
+@pytest.mark.parametrize("form,prec", [("internalized", "3xbf16"), ("internalized", "3xtf32"), ("internalized", "fp32")])
 def test_cov_corr_8192x2048(api, form, prec):
     X = inputs.cov_inputs(8192, 2048, seed=0)["X"]
     Xd = dev(X)

@@ -1,9 +1,9 @@
 """GPU parity: every kernel, form and precision against the FP64 oracle.
 
 Gate (the relative Frobenius error of each output tensor against the exact
-FP64 result): 1e-5 for FP32 (plain and tiled) and for the 3xBF16 / 6xBF16
-split tensor-core modes; single-pass BF16 is reported against a loose sanity
-bound only. Integer-valued inputs must match bit for bit in every mode that
+FP64 result): 1e-5 for FP32 (plain and tiled) and for the 3xBF16 / 6xBF16 /
+3xTF32 split tensor-core modes; single-pass BF16 and TF32 are checked against a
+loose sanity bound only. Integer-valued inputs must match bit for bit in every mode that
 represents them exactly. Sizes span several tiles and ragged tails.
 """
 import numpy as np
@@ -18,12 +18,15 @@ pytestmark = pytest.mark.gpu
 GATE = 1e-5
 BF16_SANITY = 3e-2
 MODES = [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "bf16"),
-         ("internalized", "3xbf16"), ("internalized", "6xbf16")]
-EXACT_MODES = [m for m in MODES if m[1] != "bf16"]
+         ("internalized", "3xbf16"), ("internalized", "6xbf16"), ("internalized", "tf32"),
+         ("internalized", "3xtf32")]
+LOOSE = ("bf16", "tf32")  # single-pass modes: a sanity bound, not the gate
+EXACT_MODES = [m for m in MODES if m[1] not in LOOSE]
+SINGLE_PASS = [("internalized", "bf16"), ("internalized", "tf32")]
 
 
 def tol(prec):
-    return BF16_SANITY if prec == "bf16" else GATE
+    return BF16_SANITY if prec in LOOSE else GATE
 
 
 @pytest.fixture(scope="module")
@@ -59,7 +62,23 @@ def test_gemm(api, form, prec, M, N, K):
     assert inputs.rel_fro(host(C), ref) <= tol(prec)
 
 
-@pytest.mark.parametrize("form,prec", EXACT_MODES + [("internalized", "bf16")])
+def test_tf32_modes_are_tf32(api):
+    """The TF32 modes round to TF32, not to BF16 or FP32: single-pass TF32's
+    error sits between FP32's and BF16's, 3xTF32's below 3xBF16's."""
+    d = inputs.gemm_inputs(512, 384, 640, seed=12)
+    ref = oracle.gemm(d["A"], d["B"], d["C"], d["alpha"], d["beta"])
+    err = {}
+    for prec in ("bf16", "tf32", "3xbf16", "3xtf32", "fp32"):
+        C = dev(d["C"])
+        api.gemm(dev(d["A"]), dev(d["B"]), C, d["alpha"], d["beta"], prec=prec)
+        err[prec] = inputs.rel_fro(host(C), ref)
+    api.stream_check()
+    assert err["fp32"] < err["tf32"] < err["bf16"] / 4, err
+    assert err["3xtf32"] < err["3xbf16"] / 4 and err["3xtf32"] <= GATE, err
+    assert 2e-5 < err["tf32"] < 3e-3, err
+
+
+@pytest.mark.parametrize("form,prec", EXACT_MODES + SINGLE_PASS)
 def test_gemm_integer_bitexact(api, form, prec):
     M, N, K = 150, 190, 300
     A, B, C = (inputs.int_matrix(s, seed=i) for i, s in enumerate([(M, K), (K, N), (M, N)]))
@@ -69,7 +88,8 @@ def test_gemm_integer_bitexact(api, form, prec):
     assert np.array_equal(host(Ct).astype(np.float64), ref)
 
 
-@pytest.mark.parametrize("form,prec", [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16")])
+@pytest.mark.parametrize("form,prec", [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16"),
+                                       ("internalized", "3xtf32")])
 def test_gemm_edge_cases(api, form, prec):
     # K == 0: C = beta * C
     C = dev(inputs.gemm_inputs(5, 6, 1)["C"])
@@ -149,7 +169,7 @@ def test_covariance_correlation(api, form, prec, n, m):
     assert inputs.rel_fro(r, corr_ref) <= tol(prec)
     assert np.array_equal(c, c.T) and np.array_equal(r, r.T)
     assert np.all(np.diag(r) == 1.0)
-    if prec != "bf16":
+    if prec not in LOOSE:
         s = np.sqrt(np.diag(cov_ref))
         # error scaled by the columns' spreads: small-variance columns are checked too
         assert np.max(np.abs(c - cov_ref) / np.outer(s, s)) < 5e-5
@@ -166,7 +186,8 @@ def test_covariance_integer_bitexact(api, form, prec):
     assert np.array_equal(got, ref)
 
 
-@pytest.mark.parametrize("form,prec", [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16")])
+@pytest.mark.parametrize("form,prec", [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16"),
+                                       ("internalized", "3xtf32")])
 def test_correlation_zero_variance_column(api, form, prec):
     X = inputs.cov_inputs(100, 6, seed=9)["X"]
     X[:, 2] = 42.0
@@ -196,7 +217,7 @@ def test_syrk_syr2k(api, form, prec, fill, n, k):
         assert np.array_equal(g1[iu], d["C"][iu]) and np.array_equal(g2[iu], d["C"][iu])
 
 
-@pytest.mark.parametrize("form,prec", EXACT_MODES + [("internalized", "bf16")])
+@pytest.mark.parametrize("form,prec", EXACT_MODES + SINGLE_PASS)
 def test_syrk_syr2k_integer_bitexact(api, form, prec):
     n, k = 140, 150
     A, B, C = inputs.int_matrix((n, k), seed=1), inputs.int_matrix((n, k), seed=2), inputs.int_matrix((n, n), seed=3)
@@ -228,7 +249,8 @@ def test_batched(api, form, prec, two):
         assert inputs.rel_fro(host(C), ref) <= tol(prec), (x["n"], x["k"])
 
 
-@pytest.mark.parametrize("form,prec", [("internalized", "fp32"), ("internalized", "3xbf16")])
+@pytest.mark.parametrize("form,prec", [("internalized", "fp32"), ("internalized", "3xbf16"),
+                                       ("internalized", "3xtf32")])
 def test_batched_single_instance_matches_unbatched(api, form, prec):
     d = inputs.sym_inputs(200, 90, seed=11)
     C1, C2 = dev(d["C"]), dev(d["C"])
@@ -266,7 +288,8 @@ def test_batched_graph_replay(api):
 
 
 # ------------------------------------------------------------------------ adjoints
-@pytest.mark.parametrize("form,prec", [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16")])
+@pytest.mark.parametrize("form,prec", [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16"),
+                                       ("internalized", "3xtf32")])
 def test_chain_bwd(api, form, prec):
     d = inputs.chain_inputs(96, 80, 112, 72, seed=2)
     G = inputs.gemm_inputs(96, 72, 1, seed=5)["C"]
@@ -276,7 +299,8 @@ def test_chain_bwd(api, form, prec):
         assert inputs.rel_fro(host(g), r) <= GATE
 
 
-@pytest.mark.parametrize("form,prec", [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16")])
+@pytest.mark.parametrize("form,prec", [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16"),
+                                       ("internalized", "3xtf32")])
 @pytest.mark.parametrize("corr", [False, True])
 def test_cov_corr_bwd(api, form, prec, corr):
     d = inputs.backward_inputs(300, 70, 8, seed=4)
@@ -290,7 +314,8 @@ def test_cov_corr_bwd(api, form, prec, corr):
     assert inputs.rel_fro(host(dX2), ref) <= GATE
 
 
-@pytest.mark.parametrize("form,prec", [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16")])
+@pytest.mark.parametrize("form,prec", [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16"),
+                                       ("internalized", "3xtf32")])
 @pytest.mark.parametrize("corr", [False, True])
 def test_cov_corr_fwd_keeps_stats(api, form, prec, corr):
     """ln_covariance_fwd / ln_correlation_fwd: the result bit for bit that of
