@@ -791,7 +791,7 @@ ln_status run_batch(bool two, ln_fill fill, int count, const ln_sym_desc *h, con
     LN_TRY(sym_batched_pack(two, count, d, bp.pack_off, bp.pack_prefix, bp.order, (int)bp.total_pack_tiles, bp.pack,
                             P, tf, st));
     return umma_contract_batched(bp.probs, bp.tile_prefix, bp.tile_owner, (int)bp.total_tiles, bp.queue,
-                                 mma_terms(prec), st);
+                                 mma_terms(prec), tf, st);
 }
 
 // ------------------------------------------------------------------ backward

@@ -299,9 +299,16 @@ ln_status umma_contract_pair(int ek, const UmmaProblem &p, int terms, int bn, in
 ln_status umma_contract_sym_pair(const UmmaProblem &p, int terms, int total, cudaStream_t st);
 ln_status umma_read_error_pair(int *value);
 // d_tile_owner[t] = the problem (in d_probs order) that tile t belongs to;
-// terms = the split terms of the products (mma_terms).
+// terms = the split terms of the products (mma_terms); tf32: TF32 operands.
 ln_status umma_contract_batched(const UmmaProblem *d_probs, const int *d_tile_prefix, const int *d_tile_owner,
-                                int total_tiles, int *d_queue, int terms, cudaStream_t st);
+                                int total_tiles, int *d_queue, int terms, int tf32, cudaStream_t st);
+// ln_umma_tf32.cu: the TF32 launches (problems already in 32-K tiles, `terms`
+// the TF32 term count)
+ln_status umma_contract_tf32(int ek, const UmmaProblem &p, int terms, int bn, int total, cudaStream_t st);
+ln_status umma_contract_sym_tf32(const UmmaProblem &p, int terms, int total, cudaStream_t st);
+ln_status umma_contract_batched_tf32(const UmmaProblem *d_probs, const int *d_tile_prefix, const int *d_tile_owner,
+                                     int total_tiles, int *d_queue, int terms, cudaStream_t st);
+ln_status umma_read_error_tf32(int *value);
 ln_status umma_read_error(int *value);
 // batched planning on the device
 // ln_pack.cu: batched layout. The plan kernel orders instances by decreasing

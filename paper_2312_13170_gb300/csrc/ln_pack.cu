@@ -19,7 +19,7 @@ namespace {
 // One 128-row x 64-k tile (all P terms) of the packed operand described by p.
 // `s` is a 64 x 129 shared-memory staging block used by the transposed case.
 // All global loads of a thread are issued before any split or store.
-template <int TRANS, int P>
+template <int TRANS, int P, bool TF = false>
 __device__ __forceinline__ void pack_tile(const PackSrc &p, int kt, int rt, float (*s)[PK_ROWS + 1]) {
     const int tid = threadIdx.x;
     const int r0 = rt * PK_ROWS, k0 = kt * PK_K;
@@ -58,7 +58,7 @@ __device__ __forceinline__ void pack_tile(const PackSrc &p, int kt, int rt, floa
                 for (int q = 0; q < 8; ++q)
                     if (gk + q < p.K) v[pass][q] = (v[pass][q] - h) - l;
             }
-            store_chunk_any<P>(tile0, r, c, v[pass], p.tf32);
+            store_chunk_fmt<P, TF>(tile0, r, c, v[pass]);
         }
     } else {
         // element (r, k) = S[k*ld + r]: stage the 64 x 128 block through shared
@@ -115,20 +115,21 @@ __device__ __forceinline__ void pack_tile(const PackSrc &p, int kt, int rt, floa
             float v[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) v[q] = s[c * 8 + q][r];
-            store_chunk_any<P>(tile0, r, c, v, p.tf32);
+            store_chunk_fmt<P, TF>(tile0, r, c, v);
         }
     }
 }
 
 // grid (kt, rt)
-template <int TRANS, int P>
+// TF: TF32 blocks (PackSrc::tf32); P is then even (two pieces per TF32 term)
+template <int TRANS, int P, bool TF>
 __global__ __launch_bounds__(256) void k_pack(PackSrc p) {
     __shared__ float s[TRANS ? PK_K : 1][PK_ROWS + 1];
-    pack_tile<TRANS, P>(p, blockIdx.x, blockIdx.y, s);
+    pack_tile<TRANS, P, TF>(p, blockIdx.x, blockIdx.y, s);
 }
 
 // Several operands in one launch: a flat grid over all their tiles.
-template <int P>
+template <int P, bool TF>
 __global__ __launch_bounds__(256) void k_pack_multi(const __grid_constant__ PackMulti m) {
     __shared__ float s[PK_K][PK_ROWS + 1];
     const int t = blockIdx.x;
@@ -136,15 +137,15 @@ __global__ __launch_bounds__(256) void k_pack_multi(const __grid_constant__ Pack
     while (i + 1 < m.count && m.prefix[i + 1] <= t) ++i;
     const PackSrc &p = m.op[i];
     const int local = t - m.prefix[i];
-    if (p.trans) pack_tile<1, P>(p, local % p.kt, local / p.kt, s);
-    else pack_tile<0, P>(p, local % p.kt, local / p.kt, s);
+    if (p.trans) pack_tile<1, P, TF>(p, local % p.kt, local / p.kt, s);
+    else pack_tile<0, P, TF>(p, local % p.kt, local / p.kt, s);
 }
 
 // Persistent bulk-copy pack stream (ln_pack_stream.cuh), one CTA per SM.
-template <int P, int NT>
+template <int P, int NT, bool TF>
 __global__ __launch_bounds__(NT, 1) void k_pack_stream(const __grid_constant__ PackMulti m, int ns, int nout) {
     extern __shared__ __align__(128) unsigned char ps_smem[];
-    pack_stream<P, NT>(m, blockIdx.x, gridDim.x, ps_smem, ns, nout);
+    pack_stream<P, NT, TF>(m, blockIdx.x, gridDim.x, ps_smem, ns, nout);
 }
 
 // Batched layout, one CTA of 1024 threads: (1) rank instances by decreasing
@@ -266,11 +267,11 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_batch_plan(int is_syr2k, int c
 
 // Packs every instance's operands: a flat grid over all (rank, operand, row
 // tile, k tile); each CTA finds its rank by binary search of the prefix sums.
-template <int P>
+template <int P, bool TF>
 __global__ __launch_bounds__(256) void k_pack_batched(int is_syr2k, int count, const ln_sym_desc *__restrict__ descs,
                                                       const long long *__restrict__ pack_off,
                                                       const int *__restrict__ pack_prefix,
-                                                      const int *__restrict__ order, char *pack_base, int tf32) {
+                                                      const int *__restrict__ order, char *pack_base) {
     __shared__ float s[1][PK_ROWS + 1];
     const int t = blockIdx.x;
     int lo = 0, hi = count - 1;
@@ -296,8 +297,8 @@ __global__ __launch_bounds__(256) void k_pack_batched(int is_syr2k, int count, c
     p.dst = pack_base + pack_off[2 * lo + operand];
     p.rt = mt;
     p.kt = kt;
-    p.tf32 = tf32;
-    pack_tile<0, P>(p, rem % kt, rem / kt, s);
+    p.tf32 = TF;
+    pack_tile<0, P, TF>(p, rem % kt, rem / kt, s);
 }
 
 }  // namespace
@@ -311,17 +312,19 @@ ln_status pack_operand(const PackSrc &p, int terms, cudaStream_t st) {
     if (p.rt > 65535) return fail(LN_ERR_INVALID_VALUE, "operand too tall to pack (%d row tiles)", p.rt);
     dim3 grid((unsigned)p.kt, (unsigned)p.rt);
     LaunchScope ls_(FAM_PACK, st);
-#define LN_PACK_CASE(T, P) \
-    if (p.trans == T && terms == P) k_pack<T, P><<<grid, 256, 0, st>>>(p)
-    LN_PACK_CASE(0, 1);
-    else LN_PACK_CASE(0, 2);
-    else LN_PACK_CASE(0, 3);
-    else LN_PACK_CASE(0, 4);
-    else LN_PACK_CASE(1, 1);
-    else LN_PACK_CASE(1, 2);
-    else LN_PACK_CASE(1, 3);
-    else LN_PACK_CASE(1, 4);
-    else return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
+#define LN_PACK_CASE(T, P, F) \
+    if (p.trans == T && terms == P && (p.tf32 != 0) == F) k_pack<T, P, F><<<grid, 256, 0, st>>>(p)
+    LN_PACK_CASE(0, 1, false);
+    else LN_PACK_CASE(0, 2, false);
+    else LN_PACK_CASE(0, 3, false);
+    else LN_PACK_CASE(0, 2, true);
+    else LN_PACK_CASE(0, 4, true);
+    else LN_PACK_CASE(1, 1, false);
+    else LN_PACK_CASE(1, 2, false);
+    else LN_PACK_CASE(1, 3, false);
+    else LN_PACK_CASE(1, 2, true);
+    else LN_PACK_CASE(1, 4, true);
+    else return fail(LN_ERR_INVALID_VALUE, "unsupported packed format (%d pieces, tf32 %d)", terms, p.tf32);
 #undef LN_PACK_CASE
     return check_launch("split-and-pack");
 }
@@ -362,7 +365,7 @@ static_assert(pack_stream_smem(stream_stages(2), stream_outs(2), 2) <= 227 * 102
 static_assert(pack_stream_smem(stream_stages(3), stream_outs(3), 3) <= 227 * 1024, "pack stream smem");
 static_assert(pack_stream_smem(stream_stages(4), stream_outs(4), 4) <= 227 * 1024, "pack stream smem");
 
-template <int P, int NT>
+template <int P, int NT, bool TF>
 ln_status launch_pack_stream(const PackMulti &m, cudaStream_t st) {
     const int ns = stream_stages(P), nout = stream_outs(P);
     const int bytes = pack_stream_smem(ns, nout, P);
@@ -372,7 +375,7 @@ ln_status launch_pack_stream(const PackMulti &m, cudaStream_t st) {
     int dev = 0;
     LN_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        LN_CUDA_TRY(cudaFuncSetAttribute(k_pack_stream<P, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        LN_CUDA_TRY(cudaFuncSetAttribute(k_pack_stream<P, NT, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     const int tiles = m.prefix[m.count];
@@ -388,14 +391,14 @@ ln_status launch_pack_stream(const PackMulti &m, cudaStream_t st) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t le = cudaLaunchKernelEx(&cfg, k_pack_stream<P, NT>, m, ns, nout);
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, k_pack_stream<P, NT, TF>, m, ns, nout);
     if (le != cudaSuccess) return fail(LN_ERR_CUDA, "split-and-pack stream launch: %s", cudaGetErrorString(le));
     return check_launch("split-and-pack stream");
 }
 
-template <int P>
+template <int P, bool TF = false>
 ln_status launch_pack_stream(const PackMulti &m, cudaStream_t st) {
-    return tune_pack_threads() == 1024 ? launch_pack_stream<P, 1024>(m, st) : launch_pack_stream<P, 512>(m, st);
+    return tune_pack_threads() == 1024 ? launch_pack_stream<P, 1024, TF>(m, st) : launch_pack_stream<P, 512, TF>(m, st);
 }
 
 }  // namespace
@@ -406,21 +409,29 @@ ln_status pack_operands(const PackSrc *ps, int count, int terms, cudaStream_t st
     if (!make_pack_multi(ps, count, m)) return fail(LN_ERR_INVALID_VALUE, "too many tiles to pack");
     const int tiles = m.prefix[count];
     if (tiles == 0) return LN_SUCCESS;
+    const bool tf = m.op[0].tf32 != 0;  // one format per launch
+    for (int i = 1; i < count; ++i)
+        if ((ps[i].tf32 != 0) != tf) return fail(LN_ERR_INVALID_VALUE, "pack_operands: mixed operand formats");
+    if (tf && terms != 2 && terms != 4) return fail(LN_ERR_INVALID_VALUE, "TF32 operand with %d pieces", terms);
     if (pack_stream_eligible(m)) {
+        if (tf) return terms == 2 ? launch_pack_stream<2, true>(m, st) : launch_pack_stream<4, true>(m, st);
         switch (terms) {
             case 1: return launch_pack_stream<1>(m, st);
             case 2: return launch_pack_stream<2>(m, st);
             case 3: return launch_pack_stream<3>(m, st);
-            case 4: return launch_pack_stream<4>(m, st);
             default: return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
         }
     }
     LaunchScope ls_(FAM_PACK, st);
+    if (tf) {
+        if (terms == 2) k_pack_multi<2, true><<<(unsigned)tiles, 256, 0, st>>>(m);
+        else k_pack_multi<4, true><<<(unsigned)tiles, 256, 0, st>>>(m);
+        return check_launch("split-and-pack (multi)");
+    }
     switch (terms) {
-        case 1: k_pack_multi<1><<<(unsigned)tiles, 256, 0, st>>>(m); break;
-        case 2: k_pack_multi<2><<<(unsigned)tiles, 256, 0, st>>>(m); break;
-        case 3: k_pack_multi<3><<<(unsigned)tiles, 256, 0, st>>>(m); break;
-        case 4: k_pack_multi<4><<<(unsigned)tiles, 256, 0, st>>>(m); break;
+        case 1: k_pack_multi<1, false><<<(unsigned)tiles, 256, 0, st>>>(m); break;
+        case 2: k_pack_multi<2, false><<<(unsigned)tiles, 256, 0, st>>>(m); break;
+        case 3: k_pack_multi<3, false><<<(unsigned)tiles, 256, 0, st>>>(m); break;
         default: return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
     }
     return check_launch("split-and-pack (multi)");
@@ -441,17 +452,22 @@ ln_status sym_batched_pack(int is_syr2k, int count, const ln_sym_desc *d_descs, 
                            const int *d_pack_prefix, const int *d_order, int total_pack_tiles, char *pack_base,
                            int terms, int tf32, cudaStream_t st) {
     if (total_pack_tiles == 0) return LN_SUCCESS;
-    if (terms < 1 || terms > 4) return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
-#define LN_PACK_BATCHED(P)                                                                                   \
-    k_pack_batched<P><<<total_pack_tiles, 256, 0, st>>>(is_syr2k, count, d_descs, d_pack_off, d_pack_prefix, \
-                                                        d_order, pack_base, tf32)
+    const bool ok = tf32 ? (terms == 2 || terms == 4) : (terms >= 1 && terms <= 3);
+    if (!ok) return fail(LN_ERR_INVALID_VALUE, "unsupported packed format (%d pieces, tf32 %d)", terms, tf32);
+#define LN_PACK_BATCHED(P, F)                                                                                   \
+    k_pack_batched<P, F><<<total_pack_tiles, 256, 0, st>>>(is_syr2k, count, d_descs, d_pack_off, d_pack_prefix, \
+                                                           d_order, pack_base)
     {
         LaunchScope ls_(FAM_PACK, st);
-        switch (terms) {
-            case 1: LN_PACK_BATCHED(1); break;
-            case 2: LN_PACK_BATCHED(2); break;
-            case 3: LN_PACK_BATCHED(3); break;
-            default: LN_PACK_BATCHED(4); break;
+        if (tf32) {
+            if (terms == 2) LN_PACK_BATCHED(2, true);
+            else LN_PACK_BATCHED(4, true);
+        } else {
+            switch (terms) {
+                case 1: LN_PACK_BATCHED(1, false); break;
+                case 2: LN_PACK_BATCHED(2, false); break;
+                default: LN_PACK_BATCHED(3, false); break;
+            }
         }
     }
 #undef LN_PACK_BATCHED

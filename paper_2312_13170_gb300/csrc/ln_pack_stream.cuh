@@ -112,7 +112,7 @@ __device__ __forceinline__ void ps_issue(const PsTile &tl, float *stage, int tid
 
 // Split one staged tile into the P-term packed image at `out`. The staged
 // tile is zero outside the matrix, so only centring needs the extent.
-template <int P, int NT>
+template <int P, int NT, bool TF>
 __device__ __forceinline__ void ps_split(const PsTile &tl, const float *stage, char *out, int tid) {
     const PackSrc &p = *tl.p;
     const bool centre = p.off_hi != nullptr;
@@ -133,7 +133,7 @@ __device__ __forceinline__ void ps_split(const PsTile &tl, const float *stage, c
                 for (int q = 0; q < 8; ++q)
                     if (c * 8 + q < tl.nk) v[q] = (v[q] - h) - l;
             }
-            store_chunk_any<P>(out, r, c, v, p.tf32);
+            store_chunk_fmt<P, TF>(out, r, c, v);
         }
     } else {
         // warp w builds chunk c = w % 8 of 32 consecutive rows per pass: each
@@ -151,7 +151,7 @@ __device__ __forceinline__ void ps_split(const PsTile &tl, const float *stage, c
                 for (int q = 0; q < 8; ++q)
                     if (c * 8 + q < tl.nk) v[q] = (v[q] - h) - l;
             }
-            store_chunk_any<P>(out, r, c, v, p.tf32);
+            store_chunk_fmt<P, TF>(out, r, c, v);
         }
     }
 }
@@ -160,7 +160,8 @@ __device__ __forceinline__ void ps_split(const PsTile &tl, const float *stage, c
 // bytes (16-byte aligned); ns in [2, PS_MAX_STAGES], nout 2 or 3. Threads >= NT
 // must not call this. Every wait is on this thread's own copies (no flag
 // written by another agent), so none can outlast the memory system.
-template <int P, int NT>
+// TF: the operands take TF32 blocks (PackSrc::tf32, the same for every operand of m).
+template <int P, int NT, bool TF>
 __device__ void pack_stream(const PackMulti &m, int cta, int ncta, unsigned char *smem, int ns, int nout) {
     const int tid = threadIdx.x;
     float *stages = reinterpret_cast<float *>(smem);
@@ -194,7 +195,7 @@ __device__ void pack_stream(const PackMulti &m, int cta, int ncta, unsigned char
         named_sync(PS_BARRIER, NT);
         const PsTile tl = ps_tile(m, cta + i * ncta, P);
         char *out = outs + oo * P * PK_TILE_BYTES;
-        ps_split<P, NT>(tl, stages + so * (PS_IN_BYTES / 4), out, tid);
+        ps_split<P, NT, TF>(tl, stages + so * (PS_IN_BYTES / 4), out, tid);
         fence_proxy_async_smem();
         // every thread is past the split: stage `so` may be refilled, and the
         // output buffer is complete

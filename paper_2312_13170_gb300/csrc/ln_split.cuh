@@ -83,17 +83,15 @@ __device__ __forceinline__ void store_chunk_tf32(char *block0, int r, int c, con
     }
 }
 
-// store_chunk for a block of P pieces: BF16 terms, or (tf32, P even) P / 2
-// TF32 terms
-template <int P>
-__device__ __forceinline__ void store_chunk_any(char *block0, int r, int c, const float *v, int tf32) {
-    if constexpr (P % 2 == 0) {
-        if (tf32) {
-            store_chunk_tf32<P / 2>(block0, r, c, v);
-            return;
-        }
+// store_chunk for a block of P pieces: P BF16 terms, or (TF) P / 2 TF32 terms
+template <int P, bool TF>
+__device__ __forceinline__ void store_chunk_fmt(char *block0, int r, int c, const float *v) {
+    if constexpr (TF) {
+        static_assert(P % 2 == 0, "a TF32 block has two pieces per term");
+        store_chunk_tf32<P / 2>(block0, r, c, v);
+    } else {
+        store_chunk<P>(block0, r, c, v);
     }
-    store_chunk<P>(block0, r, c, v);
 }
 
 }  // namespace ln

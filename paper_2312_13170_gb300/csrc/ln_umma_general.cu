@@ -106,7 +106,8 @@ ln_status umma_contract(const UmmaProblem &p0, int terms, cudaStream_t st, const
     // CTA pairs over vertically adjacent tiles ("pair" knob 1: 256-wide tiles, where
     // they measured faster; 2: every width): `total` counts pair tiles
     const int bn_pair = p.bn > 0 ? p.bn : umma_tile_n(terms, 0, p.epi.M, p.epi.N);
-    if ((tune_pair() == 2 || (tune_pair() == 1 && bn_pair == 256)) && p.ksplit <= 1 && !p.streamk && p.mt >= 2) {
+    if (!p.tf32 && (tune_pair() == 2 || (tune_pair() == 1 && bn_pair == 256)) && p.ksplit <= 1 && !p.streamk &&
+        p.mt >= 2) {
         p.pair = 1;
         tiles = ceil_div(p.mt, 2) * p.nt;
     }
@@ -115,6 +116,7 @@ ln_status umma_contract(const UmmaProblem &p0, int terms, cudaStream_t st, const
     if (bn != 128 && bn != 256) return fail(LN_ERR_INVALID_VALUE, "tile width %d", bn);
     if (terms > 2 && bn != 128) return fail(LN_ERR_INVALID_VALUE, "three split terms need 128-wide tiles");
     const bool wide = bn == 256;
+    if (p.tf32) return umma_contract_tf32(ek, p, terms, bn, total, st);
     if (p.pair) return umma_contract_pair(ek, p, terms, bn, total, st, side, side_done);
     switch (terms) {
         case 1:
@@ -137,14 +139,16 @@ ln_status umma_read_error_general(int *value) {
 }
 
 ln_status umma_read_error(int *value) {
-    int a = 0, b = 0, c = 0;
+    int a = 0, b = 0, c = 0, d = 0;
     ln_status s = umma_read_error_general(&a);
     if (s != LN_SUCCESS) return s;
     s = umma_read_error_sym(&b);
     if (s != LN_SUCCESS) return s;
     s = umma_read_error_pair(&c);
     if (s != LN_SUCCESS) return s;
-    *value = a | b | c;
+    s = umma_read_error_tf32(&d);
+    if (s != LN_SUCCESS) return s;
+    *value = a | b | c | d;
     return LN_SUCCESS;
 }
 

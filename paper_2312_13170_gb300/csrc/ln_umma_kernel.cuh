@@ -217,31 +217,26 @@ __device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t a, uint
 // TF32 operands (kind::tf32, K = 8 per instruction: the same 32 bytes of each
 // 128-byte row as a BF16 K = 16 step, so the descriptors advance alike). The
 // instruction descriptor differs from the BF16 one only in the A and B format
-// fields (TF32 = 2). The MMA of either kind is one predicated pair of
-// instructions, so the issue loop has no branch on the operand type.
+// fields (TF32 = 2).
 __host__ __device__ constexpr uint32_t idesc_tf32(int n, int m = BM) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 template <int BN>
-__device__ __forceinline__ void umma_any(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc, uint32_t tf32) {
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
     asm volatile(
-        "{\n\t.reg .pred p, t;\n\t"
+        "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "setp.ne.b32 t, %5, 0;\n\t"
-        "@t tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %6, p;\n\t"
-        "@!t tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc_bf16(BN)), "r"(acc), "r"(tf32), "r"(idesc_tf32(BN))
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc_tf32(BN)), "r"(acc)
         : "memory");
 }
 template <int BN>
-__device__ __forceinline__ void umma_any_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc, uint32_t tf32) {
+__device__ __forceinline__ void umma_tf32_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
     asm volatile(
-        "{\n\t.reg .pred p, t;\n\t"
+        "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "setp.ne.b32 t, %5, 0;\n\t"
-        "@t tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %6, p;\n\t"
-        "@!t tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc_bf16(BN, 2 * BM)), "r"(acc), "r"(tf32), "r"(idesc_tf32(BN, 2 * BM))
+        "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc_tf32(BN, 2 * BM)), "r"(acc)
         : "memory");
 }
 // completion of the pair's MMAs, signalled on the mbarrier at bar's offset in both CTAs
@@ -676,10 +671,36 @@ __device__ __forceinline__ void block_store_f(const EpiParams &e, float *sc, int
 // queue); CTAs from tile_ctas on (only launched for single problems with the
 // packing epilogue, see Cfg::SIDE_OK) run the pack stream over `side`, the
 // operand of the next contraction, on SMs that have no output tile.
+// The MMAs of one k tile (every split product, K / 16 steps each) into the
+// accumulator d; `first` starts the accumulation (no add to d's old value).
+template <class C, class PR, int BN, bool PAIR, bool TF>
+__device__ __forceinline__ void issue_ktile(uint32_t d, uint32_t a0, uint32_t b0, bool first) {
+#pragma unroll
+    for (int pr = 0; pr < PR::n; ++pr) {
+#pragma unroll
+        for (int ks = 0; ks < PK_K / 16; ++ks) {
+            const uint64_t ad = sw128_desc(a0 + PR::a(pr) * PK_TILE_BYTES + ks * 32);
+            const uint32_t acc_in = (!first || pr || ks) ? 1u : 0u;
+            if constexpr (PAIR) {
+                const uint64_t bd = sw128_desc(b0 + PR::b(pr) * C::BH_BYTES + ks * 32);
+                if constexpr (TF) umma_tf32_pair<BN>(d, ad, bd, acc_in);
+                else umma_bf16_pair<BN>(d, ad, bd, acc_in);
+            } else {
+                const uint64_t bd = sw128_desc(b0 + PR::b(pr) * C::HALVES * PK_TILE_BYTES + ks * 32);
+                if constexpr (TF) umma_tf32<BN>(d, ad, bd, acc_in);
+                else umma_bf16<BN>(d, ad, bd, acc_in);
+            }
+        }
+    }
+}
+
 template <int EK>
 constexpr int epi_width() { return EK == EK_SYM ? 64 : 128; }
 
-template <int P, int BN, int BATCHED, int EK, int PAIR = 0>
+// TF: TF32 operands (kind::tf32, 32-K tiles, TF32 packing epilogue). A
+// template parameter so that the BF16 instantiations carry no TF32 code (a
+// runtime choice enlarged the issue loop and slowed the BF16 kernels).
+template <int P, int BN, int BATCHED, int EK, int PAIR = 0, int TF = 0>
 __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>(), PAIR>::NTHREADS, 1) void k_umma(const __grid_constant__ UmmaProblem single,
                                                                   const UmmaProblem *__restrict__ probs,
                                                                   const int *__restrict__ prefix,
@@ -694,13 +715,13 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>(), PAIR>::NTHREADS, 1) voi
     // 1024-byte alignment of the stage area is required by the 128-byte swizzle.
     const uint32_t raw = saddr(smem_raw);
     const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
-    if constexpr (EK == EK_PACK && !BATCHED && C::SIDE_OK) {
+    if constexpr (EK == EK_PACK && !BATCHED && C::SIDE_OK && !TF) {
         if ((int)blockIdx.x >= tile_ctas) {
             pdl_wait();
             pdl_trigger();
             if (threadIdx.x < 256)
-                pack_stream<P, 256>(side, (int)blockIdx.x - tile_ctas, (int)gridDim.x - tile_ctas, smem_raw + pad,
-                                    C::SIDE_NS, C::SIDE_NOUT);
+                pack_stream<P, 256, false>(side, (int)blockIdx.x - tile_ctas, (int)gridDim.x - tile_ctas,
+                                           smem_raw + pad, C::SIDE_NS, C::SIDE_NOUT);
             return;
         }
     }
@@ -920,7 +941,6 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>(), PAIR>::NTHREADS, 1) voi
                 const UmmaProblem &pb = sl.prob;
                 const int qa = sl.qa, qb = sl.qb;
                 const int ck = pb.chunk_kt > 0 ? pb.chunk_kt : (qb - qa > 0 ? qb - qa : 1);
-                const uint32_t tf32 = pb.tf32 ? 1u : 0u;
                 bool ok = true;
                 if (pair && rank != 0) {
                     // the peer of a pair issues no MMA: it tells the leader when each
@@ -960,22 +980,7 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>(), PAIR>::NTHREADS, 1) voi
                         tc_fence_after();
                         const uint32_t a0 = stage0 + st * C::STAGE_BYTES;
                         const uint32_t b0 = a0 + C::A_BYTES;
-#pragma unroll
-                        for (int pr = 0; pr < PR::n; ++pr) {
-#pragma unroll
-                            for (int ks = 0; ks < PK_K / 16; ++ks) {
-                                const uint64_t ad = sw128_desc(a0 + PR::a(pr) * PK_TILE_BYTES + ks * 32);
-                                const uint32_t acc_in = ((q - q0) | pr | ks) ? 1u : 0u;
-                                if constexpr (pair) {
-                                    const uint64_t bd = sw128_desc(b0 + PR::b(pr) * C::BH_BYTES + ks * 32);
-                                    umma_any_pair<BN>(d, ad, bd, acc_in, tf32);
-                                } else {
-                                    const uint64_t bd =
-                                        sw128_desc(b0 + PR::b(pr) * C::HALVES * PK_TILE_BYTES + ks * 32);
-                                    umma_any<BN>(d, ad, bd, acc_in, tf32);
-                                }
-                            }
-                        }
+                        issue_ktile<C, PR, BN, pair, TF != 0>(d, a0, b0, q == q0);
                         if constexpr (pair) umma_commit_pair_mc(&ctl->empty[st]);
                         else umma_commit(&ctl->empty[st]);
                         ++it;
@@ -1216,7 +1221,7 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>(), PAIR>::NTHREADS, 1) voi
 #pragma unroll
                 for (int g = 0; g < EPW / 32; ++g) {
                     const int kt = (col0 + g * 32) / PK_K;  // 128 x 64 block of the packed operand
-                    if (pb.tf32) {  // blocks of 2P pieces: P TF32 terms of two 32-K tiles
+                    if constexpr (TF != 0) {  // blocks of 2P pieces: P TF32 terms of two 32-K tiles
                         char *blk = e.pack + (size_t)((long long)tr.mi * e.pack_kt + kt) * 2 * P * PK_TILE_BYTES;
 #pragma unroll
                         for (int cc = 0; cc < 4; ++cc)
@@ -1282,11 +1287,11 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>(), PAIR>::NTHREADS, 1) voi
 // With `side` (single problems, packing epilogue, Cfg::SIDE_OK), CTAs beyond
 // the tile CTAs pack that operand when enough SMs are free to finish it within
 // the contraction's own time; *side_done reports whether they were launched.
-template <int P, int BN, int BATCHED, int EK, int PAIR = 0>
+template <int P, int BN, int BATCHED, int EK, int PAIR = 0, int TF = 0>
 ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int *prefix, const int *owner, int total,
                  int *queue, cudaStream_t st, const PackMulti *side = nullptr, bool *side_done = nullptr) {
     using C = Cfg<P, BN, epi_width<EK>(), PAIR>;
-    auto kern = k_umma<P, BN, BATCHED, EK, PAIR>;
+    auto kern = k_umma<P, BN, BATCHED, EK, PAIR, TF>;
     // the shared-memory opt-in is set once per device (so nothing but launches
     // happens while a caller captures a graph)
     static bool attr_set[64] = {false};
@@ -1348,7 +1353,7 @@ ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int 
     int side_ctas = 0;
     PackMulti none{};
     if (side_done) *side_done = false;
-    if constexpr (EK == EK_PACK && !BATCHED && C::SIDE_OK) {
+    if constexpr (EK == EK_PACK && !BATCHED && C::SIDE_OK && !TF) {
         if (!sk && side && single && side->prefix[side->count] > 0 && pack_stream_eligible(*side)) {
             // time model: a 128 x BN x 64 MMA step per product at the SM's share of
             // the BF16 peak (~0.33 us at BN = 256) against ~60 GB/s of split

@@ -17,7 +17,7 @@ ln_status umma_contract_sym(const UmmaProblem &p0, int terms, cudaStream_t st) {
         if (!p.kpart || !p.kcnt) return fail(LN_ERR_INVALID_VALUE, "split-K without its workspace");
         LN_CUDA_TRY(cudaMemsetAsync(p.kcnt, 0, umma_split_cnt_bytes(tiles, 128), st));
         tiles *= p.ksplit;
-    } else if (tune_pair() == 2 && !p.streamk && p.mt >= 2) {  // measured slower on 128-wide tiles: opt-in
+    } else if (!p.tf32 && tune_pair() == 2 && !p.streamk && p.mt >= 2) {  // slower on 128-wide tiles: opt-in
         // CTA pairs: row-tile pair q covers the column tiles 0 .. min(2q + 1, mt - 1)
         p.pair = 1;
         tiles = 0;
@@ -25,6 +25,7 @@ ln_status umma_contract_sym(const UmmaProblem &p0, int terms, cudaStream_t st) {
     }
     if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many output tiles");
     const int total = (int)tiles;
+    if (p.tf32) return umma_contract_sym_tf32(p, terms, total, st);
     if (p.pair) return umma_contract_sym_pair(p, terms, total, st);
     switch (terms) {
         case 1: return launch<1, 128, 0, EK_SYM>(&p, nullptr, nullptr, nullptr, total, nullptr, st);
@@ -35,9 +36,10 @@ ln_status umma_contract_sym(const UmmaProblem &p0, int terms, cudaStream_t st) {
 }
 
 ln_status umma_contract_batched(const UmmaProblem *d_probs, const int *d_tile_prefix, const int *d_tile_owner,
-                                int total_tiles, int *d_queue, int terms, cudaStream_t st) {
+                                int total_tiles, int *d_queue, int terms, int tf32, cudaStream_t st) {
     if (total_tiles == 0) return LN_SUCCESS;
     LN_CUDA_TRY(cudaMemsetAsync(d_queue, 0, sizeof(int), st));
+    if (tf32) return umma_contract_batched_tf32(d_probs, d_tile_prefix, d_tile_owner, total_tiles, d_queue, terms, st);
     switch (terms) {
         case 1: return launch<1, 128, 1, EK_SYM>(nullptr, d_probs, d_tile_prefix, d_tile_owner, total_tiles, d_queue, st);
         case 2: return launch<2, 128, 1, EK_SYM>(nullptr, d_probs, d_tile_prefix, d_tile_owner, total_tiles, d_queue, st);
