@@ -546,7 +546,7 @@ def suite_lines(modes, only, reps, sink):
 
 
 ALL_WORKLOADS = {"gemm", "chain", "3mm", "cov", "batched", "backward", "gramschmidt"}
-SUITE_MODES = [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16")]
+SUITE_MODES = [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "3xbf16"), ("internalized", "3xtf32")]
 ALL_MODES = [("plain", "fp32"), ("internalized", "fp32"), ("internalized", "bf16"), ("internalized", "3xbf16"),
              ("internalized", "6xbf16"), ("internalized", "tf32"), ("internalized", "3xtf32")]
 
