@@ -165,6 +165,13 @@ ln_status ln_timing_read(const char *family, double *total_ms /*host*/, int *lau
  *              block of D (chain) or C (GEMM) into the operand stages once its
  *              MMAs are done, so the epilogue stores E at once and reads D or
  *              C from shared memory;
+ *   "sym_wide" 0, 1 or 2 (default 0): output tiles of 128 x 256 instead of
+ *              128 x 128 over the lower triangle of single symmetric
+ *              contractions (covariance, correlation, SYRK/SYR2K); 2 takes them
+ *              where they fill at most half the SMs and so take stream-K
+ *              (deep problems such as covariance of 8192 samples), 1 always
+ *              (one or two split terms), 0 never (measured faster on the
+ *              shipped workloads); results are bit-identical on integer inputs;
  *   "stream_k" 0, 1 or 2 (default 2): stream-K for single tensor-core
  *              contractions with fewer output tiles than SMs (covariance,
  *              correlation, SYRK/SYR2K and the general contractions that do

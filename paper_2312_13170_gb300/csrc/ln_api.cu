@@ -85,6 +85,7 @@ std::atomic<int> g_gs_rows{4};
 std::atomic<int> g_stream_k{2};
 std::atomic<int> g_pair{1};
 std::atomic<int> g_stage_beta{1};
+std::atomic<int> g_sym_wide{0};
 std::atomic<int> g_simt_exact{1};
 }  // namespace
 
@@ -96,6 +97,7 @@ int tune_gs_rows() { return g_gs_rows.load(std::memory_order_relaxed); }
 int tune_stream_k() { return g_stream_k.load(std::memory_order_relaxed); }
 int tune_pair() { return g_pair.load(std::memory_order_relaxed); }
 int tune_stage_beta() { return g_stage_beta.load(std::memory_order_relaxed); }
+int tune_sym_wide() { return g_sym_wide.load(std::memory_order_relaxed); }
 int tune_simt_exact() { return g_simt_exact.load(std::memory_order_relaxed); }
 
 bool inject_timeout_requested() {
@@ -495,6 +497,7 @@ struct CovPlan {
     float *hi = nullptr, *lo = nullptr, *rs = nullptr;
     char *pack = nullptr;
     int mt = 0, kt = 0;
+    int bn = 128, prt = 0;  // symmetric tile width, packed 128-row tiles
     SplitPlan split;
 };
 
@@ -508,8 +511,10 @@ void plan_cov(Ws &w, int n, int m, ln_form form, ln_precision prec, CovPlan &p) 
     if (form == LN_FORM_INTERNALIZED && tensor_prec(prec)) {
         p.mt = (int)ceil_div(m, PK_ROWS);
         p.kt = (int)ceil_div(n, PK_K);
-        p.pack = w.take<char>(packed_bytes(p.mt, p.kt, prec_terms(prec)));
-        plan_split(w, (long long)p.mt * (p.mt + 1) / 2, p.kt, 128, p.split);
+        p.bn = umma_sym_tile_n(prec_terms(prec), p.mt, p.kt);
+        p.prt = sym_packed_rt(p.mt, p.bn);
+        p.pack = w.take<char>(packed_bytes(p.prt, p.kt, prec_terms(prec)));
+        plan_split(w, sym_tiles(p.mt, p.bn), p.kt, p.bn, p.split);
     }
 }
 
@@ -575,7 +580,7 @@ ln_status run_cov(bool corr, int n, int m, const float *X, int ldx, float *out, 
         return simt_contract(m, m, n, op, e, st);
     }
     const int P = prec_terms(prec);
-    PackSrc ps{X, ldx, 1, m, n, p.hi, p.lo, p.pack, p.mt, p.kt};
+    PackSrc ps{X, ldx, 1, m, n, p.hi, p.lo, p.pack, p.prt, p.kt};
     ps.tf32 = is_tf32(prec);
     LN_TRY(pack_operand(ps, P, st));
     UmmaProblem pb{};
@@ -583,7 +588,9 @@ ln_status run_cov(bool corr, int n, int m, const float *X, int ldx, float *out, 
     pb.nseg = 1;
     pb.kt = p.kt;
     pb.x_kt = pb.y_kt = p.kt;
-    pb.mt = pb.nt = p.mt;
+    pb.mt = p.mt;
+    pb.nt = (int)ceil_div(p.mt * 128, p.bn);
+    pb.bn = p.bn;
     pb.sym = 1;
     pb.chunk_kt = tune_chunk_kt();
     pb.tf32 = is_tf32(prec);
@@ -596,6 +603,7 @@ ln_status run_cov(bool corr, int n, int m, const float *X, int ldx, float *out, 
 struct SymPlan {
     char *pa = nullptr, *pb = nullptr;
     int mt = 0, kt = 0;
+    int bn = 128, prt = 0;  // symmetric tile width, packed 128-row tiles
     SplitPlan split;
 };
 
@@ -603,9 +611,12 @@ void plan_sym(Ws &w, bool two, int n, int k, ln_form form, ln_precision prec, Sy
     if (form != LN_FORM_INTERNALIZED || !tensor_prec(prec)) return;
     p.mt = (int)ceil_div(n, PK_ROWS);
     p.kt = (int)ceil_div(k, PK_K);
-    p.pa = w.take<char>(packed_bytes(p.mt, p.kt, prec_terms(prec)));
-    if (two) p.pb = w.take<char>(packed_bytes(p.mt, p.kt, prec_terms(prec)));
-    plan_split(w, (long long)p.mt * (p.mt + 1) / 2, (two ? 2 : 1) * p.kt, 128, p.split);
+    const int ktot = (two ? 2 : 1) * p.kt;
+    p.bn = umma_sym_tile_n(prec_terms(prec), p.mt, ktot);
+    p.prt = sym_packed_rt(p.mt, p.bn);
+    p.pa = w.take<char>(packed_bytes(p.prt, p.kt, prec_terms(prec)));
+    if (two) p.pb = w.take<char>(packed_bytes(p.prt, p.kt, prec_terms(prec)));
+    plan_split(w, sym_tiles(p.mt, p.bn), ktot, p.bn, p.split);
 }
 
 ln_status run_sym(bool two, ln_fill fill, int n, int k, float alpha, const float *A, int lda, const float *B, int ldb,
@@ -656,8 +667,8 @@ ln_status run_sym(bool two, ln_fill fill, int n, int k, float alpha, const float
         return simt_contract(n, n, k, op, e, st);
     }
     const int P = prec_terms(prec);
-    PackSrc ps[2] = {{A, lda, 0, n, k, nullptr, nullptr, p.pa, p.mt, p.kt},
-                     {B, ldb, 0, n, k, nullptr, nullptr, p.pb, p.mt, p.kt}};
+    PackSrc ps[2] = {{A, lda, 0, n, k, nullptr, nullptr, p.pa, p.prt, p.kt},
+                     {B, ldb, 0, n, k, nullptr, nullptr, p.pb, p.prt, p.kt}};
     for (PackSrc &q : ps) q.tf32 = is_tf32(prec);
     LN_TRY(zero_streamk_flags(p.split, st));
     LN_TRY(pack_operands(ps, two ? 2 : 1, P, st));
@@ -672,7 +683,9 @@ ln_status run_sym(bool two, ln_fill fill, int n, int k, float alpha, const float
     }
     pb.kt = p.kt;
     pb.x_kt = pb.y_kt = p.kt;
-    pb.mt = pb.nt = p.mt;
+    pb.mt = p.mt;
+    pb.nt = (int)ceil_div(p.mt * 128, p.bn);
+    pb.bn = p.bn;
     pb.sym = 1;
     pb.chunk_kt = tune_chunk_kt();
     pb.tf32 = is_tf32(prec);
@@ -1012,6 +1025,11 @@ ln_status ln_set_tuning(const char *key, int value) {
         g_stage_beta.store(value);
         return LN_SUCCESS;
     }
+    if (strcmp(key, "sym_wide") == 0) {
+        if (value < 0 || value > 2) return fail(LN_ERR_INVALID_VALUE, "sym_wide must be 0, 1 or 2 (got %d)", value);
+        g_sym_wide.store(value);
+        return LN_SUCCESS;
+    }
     if (strcmp(key, "pair") == 0) {
         if (value < 0 || value > 2) return fail(LN_ERR_INVALID_VALUE, "pair must be 0, 1 or 2 (got %d)", value);
         g_pair.store(value);
@@ -1047,6 +1065,7 @@ ln_status ln_get_tuning(const char *key, int *value) {
     else if (strcmp(key, "stream_k") == 0) *value = g_stream_k.load();
     else if (strcmp(key, "pair") == 0) *value = g_pair.load();
     else if (strcmp(key, "stage_beta") == 0) *value = g_stage_beta.load();
+    else if (strcmp(key, "sym_wide") == 0) *value = g_sym_wide.load();
     else if (strcmp(key, "simt_exact") == 0) *value = g_simt_exact.load();
     else return fail(LN_ERR_INVALID_VALUE, "unknown tuning key '%s'", key);
     return LN_SUCCESS;

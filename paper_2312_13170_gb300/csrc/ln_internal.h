@@ -204,6 +204,7 @@ int tune_split_k();       // 1: split the K range of contractions with few outpu
 int tune_stream_k();      // 1: stream-K for general contractions with fewer tiles than SMs
 int tune_pair();          // 1: CTA pairs sharing the column operand (UmmaProblem::pair)
 int tune_stage_beta();    // UmmaProblem::stage_beta
+int tune_sym_wide();      // umma_sym_tile_n: 0 never, 1 always, 2 automatic
 
 // ln_umma.cu: tcgen05 contraction over packed operands
 struct UmmaSeg {
@@ -267,6 +268,20 @@ bool inject_timeout_requested();
 // problem counts tiles of this width, and the packed N-side operand must hold
 // 128 * (width / 128) * nt rows (zero padded).
 int umma_tile_n(int terms, int sym, long long M, long long N);
+// Tile width of a symmetric problem with `mt` 128-row tiles and `ktot` k tiles
+// (64-K blocks): 256 (tiles of 128 x 256 over the lower triangle) where the
+// "sym_wide" knob allows it -- by default where those tiles fill at most half
+// the SMs and take stream-K -- else 128. Three split terms always take 128.
+int umma_sym_tile_n(int terms, long long mt, int ktot);
+// Lower-triangle output tiles of a symmetric problem at tile width bn; 256-wide
+// tiles read the packed operand as sym_packed_rt(mt, bn) 128-row tiles (an even
+// count, the last one zero).
+inline long long sym_tiles(long long mt, int bn) {
+    if (bn != 256) return mt * (mt + 1) / 2;
+    const long long q = mt / 2;
+    return (mt % 2) ? (q + 1) * (q + 1) : q * (q + 1);
+}
+inline int sym_packed_rt(int mt, int bn) { return bn == 256 ? (mt + 1) / 2 * 2 : mt; }
 // Split-K slices for a single problem with `tiles` output tiles and `ktot`
 // k tiles (segments x k tiles): enough to fill the SMs, at least four k tiles
 // each, none empty; 1 when the tiles already fill the GPU or the "split_k"
@@ -305,7 +320,7 @@ ln_status umma_contract_batched(const UmmaProblem *d_probs, const int *d_tile_pr
 // ln_umma_tf32.cu: the TF32 launches (problems already in 32-K tiles, `terms`
 // the TF32 term count)
 ln_status umma_contract_tf32(int ek, const UmmaProblem &p, int terms, int bn, int total, cudaStream_t st);
-ln_status umma_contract_sym_tf32(const UmmaProblem &p, int terms, int total, cudaStream_t st);
+ln_status umma_contract_sym_tf32(const UmmaProblem &p, int terms, int bn, int total, cudaStream_t st);
 ln_status umma_contract_batched_tf32(const UmmaProblem *d_probs, const int *d_tile_prefix, const int *d_tile_owner,
                                      int total_tiles, int *d_queue, int terms, cudaStream_t st);
 ln_status umma_read_error_tf32(int *value);

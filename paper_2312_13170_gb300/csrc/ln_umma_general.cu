@@ -37,6 +37,13 @@ int umma_tile_n(int terms, int sym, long long M, long long N) {
     return 2 * wide_tiles <= sm_count() ? 128 : 256;
 }
 
+int umma_sym_tile_n(int terms, long long mt, int ktot) {
+    const int knob = tune_sym_wide();
+    if (terms == 3 || mt < 2 || knob == 0) return 128;
+    if (knob == 1) return 256;
+    return umma_streamk(sym_tiles(mt, 256), ktot) ? 256 : 128;
+}
+
 int umma_ksplit(long long tiles, int ktot) {
     const int sms = sm_count();
     if (!tune_split_k() || tiles <= 0 || ktot < 8 || 2 * tiles > sms) return 1;

@@ -303,6 +303,23 @@ __device__ __forceinline__ void tri_tile(int t, int &ti, int &tj) {
     tj = t - r * (r + 1) / 2;
 }
 
+// Lower-triangle tiles of 128 rows x 256 columns: row tile mi holds column
+// tiles 0 .. mi / 2 (those with a column <= some row of the tile), so row
+// tiles 2q and 2q + 1 hold q + 1 each and tiles 0 .. q(q + 1) - 1 cover row
+// tiles below 2q.
+__device__ __forceinline__ void tri_tile_wide(int t, int &ti, int &tj) {
+    int q = (int)((sqrtf(4.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((q + 1) * (q + 2) <= t) ++q;
+    while (q * (q + 1) > t) --q;
+    if (t < (q + 1) * (q + 1)) {
+        ti = 2 * q;
+        tj = t - q * (q + 1);
+    } else {
+        ti = 2 * q + 1;
+        tj = t - (q + 1) * (q + 1);
+    }
+}
+
 struct TileRef {
     const UmmaProblem *p;
     int mi, ni;
@@ -310,7 +327,7 @@ struct TileRef {
 
 // Tile index -> (problem, row tile, column tile). Batched launches look the
 // problem up in the tile -> instance map the planning kernel wrote.
-template <int BATCHED>
+template <int BATCHED, int BN = 128>
 __device__ __forceinline__ TileRef resolve(int t, const UmmaProblem *single, const UmmaProblem *probs,
                                            const int *prefix, const int *owner) {
     TileRef r;
@@ -323,7 +340,8 @@ __device__ __forceinline__ TileRef resolve(int t, const UmmaProblem *single, con
         r.p = single;
     }
     if (r.p->sym) {
-        tri_tile(local, r.mi, r.ni);
+        if constexpr (BN == 256) tri_tile_wide(local, r.mi, r.ni);
+        else tri_tile(local, r.mi, r.ni);
     } else {
         r.mi = local / r.p->nt;
         r.ni = local - r.mi * r.p->nt;
@@ -694,21 +712,24 @@ __device__ __forceinline__ void issue_ktile(uint32_t d, uint32_t a0, uint32_t b0
     }
 }
 
-template <int EK>
-constexpr int epi_width() { return EK == EK_SYM ? 64 : 128; }
+// Columns per epilogue warp: 64 for 128-wide symmetric tiles (their
+// element-wise epilogue is latency-bound and gains from twice the warps), 128
+// otherwise (eight warps at most).
+template <int EK, int BN>
+constexpr int epi_width() { return EK == EK_SYM && BN == 128 ? 64 : 128; }
 
 // TF: TF32 operands (kind::tf32, 32-K tiles, TF32 packing epilogue). A
 // template parameter so that the BF16 instantiations carry no TF32 code (a
 // runtime choice enlarged the issue loop and slowed the BF16 kernels).
 template <int P, int BN, int BATCHED, int EK, int PAIR = 0, int TF = 0>
-__global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>(), PAIR>::NTHREADS, 1) void k_umma(const __grid_constant__ UmmaProblem single,
+__global__ __launch_bounds__(Cfg<P, BN, epi_width<EK, BN>(), PAIR>::NTHREADS, 1) void k_umma(const __grid_constant__ UmmaProblem single,
                                                                   const UmmaProblem *__restrict__ probs,
                                                                   const int *__restrict__ prefix,
                                                                   const int *__restrict__ owner, int total_tiles,
                                                                   int *queue, const __grid_constant__ PackMulti side,
                                                                   int tile_ctas) {
-    using C = Cfg<P, BN, epi_width<EK>(), PAIR>;
-    constexpr int EPW = epi_width<EK>();
+    using C = Cfg<P, BN, epi_width<EK, BN>(), PAIR>;
+    constexpr int EPW = epi_width<EK, BN>();
     using PR = Products<P>;
     static_assert(!PAIR || !BATCHED, "CTA pairs take single problems");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -834,7 +855,7 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>(), PAIR>::NTHREADS, 1) voi
                     sl.qa = qa;
                     sl.qb = qb;
                 } else if (t >= 0) {
-                    tr = resolve<BATCHED>(t / ksplit, &single, probs, prefix, owner);
+                    tr = resolve<BATCHED, BN>(t / ksplit, &single, probs, prefix, owner);
                     sl.prob = *tr.p;  // roles read the problem from shared memory, not from registers
                     sl.mi = tr.mi;
                     sl.ni = tr.ni;
@@ -1253,10 +1274,12 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>(), PAIR>::NTHREADS, 1) voi
             } else {
                 float *sc = scratch + (warp - C::EPI0) * 1024;
                 const int wrow0 = tr.mi * BM + quarter * 32;
-                const bool diag = EK == EK_SYM && tr.mi == tr.ni;
 #pragma unroll
                 for (int g = 0; g < EPW / 32; ++g) {
                     if constexpr (EK == EK_SYM) {
+                        // chunks reaching above the diagonal (some column > some row
+                        // of the warp) keep only their lower-triangle elements
+                        const bool diag = col0 + g * 32 + 31 > wrow0;
                         epi_sym32(e, wrow0 + lane, col0 + g * 32, &sum[g * 32], diag);
                     } else {
                         if (!block_epilogue<EK>(e, sc, wrow0, col0 + g * 32, &sum[g * 32], lane))
@@ -1290,7 +1313,7 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK>(), PAIR>::NTHREADS, 1) voi
 template <int P, int BN, int BATCHED, int EK, int PAIR = 0, int TF = 0>
 ln_status launch(const UmmaProblem *single, const UmmaProblem *probs, const int *prefix, const int *owner, int total,
                  int *queue, cudaStream_t st, const PackMulti *side = nullptr, bool *side_done = nullptr) {
-    using C = Cfg<P, BN, epi_width<EK>(), PAIR>;
+    using C = Cfg<P, BN, epi_width<EK, BN>(), PAIR>;
     auto kern = k_umma<P, BN, BATCHED, EK, PAIR, TF>;
     // the shared-memory opt-in is set once per device (so nothing but launches
     // happens while a caller captures a graph)

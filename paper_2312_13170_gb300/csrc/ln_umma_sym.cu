@@ -10,14 +10,16 @@ namespace ln {
 ln_status umma_contract_sym(const UmmaProblem &p0, int terms, cudaStream_t st) {
     UmmaProblem p = p0;
     p.pair = 0;
-    long long tiles = (long long)p.mt * (p.mt + 1) / 2;
+    const int bn = p.bn == 256 ? 256 : 128;
+    if (bn == 256 && terms > 2) return fail(LN_ERR_INVALID_VALUE, "three split terms need 128-wide tiles");
+    long long tiles = sym_tiles(p.mt, bn);
     if (tiles == 0) return LN_SUCCESS;
     if (p.streamk && p.ksplit > 1) return fail(LN_ERR_INVALID_VALUE, "stream-K and split-K together");
     if (p.ksplit > 1) {
         if (!p.kpart || !p.kcnt) return fail(LN_ERR_INVALID_VALUE, "split-K without its workspace");
         LN_CUDA_TRY(cudaMemsetAsync(p.kcnt, 0, umma_split_cnt_bytes(tiles, 128), st));
         tiles *= p.ksplit;
-    } else if (!p.tf32 && tune_pair() == 2 && !p.streamk && p.mt >= 2) {  // slower on 128-wide tiles: opt-in
+    } else if (bn == 128 && !p.tf32 && tune_pair() == 2 && !p.streamk && p.mt >= 2) {  // slower: opt-in
         // CTA pairs: row-tile pair q covers the column tiles 0 .. min(2q + 1, mt - 1)
         p.pair = 1;
         tiles = 0;
@@ -25,8 +27,15 @@ ln_status umma_contract_sym(const UmmaProblem &p0, int terms, cudaStream_t st) {
     }
     if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many output tiles");
     const int total = (int)tiles;
-    if (p.tf32) return umma_contract_sym_tf32(p, terms, total, st);
+    if (p.tf32) return umma_contract_sym_tf32(p, terms, bn, total, st);
     if (p.pair) return umma_contract_sym_pair(p, terms, total, st);
+    if (bn == 256) {  // 128 x 256 lower-triangle tiles (deep problems with stream-K)
+        switch (terms) {
+            case 1: return launch<1, 256, 0, EK_SYM>(&p, nullptr, nullptr, nullptr, total, nullptr, st);
+            case 2: return launch<2, 256, 0, EK_SYM>(&p, nullptr, nullptr, nullptr, total, nullptr, st);
+            default: return fail(LN_ERR_INVALID_VALUE, "unsupported split term count %d", terms);
+        }
+    }
     switch (terms) {
         case 1: return launch<1, 128, 0, EK_SYM>(&p, nullptr, nullptr, nullptr, total, nullptr, st);
         case 2: return launch<2, 128, 0, EK_SYM>(&p, nullptr, nullptr, nullptr, total, nullptr, st);

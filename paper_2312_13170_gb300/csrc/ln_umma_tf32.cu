@@ -29,7 +29,14 @@ ln_status umma_contract_tf32(int ek, const UmmaProblem &p, int terms, int bn, in
     }
 }
 
-ln_status umma_contract_sym_tf32(const UmmaProblem &p, int terms, int total, cudaStream_t st) {
+ln_status umma_contract_sym_tf32(const UmmaProblem &p, int terms, int bn, int total, cudaStream_t st) {
+    if (bn == 256) {
+        switch (terms) {
+            case 1: return launch<1, 256, 0, EK_SYM, 0, 1>(&p, nullptr, nullptr, nullptr, total, nullptr, st);
+            case 2: return launch<2, 256, 0, EK_SYM, 0, 1>(&p, nullptr, nullptr, nullptr, total, nullptr, st);
+            default: return fail(LN_ERR_INVALID_VALUE, "unsupported TF32 term count %d", terms);
+        }
+    }
     switch (terms) {
         case 1: return launch<1, 128, 0, EK_SYM, 0, 1>(&p, nullptr, nullptr, nullptr, total, nullptr, st);
         case 2: return launch<2, 128, 0, EK_SYM, 0, 1>(&p, nullptr, nullptr, nullptr, total, nullptr, st);
