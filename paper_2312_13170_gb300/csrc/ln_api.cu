@@ -1670,41 +1670,65 @@ ln_status ln_gemm_chain_bwd(int ni, int nj, int nk, int nl, const float *A, cons
     char *pk = p.c.px;
     // three independent branches: BC = B C (nk x nl), dA = G BC^T;
     // GCt = G C^T (ni x nj), dB = A^T GCt; T = A B (ni x nj), dC = T^T G.
-    // When the first two branches' contractions fit on the GPU side by side,
-    // the GCt branch runs on a second stream (its own pack and split areas).
-    auto branch_b = [&](char *area, const SplitArea &sa, cudaStream_t s) -> ln_status {
-        LN_TRY(contract_into(ni, nj, nl, {G, nl, 0}, {C, nl, 1}, epi_store(ni, nj, 1.0f, p.GCt, nj), form, prec, area,
-                             sa, s));
-        return contract_into(nk, nj, ni, {A, nk, 1}, {p.GCt, nj, 0}, epi_store(nk, nj, 1.0f, dB, nj), form, prec, area,
-                             sa, s);
+    // The six contractions (M, N, K):
+    auto c_T = [&](char *a, const SplitArea &sa, cudaStream_t s) {
+        return contract_into(ni, nj, nk, {A, nk, 0}, {B, nj, 0}, epi_store(ni, nj, 1.0f, p.T, nj), form, prec, a, sa,
+                             s);
     };
-    auto branches_ac = [&]() -> ln_status {
-        LN_TRY(contract_into(nk, nl, nj, {B, nj, 0}, {C, nl, 0}, epi_store(nk, nl, 1.0f, p.BC, nl), form, prec, pk,
-                             p.split, st));
-        LN_TRY(contract_into(ni, nk, nl, {G, nl, 0}, {p.BC, nl, 1}, epi_store(ni, nk, 1.0f, dA, nk), form, prec, pk,
-                             p.split, st));
-        LN_TRY(contract_into(ni, nj, nk, {A, nk, 0}, {B, nj, 0}, epi_store(ni, nj, 1.0f, p.T, nj), form, prec, pk,
-                             p.split, st));
-        return contract_into(nj, nl, ni, {p.T, nj, 1}, {G, nl, 0}, epi_store(nj, nl, 1.0f, dC, nl), form, prec, pk,
-                             p.split, st);
+    auto c_dC = [&](char *a, const SplitArea &sa, cudaStream_t s) {
+        return contract_into(nj, nl, ni, {p.T, nj, 1}, {G, nl, 0}, epi_store(nj, nl, 1.0f, dC, nl), form, prec, a, sa,
+                             s);
     };
+    auto c_BC = [&](char *a, const SplitArea &sa, cudaStream_t s) {
+        return contract_into(nk, nl, nj, {B, nj, 0}, {C, nl, 0}, epi_store(nk, nl, 1.0f, p.BC, nl), form, prec, a, sa,
+                             s);
+    };
+    auto c_dA = [&](char *a, const SplitArea &sa, cudaStream_t s) {
+        return contract_into(ni, nk, nl, {G, nl, 0}, {p.BC, nl, 1}, epi_store(ni, nk, 1.0f, dA, nk), form, prec, a, sa,
+                             s);
+    };
+    auto c_GCt = [&](char *a, const SplitArea &sa, cudaStream_t s) {
+        return contract_into(ni, nj, nl, {G, nl, 0}, {C, nl, 1}, epi_store(ni, nj, 1.0f, p.GCt, nj), form, prec, a, sa,
+                             s);
+    };
+    auto c_dB = [&](char *a, const SplitArea &sa, cudaStream_t s) {
+        return contract_into(nk, nj, ni, {A, nk, 1}, {p.GCt, nj, 0}, epi_store(nk, nj, 1.0f, dB, nj), form, prec, a, sa,
+                             s);
+    };
+    // When pairs of them fit on the GPU side by side, they run as three rounds
+    // on two streams -- (T | GCt), (BC | dB), (dA | dC), dC waiting for T by an
+    // event -- so the longest chain is three contractions, not four; the second
+    // stream has its own pack and split areas.
     SideStream *ss = nullptr;
     if (p.px2) {
         const int P = prec_terms(prec);
         const long long sms = sm_count();
-        if (contract_work(nk, nl, nj, P) + contract_work(ni, nj, nl, P) <= sms &&
-            contract_work(ni, nk, nl, P) + contract_work(nk, nj, ni, P) <= sms)
+        if (contract_work(ni, nj, nk, P) + contract_work(ni, nj, nl, P) <= sms &&
+            contract_work(nk, nl, nj, P) + contract_work(nk, nj, ni, P) <= sms &&
+            contract_work(ni, nk, nl, P) + contract_work(nj, nl, ni, P) <= sms)
             ss = side_stream(st);
     }
     if (!ss) {
-        LN_TRY(branches_ac());
-        return branch_b(pk, p.split, st);
+        LN_TRY(c_BC(pk, p.split, st));
+        LN_TRY(c_dA(pk, p.split, st));
+        LN_TRY(c_T(pk, p.split, st));
+        LN_TRY(c_dC(pk, p.split, st));
+        LN_TRY(c_GCt(pk, p.split, st));
+        return c_dB(pk, p.split, st);
     }
     LN_CUDA_TRY(cudaEventRecord(ss->fork, st));
     LN_CUDA_TRY(cudaStreamWaitEvent(ss->s, ss->fork, 0));
-    const ln_status sb = branch_b(p.px2, p.split2, ss->s);
+    // main stream: T, then BC, dA; second stream: GCt, dB, then dC once T is done
+    ln_status sa = c_T(pk, p.split, st);
+    if (sa == LN_SUCCESS) sa = cudaEventRecord(ss->mid_a, st) == cudaSuccess ? LN_SUCCESS : fail(LN_ERR_CUDA, "event");
+    ln_status sb = c_GCt(p.px2, p.split2, ss->s);
+    if (sb == LN_SUCCESS) sb = c_dB(p.px2, p.split2, ss->s);
+    if (sb == LN_SUCCESS && sa == LN_SUCCESS)
+        sb = cudaStreamWaitEvent(ss->s, ss->mid_a, 0) == cudaSuccess ? LN_SUCCESS : fail(LN_ERR_CUDA, "event wait");
+    if (sb == LN_SUCCESS && sa == LN_SUCCESS) sb = c_dC(p.px2, p.split2, ss->s);
+    if (sa == LN_SUCCESS) sa = c_BC(pk, p.split, st);
+    if (sa == LN_SUCCESS) sa = c_dA(pk, p.split, st);
     LN_CUDA_TRY(cudaEventRecord(ss->join, ss->s));
-    const ln_status sa = branches_ac();
     LN_CUDA_TRY(cudaStreamWaitEvent(st, ss->join, 0));  // joined whatever either branch returned
     LN_TRY(sb);
     return sa;
