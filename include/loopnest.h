@@ -165,6 +165,12 @@ ln_status ln_timing_read(const char *family, double *total_ms /*host*/, int *lau
  *              block of D (chain) or C (GEMM) into the operand stages once its
  *              MMAs are done, so the epilogue stores E at once and reads D or
  *              C from shared memory;
+ *   "stage_out" 0 or 1 (default 1): the last 256-wide tile of each CTA of a
+ *              contraction with the packing epilogue (the chain's T, 3mm's E
+ *              and F) builds its packed output in the freed operand stages and
+ *              writes it with bulk copies (4 KiB per warp, block and term)
+ *              instead of 16-byte stores from registers; results are
+ *              bit-identical;
  *   "sym_wide" 0, 1 or 2 (default 0): output tiles of 128 x 256 instead of
  *              128 x 128 over the lower triangle of single symmetric
  *              contractions (covariance, correlation, SYRK/SYR2K); 2 takes them

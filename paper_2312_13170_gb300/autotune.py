@@ -15,7 +15,7 @@ for general contractions, ``chunk_kt`` in {1, 2} (k tiles accumulated in
 tensor memory before promotion to FP32 registers), ``pair`` in {0, 1} (CTA
 pairs with tcgen05.mma.cta_group::2), ``stage_beta`` in {0, 1}, ``stream_k``
 in {0, 1, 2} (never, always, automatic), ``sym_wide`` in {0, 1, 2} (128 x 256
-symmetric tiles: never, always, automatic), and for the FP32 tiled form ``simt_exact`` in {0, 1}. Batched
+symmetric tiles: never, always, automatic), ``stage_out`` in {0, 1}, and for the FP32 tiled form ``simt_exact`` in {0, 1}. Batched
 SYRK/SYR2K are tuned over ``chunk_kt`` (their 128 x 128 symmetric tiles and
 stage count are fixed by the kernel's shared-memory plan). Only
 configurations that keep the library's accuracy gate are offered; every one
@@ -34,7 +34,7 @@ import numpy as np
 
 # tile_n 0 is the library's automatic width (256, or 128 for problems whose
 # 256-wide tiles would fill at most half the SMs)
-DEFAULT = {"tile_n": 0, "chunk_kt": 2, "pair": 1, "stage_beta": 1, "stream_k": 2, "simt_exact": 1, "sym_wide": 0}
+DEFAULT = {"tile_n": 0, "chunk_kt": 2, "pair": 1, "stage_beta": 1, "stream_k": 2, "simt_exact": 1, "sym_wide": 0, "stage_out": 1}
 
 
 def _c(**kw):
@@ -42,7 +42,7 @@ def _c(**kw):
 
 
 _GENERAL = [_c(), _c(tile_n=256), _c(tile_n=128), _c(chunk_kt=1), _c(pair=0), _c(stage_beta=0), _c(stream_k=1),
-            _c(stream_k=0)]
+            _c(stream_k=0), _c(stage_out=0)]
 _SYM = [_c(), _c(chunk_kt=1), _c(stream_k=1), _c(stream_k=0), _c(sym_wide=2), _c(sym_wide=1, stream_k=1)]
 CANDIDATES = {
     "gemm": _GENERAL,

@@ -204,6 +204,7 @@ int tune_split_k();       // 1: split the K range of contractions with few outpu
 int tune_stream_k();      // 1: stream-K for general contractions with fewer tiles than SMs
 int tune_pair();          // 1: CTA pairs sharing the column operand (UmmaProblem::pair)
 int tune_stage_beta();    // UmmaProblem::stage_beta
+int tune_stage_out();     // UmmaProblem::stage_out
 int tune_sym_wide();      // umma_sym_tile_n: 0 never, 1 always, 2 automatic
 
 // ln_umma.cu: tcgen05 contraction over packed operands
@@ -253,10 +254,14 @@ struct UmmaProblem {
     // TF32 operands: tcgen05.mma kind::tf32, 32-K tiles. The host sets it with
     // k-tile counts in 64-K blocks; umma_contract doubles them (and halves the
     // term count) before the launch. A packing epilogue writes TF32 blocks.
-    // (pair and stage_beta are short so that the problem keeps the size and
-    // layout the epilogue registers were tuned with: a larger struct moved
-    // registers into spills in the E/F epilogue)
-    int tf32;
+    // (the flags are short so that the problem keeps the size and layout the
+    // epilogue registers were tuned with: a larger struct moved registers into
+    // spills in the E/F epilogue)
+    short tf32;
+    // the "stage_out" knob: a CTA's last 256-wide tile with the packing
+    // epilogue builds its packed output in the freed stage memory and writes it
+    // with bulk copies
+    short stage_out;
     EpiParams epi;
 };
 // True when LN_FAULT_INJECT=timeout is set in the environment (read per call).

@@ -82,6 +82,7 @@ ln_status umma_contract(const UmmaProblem &p0, int terms, cudaStream_t st, const
     UmmaProblem p = p0;
     p.pair = 0;
     p.stage_beta = tune_stage_beta();
+    p.stage_out = tune_stage_out();
     if (p.tf32) {
         // TF32 operands: `terms` counts the 16 KiB pieces of a 128 x 64 block
         // (two per TF32 term) and the k-tile counts are in such blocks; the

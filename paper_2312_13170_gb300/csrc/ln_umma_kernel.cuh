@@ -67,7 +67,8 @@ struct SchedSlot {
     int ghost;          // pairs: this CTA's tile lies outside the output (or above the diagonal):
                         // it only copies and releases its share of the pair's stages
     int dsmem;          // the CTA's last tile: once its MMAs are done the producer copies the tile's
-                        // block of the beta input (D or C) into the freed stage memory (dfull)
+                        // block of the beta input (D or C) into the freed stage memory (dfull);
+                        // packing epilogue: the tile's packed output is built there and bulk-stored
     UmmaProblem prob;
 };
 
@@ -411,6 +412,8 @@ struct Cfg {
     // 256-wide tiles only (on 128-wide ones, loading it after the mainloop
     // measured slower than the epilogue's own loads)
     static constexpr bool DSMEM_OK = BN == 256 && BM * BN * 4 <= STAGES * STAGE_BYTES;
+    // the packed image of a 256-wide tile (BN / 64 blocks of P terms) fits in the stage memory
+    static constexpr bool POUT_OK = BN == 256 && (BN / PK_K) * P * PK_TILE_BYTES <= STAGES * STAGE_BYTES;
     static_assert((EPW == 64 || EPW == 128) && NEPI <= 8, "epilogue width");
     static_assert(NACC <= MAX_NACC && STAGES >= 2, "tile configuration does not fit");
     static_assert(!REG_SPLIT || (128 * REG_LO + 32 * NEPI * REG_HI <= REG_LAUNCH * NTHREADS && REG_HI <= 256 &&
@@ -865,6 +868,11 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK, BN>(), PAIR>::NTHREADS, 1)
                     sl.qb = qb;
                 }
                 sl.dsmem = 0;
+                if constexpr (EK == EK_PACK && !BATCHED && !TF && C::POUT_OK) {
+                    // the last tile of a statically scheduled CTA: no later copy reuses the stages
+                    sl.dsmem = single.stage_out && t >= 0 && !queue && !sk && ksplit <= 1 && next >= total_tiles &&
+                               !sl.ghost;
+                }
                 if constexpr ((EK == EK_EF || EK == EK_GEMM) && !BATCHED && C::DSMEM_OK) {
                     // the last tile of a statically scheduled CTA, wholly inside an aligned output
                     const EpiParams &e = single.epi;
@@ -1237,6 +1245,47 @@ __global__ __launch_bounds__(Cfg<P, BN, epi_width<EK, BN>(), PAIR>::NTHREADS, 1)
             const EpiParams &e = pb.epi;
             if (!last) {
                 // another slice of this tile finishes it
+            } else if constexpr (EK == EK_PACK && !TF && C::POUT_OK) {
+                // row rloc of M tile mi; column j of the result is k = j of the packed operand
+                if (sl.dsmem) {
+                    // the tile's packed image in the freed stage memory, [block][term][row][128 B]
+                    // as in global memory; each warp then bulk-stores its 32 rows of each
+                    // (block, term): 4 KiB, contiguous on both sides
+                    char *img = reinterpret_cast<char *>(smem_raw + pad + CTL_BYTES);
+                    const int kb0 = col_base / PK_K;  // this warp's first block of the tile
+#pragma unroll
+                    for (int g = 0; g < EPW / 32; ++g) {
+                        char *blk = img + (size_t)(kb0 + g / 2) * P * PK_TILE_BYTES;
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc)
+                            store_chunk<P>(blk, rloc, (g & 1) * 4 + cc, &sum[g * 32 + cc * 8]);
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        char *gt = e.pack + (size_t)((long long)tr.mi * e.pack_kt + tr.ni * (BN / PK_K)) * P *
+                                                PK_TILE_BYTES;
+#pragma unroll
+                        for (int b = 0; b < EPW / PK_K; ++b)
+#pragma unroll
+                            for (int q = 0; q < P; ++q) {
+                                const size_t off = ((size_t)(kb0 + b) * P + q) * PK_TILE_BYTES + (size_t)quarter * 4096;
+                                bulk_s2g(gt + off, saddr(img + off), 4096u);
+                            }
+                        bulk_commit();
+                        bulk_wait<0>();
+                    }
+                    __syncwarp();
+                } else {
+#pragma unroll
+                    for (int g = 0; g < EPW / 32; ++g) {
+                        const int kt = (col0 + g * 32) / PK_K;  // 128 x 64 block of the packed operand
+                        char *tile0 = e.pack + (size_t)((long long)tr.mi * e.pack_kt + kt) * P * PK_TILE_BYTES;
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc)
+                            store_chunk<P>(tile0, rloc, (g & 1) * 4 + cc, &sum[g * 32 + cc * 8]);
+                    }
+                }
             } else if constexpr (EK == EK_PACK) {
                 // row rloc of M tile mi; column j of the result is k = j of the packed operand
 #pragma unroll

@@ -186,3 +186,37 @@ def test_stage_beta_bit_identical(api, shape):
     E_ref, F_ref = oracle.gemm_chain(d["A"][rows], d["B"], d["C"], d["D"][rows], d["alpha"], d["beta"])
     assert inputs.rel_fro(out[0][1][rows], F_ref) <= GATE
     assert inputs.rel_fro(out[0][2], oracle.gemm(g["A"], g["B"], g["C"], g["alpha"], g["beta"])) <= GATE
+
+
+@pytest.mark.parametrize("shape", [(2048, 2048, 2048, 2048), (1500, 1700, 900, 1100)])
+@pytest.mark.parametrize("pair", [0, 1])
+def test_stage_out_bit_identical(api, shape, pair):
+    """Building the packed intermediate (the chain's T, 3mm's E and F) of a
+    CTA's last 256-wide tile in the freed stage memory and bulk-storing it
+    changes how it reaches global memory, not the result. The second shape has
+    ragged row and column tiles; both take 256-wide tiles."""
+    d = inputs.chain_inputs(*shape, seed=46)
+    t = {k: dev(d[k]) for k in "ABCD"}
+    rng = np.random.default_rng(47)
+    ni, nj = shape[0], shape[1]
+    m3 = [rng.uniform(-1, 1, size=s).astype(np.float32) for s in ((ni, 600), (600, nj), (nj, 500), (500, 1100))]
+    t3 = [dev(x) for x in m3]
+    out = []
+    api.set_tuning("pair", pair)
+    try:
+        for on in (1, 0):
+            api.set_tuning("stage_out", on)
+            E, F = api.gemm_chain(t["A"], t["B"], t["C"], t["D"], d["alpha"], d["beta"], prec="3xbf16")
+            G = api.three_mm(*t3, prec="3xbf16")
+            api.stream_check()
+            out.append((host(E), host(F), host(G)))
+    finally:
+        api.set_tuning("stage_out", 1)
+        api.set_tuning("pair", 1)
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    rows = slice(0, 40)
+    E_ref, F_ref = oracle.gemm_chain(d["A"][rows], d["B"], d["C"], d["D"][rows], d["alpha"], d["beta"])
+    assert inputs.rel_fro(out[0][0][rows], E_ref) <= GATE and inputs.rel_fro(out[0][1][rows], F_ref) <= GATE
+    G_ref = oracle.three_mm(m3[0][rows], m3[1], m3[2], m3[3])
+    assert inputs.rel_fro(out[0][2][rows], G_ref) <= GATE
