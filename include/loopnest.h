@@ -2,9 +2,10 @@
  * libloopnest — GB300 (sm_103a) kernels for the loop nests that loop
  * internalization and array-reduction detection speed up
  * ("Experiences Building an MLIR-based SYCL Compiler", arXiv 2312.13170):
- * GEMM, a chain of two GEMMs (polybench 2mm), covariance, correlation, SYRK
- * and SYR2K, plus the vector-Jacobian products of the chain, covariance and
- * correlation.
+ * GEMM, a chain of two GEMMs (polybench 2mm), three chained products
+ * (polybench 3mm), covariance, correlation, SYRK and SYR2K (single and
+ * batched), modified Gram-Schmidt QR, plus the vector-Jacobian products of the
+ * chain, 3mm, covariance and correlation.
  *
  * Every operation exists in two forms:
  *   LN_FORM_PLAIN        one thread per output element, reading global memory
@@ -16,10 +17,10 @@
  *                        with work-group local memory (Sec. VI-C, Listing 6):
  *                        with LN_PREC_FP32 a shared-memory tiled FP32 SIMT
  *                        kernel; with a tensor-core precision, operands are
- *                        split into BF16 terms, packed in tcgen05 operand
- *                        tiles, copied into shared memory by the bulk-copy
- *                        (TMA) engine and multiplied by tcgen05.mma into
- *                        TMEM accumulators.
+ *                        split into BF16 or TF32 terms, packed in tcgen05
+ *                        operand tiles, copied into shared memory by the
+ *                        bulk-copy (TMA) engine and multiplied by
+ *                        tcgen05.mma into TMEM accumulators.
  *
  * Conventions shared by every entry point
  *  - Matrices are FP32, row-major; ld* are leading dimensions in elements
