@@ -237,7 +237,8 @@ def run_reference(args):
     line = {
         "metric": METRIC, "value": gflops, "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": WORKLOAD, "impl": "reference",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(WORKLOAD, parallelism=f"replicas x{ws}"), "impl": "reference",
         "cpu_baseline": {"value": gflops, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                          "sample": f"first {R} of {N} rows of E and F per step"},
         "e2e": {"value": gflops, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
