@@ -161,6 +161,11 @@ ln_status ln_timing_read(const char *family, double *total_ms /*host*/, int *lau
  *              M, N are multiples of its tile width, K of 8, and every operand
  *              and output row is 16-byte aligned; 0 always takes the general
  *              instance; results are bit-identical;
+ *   "simt_tile" 0, 64 or 128 (default 0): the CTA output tile of the FP32
+ *              tiled form; 0 takes 64 when the problem has at most as many
+ *              128-wide tiles as the device has SMs and at most twice as many
+ *              64-wide tiles, else 128;
+ *              both give the same exact-FP32 sums in the same k order;
  *   "stage_beta" 0 or 1 (default 1): the last 256-wide tile of each CTA of
  *              a general tensor-core contraction with beta != 0 copies its
  *              block of D (chain) or C (GEMM) into the operand stages once its

@@ -186,7 +186,7 @@ def timing_read(family: str):
 
 def set_tuning(key: str, value: int) -> None:
     """Set a process-wide knob: "chunk_kt", "tile_n", "pack_threads", "split_k", "stream_k", "pair",
-    "stage_beta", "stage_out", "sym_wide" (tensor-core engine), "simt_exact" (FP32 tiled form) or "gs_rows"
+    "stage_beta", "stage_out", "sym_wide" (tensor-core engine), "simt_exact", "simt_tile" (FP32 tiled form) or "gs_rows"
     (Gram-Schmidt panel); the values each takes are listed in loopnest.h."""
     _check(lib().ln_set_tuning(key.encode(), int(value)), "ln_set_tuning")
 

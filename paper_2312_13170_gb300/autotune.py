@@ -15,7 +15,8 @@ for general contractions, ``chunk_kt`` in {1, 2} (k tiles accumulated in
 tensor memory before promotion to FP32 registers), ``pair`` in {0, 1} (CTA
 pairs with tcgen05.mma.cta_group::2), ``stage_beta`` in {0, 1}, ``stream_k``
 in {0, 1, 2} (never, always, automatic), ``sym_wide`` in {0, 1, 2} (128 x 256
-symmetric tiles: never, always, automatic), ``stage_out`` in {0, 1}, and for the FP32 tiled form ``simt_exact`` in {0, 1}. Batched
+symmetric tiles: never, always, automatic), ``stage_out`` in {0, 1}, and for the FP32 tiled form ``simt_exact`` in {0, 1}
+and ``simt_tile`` in {0 (automatic), 64, 128}. Batched
 SYRK/SYR2K are tuned over ``chunk_kt`` (their 128 x 128 symmetric tiles and
 stage count are fixed by the kernel's shared-memory plan). Only
 configurations that keep the library's accuracy gate are offered; every one
@@ -34,7 +35,8 @@ import numpy as np
 
 # tile_n 0 is the library's automatic width (256, or 128 for problems whose
 # 256-wide tiles would fill at most half the SMs)
-DEFAULT = {"tile_n": 0, "chunk_kt": 2, "pair": 1, "stage_beta": 1, "stream_k": 2, "simt_exact": 1, "sym_wide": 0, "stage_out": 1}
+DEFAULT = {"tile_n": 0, "chunk_kt": 2, "pair": 1, "stage_beta": 1, "stream_k": 2, "simt_exact": 1, "sym_wide": 0, "stage_out": 1,
+           "simt_tile": 0}
 
 
 def _c(**kw):
@@ -55,8 +57,9 @@ CANDIDATES = {
     "syrk_batched": [_c(), _c(chunk_kt=1)],
     "syr2k_batched": [_c(), _c(chunk_kt=1)],
 }
-# the FP32 tiled form (every operation): its EXACT instance or the general one
-FP32_CANDIDATES = [_c(), _c(simt_exact=0)]
+# the FP32 tiled form (every operation): its EXACT instance or the general one,
+# and either tile width
+FP32_CANDIDATES = [_c(), _c(simt_exact=0), _c(simt_tile=64), _c(simt_tile=128)]
 
 
 def candidates(op, prec):

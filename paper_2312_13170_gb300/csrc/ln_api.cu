@@ -86,6 +86,7 @@ std::atomic<int> g_stream_k{2};
 std::atomic<int> g_pair{1};
 std::atomic<int> g_stage_beta{1};
 std::atomic<int> g_stage_out{1};
+std::atomic<int> g_simt_tile{0};
 std::atomic<int> g_sym_wide{0};
 std::atomic<int> g_simt_exact{1};
 }  // namespace
@@ -99,6 +100,7 @@ int tune_stream_k() { return g_stream_k.load(std::memory_order_relaxed); }
 int tune_pair() { return g_pair.load(std::memory_order_relaxed); }
 int tune_stage_beta() { return g_stage_beta.load(std::memory_order_relaxed); }
 int tune_stage_out() { return g_stage_out.load(std::memory_order_relaxed); }
+int tune_simt_tile() { return g_simt_tile.load(std::memory_order_relaxed); }
 int tune_sym_wide() { return g_sym_wide.load(std::memory_order_relaxed); }
 int tune_simt_exact() { return g_simt_exact.load(std::memory_order_relaxed); }
 
@@ -1027,6 +1029,12 @@ ln_status ln_set_tuning(const char *key, int value) {
         g_stage_beta.store(value);
         return LN_SUCCESS;
     }
+    if (strcmp(key, "simt_tile") == 0) {
+        if (value != 0 && value != 64 && value != 128)
+            return fail(LN_ERR_INVALID_VALUE, "simt_tile must be 0 (automatic), 64 or 128 (got %d)", value);
+        g_simt_tile.store(value);
+        return LN_SUCCESS;
+    }
     if (strcmp(key, "stage_out") == 0) {
         if (value != 0 && value != 1) return fail(LN_ERR_INVALID_VALUE, "stage_out must be 0 or 1 (got %d)", value);
         g_stage_out.store(value);
@@ -1073,6 +1081,7 @@ ln_status ln_get_tuning(const char *key, int *value) {
     else if (strcmp(key, "pair") == 0) *value = g_pair.load();
     else if (strcmp(key, "stage_beta") == 0) *value = g_stage_beta.load();
     else if (strcmp(key, "stage_out") == 0) *value = g_stage_out.load();
+    else if (strcmp(key, "simt_tile") == 0) *value = g_simt_tile.load();
     else if (strcmp(key, "sym_wide") == 0) *value = g_sym_wide.load();
     else if (strcmp(key, "simt_exact") == 0) *value = g_simt_exact.load();
     else return fail(LN_ERR_INVALID_VALUE, "unknown tuning key '%s'", key);

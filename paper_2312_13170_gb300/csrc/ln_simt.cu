@@ -1,8 +1,8 @@
 // Internalized FP32 form: the work-group tiling of loop internalization
 // (paper Sec. VI-C, Listing 6) mapped to a CTA. Each CTA owns a TB x TB output
-// tile (TB = 128, or 64 for problems whose 128-wide tiles would leave most SMs
-// idle); the inner k loop is tiled by TK (16 at TB = 128, 8 at 64), and each
-// k-tile of both operands is copied from global memory into shared memory by
+// tile (TB = 128, or 64 for problems whose 128-wide tiles would leave SMs idle
+// while their 64-wide tiles fit two to an SM); the inner k loop is tiled by TK
+// (16 at TB = 128, 8 at 64), and each k-tile of both operands is copied from global memory into shared memory by
 // 16-byte cp.async copies (4-byte ones, or zero fill, at ragged or unaligned
 // edges) into a ring of NST stages (3 at TB = 128, 4 at 64), so that NST - 1
 // k-tiles are in flight while one is consumed and a single barrier per k-tile
@@ -25,6 +25,7 @@
 namespace ln {
 
 int tune_simt_exact();  // ln_api.cu: the "simt_exact" knob
+int tune_simt_tile();   // ln_api.cu: the "simt_tile" knob (0 automatic, 64, 128)
 
 namespace {
 
@@ -496,12 +497,17 @@ ln_status launch_simt_tb(dim3 grid, int M, int N, int K, const SimtOperands &op,
 
 ln_status simt_contract(int M, int N, int K, const SimtOperands &op, const EpiParams &epi, cudaStream_t st) {
     const bool sym = epi.mode == EPI_SYM;
-    // 64-wide tiles when 128-wide ones would fill at most half the SMs
+    // 64-wide tiles when the 128-wide ones leave SMs idle (one tile per SM at
+    // most) and the 64-wide ones still fit two to an SM; otherwise the 8 x 8
+    // register blocks of the 128-wide tiles do more FFMAs per shared load
     auto tiles_of = [&](int tb) {
         const long long t = ceil_div(M, tb);
         return sym ? t * (t + 1) / 2 : t * ceil_div(N, tb);
     };
-    const int TB = 2 * tiles_of(128) <= sm_count() ? 64 : 128;
+    const int knob = tune_simt_tile();
+    const long long sms = sm_count();
+    const int TB = knob == 64 || knob == 128 ? knob
+                                             : (tiles_of(128) <= sms && tiles_of(64) <= 2 * sms ? 64 : 128);
     dim3 grid;
     if (sym) {
         grid = dim3((unsigned)tiles_of(TB));

@@ -223,3 +223,5 @@ def test_gramschmidt_validation(L):
     assert L.ln_set_tuning(b"sym_wide", 3) == 1
     assert L.ln_get_tuning(b"stage_out", ctypes.byref(v)) == 0 and v.value == 1
     assert L.ln_set_tuning(b"stage_out", 2) == 1
+    assert L.ln_get_tuning(b"simt_tile", ctypes.byref(v)) == 0 and v.value == 0
+    assert L.ln_set_tuning(b"simt_tile", 32) == 1 and L.ln_set_tuning(b"simt_tile", 1) == 1

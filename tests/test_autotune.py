@@ -39,7 +39,8 @@ def test_cache_roundtrip(tmp_path, monkeypatch):
 
 def test_candidates_respect_knob_domains():
     domains = {"tile_n": (0, 128, 256), "chunk_kt": (1, 2), "pair": (0, 1, 2), "stage_beta": (0, 1),
-               "stream_k": (0, 1, 2), "simt_exact": (0, 1), "sym_wide": (0, 1, 2), "stage_out": (0, 1)}
+               "stream_k": (0, 1, 2), "simt_exact": (0, 1), "sym_wide": (0, 1, 2), "stage_out": (0, 1),
+               "simt_tile": (0, 64, 128)}
     for op, cands in list(autotune.CANDIDATES.items()) + [("fp32", autotune.FP32_CANDIDATES)]:
         assert cands[0] == autotune.DEFAULT, op  # the library defaults are always a candidate
         for c in cands:

@@ -1,6 +1,7 @@
 """The internalized FP32 form (exact FFMA, cp.async-staged k-tiles in a
 four-stage shared-memory ring; 64- or 128-wide tiles; an EXACT instance
-specialised on whole tiles and aligned rows, the "simt_exact" knob).
+specialised on whole tiles and aligned rows, the "simt_exact" knob; the tile
+width is forced with the "simt_tile" knob).
 
 Every layout the library uses (GEMM A[i][k] B[k][j]; covariance A[k][i]
 B[k][j] with centring; SYRK A[i][k] B[j][k]; chain and 3mm intermediates) is
@@ -31,6 +32,7 @@ def api():
 
     yield a
     a.set_tuning("simt_exact", 1)
+    a.set_tuning("simt_tile", 0)
 
 
 def dev(x):
@@ -122,3 +124,26 @@ def test_chain_fp32(api):
     assert np.array_equal(E1, E0) and np.array_equal(F1, F0)
     E_ref, F_ref = oracle.gemm_chain(d["A"], d["B"], d["C"], d["D"], d["alpha"], d["beta"])
     assert inputs.rel_fro(E1, E_ref) <= GATE and inputs.rel_fro(F1, F_ref) <= GATE
+
+
+@pytest.mark.parametrize("M,N,K", [(1024, 1024, 512), (300, 517, 389), (2048, 2048, 64)])
+def test_tile_width_bit_identical(api, M, N, K):
+    """Each output is one FFMA chain over k in order, whatever the CTA tile:
+    64- and 128-wide tiles give the same bits, GEMM and symmetric outputs."""
+    g = inputs.gemm_inputs(M, N, K, seed=M + K)
+    d = inputs.sym_inputs(M, K, seed=N)
+    out = []
+    try:
+        for tb in (64, 128):
+            api.set_tuning("simt_tile", tb)
+            C = dev(g["C"])
+            api.gemm(dev(g["A"]), dev(g["B"]), C, g["alpha"], g["beta"], form="internalized", prec="fp32")
+            S = dev(d["C"])
+            api.syrk(dev(d["A"]), S, d["alpha"], d["beta"], fill="lower", form="internalized", prec="fp32")
+            api.stream_check()
+            out.append((host(C), host(S)))
+    finally:
+        api.set_tuning("simt_tile", 0)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert inputs.rel_fro(out[0][0], oracle.gemm(g["A"], g["B"], g["C"], g["alpha"], g["beta"])) <= GATE
+    assert inputs.rel_fro(out[0][1], oracle.syrk(d["A"], d["C"], d["alpha"], d["beta"], 1)) <= GATE
