@@ -112,14 +112,19 @@ def save(cache: dict, path=None) -> None:
     os.replace(tmp, path)
 
 
-def select(candidates, timer, reps=5):
+def select(candidates, timer, reps=5, margin=0.03):
     """Time every candidate with timer(config) -> seconds (median of `reps`)
-    and return (best_config, {index: median_seconds})."""
+    and return (best_config, {index: median_seconds}). The first candidate
+    (the library defaults) stays unless the fastest beats it by more than
+    `margin`, so that call-to-call noise does not pick an equivalent
+    configuration."""
     times = {}
     for i, cfg in enumerate(candidates):
         ts = sorted(timer(cfg) for _ in range(reps))
         times[i] = ts[len(ts) // 2]
     best = min(times, key=times.get)
+    if times[best] > (1.0 - margin) * times[0]:
+        best = 0
     return dict(candidates[best]), times
 
 

@@ -23,6 +23,18 @@ def test_select_picks_fastest_median():
     assert times == {0: 3.0, 1: 2.0, 2: 9.0}
 
 
+def test_select_keeps_defaults_within_margin():
+    cands = [{"tile_n": 0}, {"tile_n": 128}, {"tile_n": 256}]
+    cost = {0: 1.0, 128: 0.98, 256: 1.5}  # 2 % faster: within the 3 % margin
+    best, _ = autotune.select(cands, lambda c: cost[c["tile_n"]], reps=1)
+    assert best == {"tile_n": 0}
+    cost[128] = 0.96
+    best, _ = autotune.select(cands, lambda c: cost[c["tile_n"]], reps=1)
+    assert best == {"tile_n": 128}
+    best, _ = autotune.select(cands, lambda c: cost[c["tile_n"]], reps=1, margin=0.05)
+    assert best == {"tile_n": 0}
+
+
 def test_cache_roundtrip(tmp_path, monkeypatch):
     path = str(tmp_path / "tune.json")
     monkeypatch.setenv("LN_AUTOTUNE_CACHE", path)
