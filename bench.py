@@ -327,10 +327,14 @@ def run_own(args):
         return sum(s.elapsed_time(e) for s, e in evs) / max(len(graphs), 1)
 
     def timed(nsteps, warm, form, prec, with_timing=False):
-        """Steps replay their own graphs. With timing, a second timed pass
-        replays graphs captured with the library's launch-timing event nodes
-        (which cost ~20 us of graph launch overlap per step, so the step time
-        comes from the first pass and only the kernel durations from this one)."""
+        """Steps replay their own graphs. With timing, two more timed passes
+        replay graphs captured with the library's launch-timing event nodes
+        (the step time comes from the first pass, the kernel durations from
+        these): "span" (timing mode 2: the chain's two contractions, launched
+        back to back with programmatic overlap, share one event pair, so the
+        second starts as it does in the timed step) and "bracketed" (mode 1:
+        an event pair around every launch, which delays the second
+        contraction until the first has finished)."""
         for _ in range(warm):
             step(form, prec)
         api.stream_check()
@@ -340,18 +344,17 @@ def run_own(args):
         ms = replay_timed(graphs)
         del graphs
         fams = {}
-        if with_timing:
-            api.timing_enable(True)
+        for tag, mode in (("span", 2), ("bracketed", 1)) if with_timing else ():
+            api.timing_enable(mode)
             for fam in ("umma", "pack", "simt", "plain", "stats"):
                 api.timing_read(fam)
             graphs = graph_steps(nsteps, form, prec)  # event nodes are captured here
-            api.timing_enable(False)
+            api.timing_enable(0)
             # each graph's event nodes are re-recorded by the timed replay below
             # (overwriting the upload replay's), then read once
             ms_t = replay_timed(graphs)
-            for fam in ("umma", "pack"):
-                fams[fam] = api.timing_read(fam)
-            fams["step_ms_with_events"] = ms_t
+            fams[tag] = {fam: api.timing_read(fam) for fam in ("umma", "pack")}
+            fams[tag]["step_ms_with_events"] = ms_t
             del graphs
         api.stream_check()
         return ms, launches, fams
@@ -404,8 +407,10 @@ def run_own(args):
     e2e_err = float((hostE - E_int.cpu()).abs().max())  # zero-copy result equals the device-resident one
 
     bf16_peak, hbm, peak_src = peaks()
-    umma_ms, umma_n = fams.get("umma", (0.0, 0))
+    span, brk = fams.get("span", {}), fams.get("bracketed", {})
+    umma_ms, umma_n = span.get("umma", (0.0, 0))
     achieved = FLOPS_PER_UMMA / (umma_ms / umma_n / 1e3) / 1e12 if umma_n else None
+    brk_ms, brk_n = brk.get("umma", (0.0, 0))
     peak = bf16_peak / PRODUCTS
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
@@ -425,10 +430,16 @@ def run_own(args):
                      "kernel": "k_umma<2,0> (tcgen05 3xBF16 contraction)",
                      "peak_note": f"{peak_src} bf16 burst {bf16_peak} TFLOP/s / {PRODUCTS} products",
                      "launches": umma_n, "ms_per_launch": (umma_ms / umma_n) if umma_n else None,
-                     "pack_ms_per_step": fams.get("pack", (0.0, 0))[0] / max(args.steps, 1),
-                     "timing_pass": "second timed pass of the same steps, graphs captured with the library's "
-                                    "per-launch event nodes",
-                     "timing_pass_ms_per_step": fams.get("step_ms_with_events")},
+                     "pack_ms_per_step": span.get("pack", (0.0, 0))[0] / max(args.steps, 1),
+                     "timing_pass": "timed pass of the same steps, graphs captured with the library's launch "
+                                    "event nodes in span mode: one pair around each step's two back-to-back "
+                                    "contractions (ms_per_launch = span / 2), one pair around each other launch",
+                     "timing_pass_ms_per_step": span.get("step_ms_with_events"),
+                     "bracketed": {"ms_per_launch": (brk_ms / brk_n) if brk_n else None, "launches": brk_n,
+                                   "frac": (FLOPS_PER_UMMA / (brk_ms / brk_n / 1e3) / 1e12 / peak) if brk_n else None,
+                                   "timing_pass_ms_per_step": brk.get("step_ms_with_events"),
+                                   "note": "an event pair around every launch: the second contraction waits for "
+                                           "the first to finish"}},
         "e2e": {"value": FLOPS / (ms_e2e / 1e3) / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
                 "path": "ln_gemm_chain on pinned host buffers (kernels read A..D and write E, F over the host link)",

@@ -128,6 +128,14 @@ ln_status ln_stream_check(void *stream);
  * into a CUDA graph get external event-record nodes, so their times are those
  * of the latest replay of the graph (read after replaying each captured graph
  * once). Enabling and reading must not happen during capture. Not thread-safe.
+ * ln_timing_enable(on): 0 off; 1 one event pair per launch; 2 spans: launches
+ * of one family that the library issues back to back on one stream with
+ * programmatic launch overlap (the two contractions of ln_gemm_chain's
+ * tensor-core path) share one event pair, so that no event node sits between
+ * them, and count as that many launches (an event between two such launches
+ * delays the second until the first has finished, a few microseconds more
+ * per launch); every other launch keeps its own pair. Other values:
+ * LN_ERR_INVALID_VALUE.
  */
 long long ln_launch_count(void);
 ln_status ln_timing_enable(int on);

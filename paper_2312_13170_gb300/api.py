@@ -171,9 +171,11 @@ def launch_count() -> int:
     return int(lib().ln_launch_count())
 
 
-def timing_enable(on: bool = True) -> None:
-    """Bracket every library kernel launch with CUDA events on its stream."""
-    _check(lib().ln_timing_enable(1 if on else 0), "ln_timing_enable")
+def timing_enable(on=True) -> None:
+    """Bracket library kernel launches with CUDA events on their streams: False
+    or 0 off, True or 1 one event pair per launch, 2 spans (back-to-back
+    launches with programmatic overlap share one pair; see loopnest.h)."""
+    _check(lib().ln_timing_enable(int(on)), "ln_timing_enable")
 
 
 def timing_read(family: str):

@@ -35,15 +35,44 @@ ln_status check_launch(const char *what) {
 }
 
 // ------------------------------------------------------------------ launch accounting
+void record_event(cudaEvent_t e, cudaStream_t st);
+
+// Alive around launches that the library issues back to back on one stream
+// (see the definition below).
+struct SpanHold {
+    SpanHold();
+    ~SpanHold();
+    SpanHold(const SpanHold &) = delete;
+    SpanHold &operator=(const SpanHold &) = delete;
+};
+
 namespace {
+// One timed run: a start and a stop event around `launches` kernel launches.
+struct TimedRun {
+    cudaEvent_t start = nullptr, stop = nullptr;
+    int launches = 0;
+};
 struct TimingState {
-    bool on = false;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[FAM_COUNT];
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
+    int mode = 0;  // 0 off, 1 every launch, 2 spans (see ln_timing_enable)
+    std::vector<TimedRun> pending[FAM_COUNT];
+    std::vector<TimedRun> pool;
+    int hold = 0;  // SpanHold scopes alive
+    // a span whose stop event is not recorded yet: the last launch of family
+    // `open_f` on stream `open_st`, inside a SpanHold
+    bool open = false;
+    Family open_f = FAM_UMMA;
+    cudaStream_t open_st = nullptr;
+    int open_slot = -1;
 };
 TimingState g_timing;
 std::atomic<long long> g_launches{0};
 const char *const kFamilies[FAM_COUNT] = {"umma", "pack", "simt", "plain", "stats"};
+
+void close_span() {
+    if (!g_timing.open) return;
+    g_timing.open = false;
+    record_event(g_timing.pending[g_timing.open_f][g_timing.open_slot].stop, g_timing.open_st);
+}
 }  // namespace
 
 // Inside stream capture a plain event record is only a dependency marker; an
@@ -58,21 +87,52 @@ void record_event(cudaEvent_t e, cudaStream_t st) {
 
 LaunchScope::LaunchScope(Family fam, cudaStream_t s) : slot(-1), st(s), f(fam) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (!g_timing.on) return;
-    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (!g_timing.mode) return;
+    if (g_timing.open) {
+        if (g_timing.open_f == f && g_timing.open_st == st) {
+            // the previous launch on this stream was of the same family, inside
+            // a SpanHold: this one joins its span, with no event between them
+            g_timing.open = false;
+            slot = g_timing.open_slot;
+            ++g_timing.pending[f][slot].launches;
+            return;
+        }
+        close_span();
+    }
+    TimedRun r;
     if (!g_timing.pool.empty()) {
-        ev = g_timing.pool.back();
+        r = g_timing.pool.back();
         g_timing.pool.pop_back();
-    } else if (cudaEventCreate(&ev.first) != cudaSuccess || cudaEventCreate(&ev.second) != cudaSuccess) {
+    } else if (cudaEventCreate(&r.start) != cudaSuccess || cudaEventCreate(&r.stop) != cudaSuccess) {
         return;
     }
-    record_event(ev.first, st);
-    g_timing.pending[f].push_back(ev);
+    r.launches = 1;
+    record_event(r.start, st);
+    g_timing.pending[f].push_back(r);
     slot = (int)g_timing.pending[f].size() - 1;
 }
 
 LaunchScope::~LaunchScope() {
-    if (slot >= 0) record_event(g_timing.pending[f][slot].second, st);
+    if (slot < 0) return;
+    if (g_timing.mode == 2 && g_timing.hold > 0) {  // the next launch may join
+        g_timing.open = true;
+        g_timing.open_f = f;
+        g_timing.open_st = st;
+        g_timing.open_slot = slot;
+        return;
+    }
+    record_event(g_timing.pending[f][slot].stop, st);
+}
+
+// Marks launches that the library issues back to back on one stream with
+// programmatic launch overlap (the chain's two contractions): in span mode
+// they share one event pair, since an event recorded between them would
+// serialise the second launch behind the first's last CTA. Only for launches
+// on a single stream: a span left open on a forked stream would be closed
+// after that stream's join.
+SpanHold::SpanHold() { ++g_timing.hold; }
+SpanHold::~SpanHold() {
+    if (--g_timing.hold == 0) close_span();
 }
 
 // ------------------------------------------------------------------ tuning knobs
@@ -1090,7 +1150,9 @@ ln_status ln_get_tuning(const char *key, int *value) {
 
 ln_status ln_timing_enable(int on) {
     clear_error();
-    g_timing.on = on != 0;
+    if (on < 0 || on > 2) return fail(LN_ERR_INVALID_VALUE, "timing mode must be 0, 1 or 2 (got %d)", on);
+    close_span();
+    g_timing.mode = on;
     return LN_SUCCESS;
 }
 
@@ -1103,13 +1165,14 @@ ln_status ln_timing_read(const char *family, double *total_ms, int *launches) {
     if (f < 0) return fail(LN_ERR_INVALID_VALUE, "unknown kernel family '%s'", family);
     double total = 0.0;
     int n = 0;
-    for (auto &ev : g_timing.pending[f]) {
-        LN_CUDA_TRY(cudaEventSynchronize(ev.second));
+    close_span();
+    for (auto &r : g_timing.pending[f]) {
+        LN_CUDA_TRY(cudaEventSynchronize(r.stop));
         float ms = 0.0f;
-        LN_CUDA_TRY(cudaEventElapsedTime(&ms, ev.first, ev.second));
+        LN_CUDA_TRY(cudaEventElapsedTime(&ms, r.start, r.stop));
         total += ms;
-        ++n;
-        g_timing.pool.push_back(ev);
+        n += r.launches;
+        g_timing.pool.push_back(r);
     }
     g_timing.pending[f].clear();
     *total_ms = total;
@@ -1254,6 +1317,7 @@ ln_status ln_gemm_chain(int ni, int nj, int nk, int nl, float alpha, const float
     apply_split(g1, p.s1);
     g1.bn = p.g1.bn;
     bool side_done = false;
+    SpanHold hold;  // GEMM2 follows GEMM1 on this stream with programmatic overlap
     LN_TRY(umma_contract(g1, P, st, try_side ? &side : nullptr, &side_done));
     if (try_side && !side_done) LN_TRY(pack_operands(ps + 2, 1, P, st));
     UmmaProblem g2{};

@@ -224,4 +224,7 @@ def test_gramschmidt_validation(L):
     assert L.ln_get_tuning(b"stage_out", ctypes.byref(v)) == 0 and v.value == 1
     assert L.ln_set_tuning(b"stage_out", 2) == 1
     assert L.ln_get_tuning(b"simt_tile", ctypes.byref(v)) == 0 and v.value == 0
+    # launch timing modes: 0 off, 1 every launch, 2 spans
+    assert L.ln_timing_enable(3) == 1 and L.ln_timing_enable(-1) == 1
+    assert L.ln_timing_enable(2) == 0 and L.ln_timing_enable(0) == 0
     assert L.ln_set_tuning(b"simt_tile", 32) == 1 and L.ln_set_tuning(b"simt_tile", 1) == 1
