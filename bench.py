@@ -458,6 +458,7 @@ def run_own(args):
         suite_lines(SUITE_MODES, ALL_WORKLOADS, 5, records.append)
         line["suite"] = suite_summary(records)
         line["suite_seconds"] = round(time.perf_counter() - t_suite, 1)
+        line["probes"] = peak_probes(api, bf16_peak, hbm)
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu, R, E_rows, F_rows = cpu_sample(d, args.cpu_seconds)
         line["cpu_baseline"] = cpu
@@ -824,6 +825,46 @@ def fp32_simt_peak():
     except Exception:
         mhz = 2070.0
     return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def peak_probes(api, bf16_peak, hbm):
+    """The library's peak probes on this GPU (median of 5 event-timed launches
+    each, after one warm-up launch): tcgen05 BF16 and TF32 MMA issue loops,
+    FFMA chains and a 1 GiB streaming copy. Context for the roofline
+    denominators above, which stay the measured copy and cuBLAS figures."""
+    import torch
+
+    def rate(kind, iters, src=None, dst=None):
+        api.peak_probe(kind, iters, src, dst)
+        torch.cuda.synchronize()
+        out = []
+        for _ in range(5):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            work = api.peak_probe(kind, iters, src, dst)
+            e.record()
+            e.synchronize()
+            out.append(work / (s.elapsed_time(e) / 1e3))
+        return sorted(out)[2]
+
+    err = torch.zeros(4, dtype=torch.int32, device="cuda")
+    bf16 = rate("mma_bf16", 16384, dst=err) / 1e12
+    tf32 = rate("mma_tf32", 16384, dst=err) / 1e12
+    timed_out = int(err[0])
+    ffma = rate("ffma", 4096, dst=torch.zeros(1, device="cuda")) / 1e12
+    src = torch.empty(1 << 28, device="cuda").fill_(1.0)  # 1 GiB each way
+    dst = torch.empty_like(src)
+    copy = rate("copy", 0, src, dst) / 1e9
+    del src, dst
+    api.stream_check()
+    return {"mma_bf16_tflops": bf16, "mma_tf32_tflops": tf32, "ffma_tflops": ffma, "copy_gbs": copy,
+            "mma_timed_out": timed_out,
+            "vs_denominators": {"mma_bf16 / measured cuBLAS bf16": bf16 / bf16_peak,
+                                "mma_tf32 / (measured cuBLAS bf16 x 1.1/2.25)": tf32 / (bf16_peak * TF32_RATIO),
+                                "ffma / (SMs x 128 lanes x 2 x max SM clock)": ffma / fp32_simt_peak(),
+                                "copy / measured copy": copy / hbm},
+            "kernels": "k_peak_mma<TF> (one CTA per SM, M=128 N=256, operands in shared memory), k_peak_ffma, "
+                       "k_peak_copy (ln_peak_probe)"}
 
 
 def main():

@@ -142,6 +142,32 @@ ln_status ln_timing_enable(int on);
 ln_status ln_timing_read(const char *family, double *total_ms /*host*/, int *launches /*host*/);
 
 /*
+ * Peak probes: the roofline denominators measured on this device. The paper
+ * has no counterpart (its evaluation reports speedups, not fractions of a
+ * peak); these exist so that a kernel's achieved rate can be set against what
+ * the same GPU does on a loop that does nothing but that one kind of work.
+ * Each call launches one kernel on `stream` and returns at once; *work
+ * receives the algorithmic work of that launch (flops, or bytes read plus
+ * bytes written), which the caller divides by the launch's CUDA-event time.
+ *   LN_PEAK_MMA_BF16, LN_PEAK_MMA_TF32: one CTA per SM issues 4 * iters
+ *     tcgen05.mma (M = 128, N = 256, K = 16 BF16 or 8 TF32 elements) on
+ *     operand tiles resident in its shared memory, accumulating in TMEM.
+ *     dst: a device word (4 bytes, bytes >= 4) that the call zeroes and the
+ *     kernel sets to 1 if its bounded wait for the MMAs (2 s) ran out.
+ *     iters in [1, 2^20].
+ *   LN_PEAK_FFMA: 8 CTAs of 256 threads per SM, each thread 128 * iters FP32
+ *     FFMAs in 8 independent chains; dst: a 4-byte device sink (never
+ *     written for these inputs); iters in [1, 2^20].
+ *   LN_PEAK_COPY: dst[0, bytes) = src[0, bytes) with 16-byte loads and
+ *     stores; both 16-byte aligned, bytes a positive multiple of 16, the
+ *     ranges disjoint (LN_ERR_ALIASING otherwise); iters unused.
+ * Bad arguments give LN_ERR_INVALID_VALUE before anything is launched.
+ */
+typedef enum { LN_PEAK_MMA_BF16 = 0, LN_PEAK_MMA_TF32 = 1, LN_PEAK_FFMA = 2, LN_PEAK_COPY = 3 } ln_peak_kind;
+ln_status ln_peak_probe(int kind, long long iters, const void *src, void *dst, long long bytes,
+                        double *work /*host*/, void *stream);
+
+/*
  * Tuning knobs of the tensor-core engine, process-wide (the autotuner in the
  * Python package picks them per problem class). Keys:
  *   "chunk_kt" 1 or 2 (default 2): k tiles of 64 accumulated in tensor memory

@@ -57,6 +57,7 @@ _SIGS = {
     "ln_launch_count": (ctypes.c_longlong, []),
     "ln_timing_enable": (_I, [_I]),
     "ln_timing_read": (_I, [ctypes.c_char_p, _P, _P]),
+    "ln_peak_probe": (_I, [_I, ctypes.c_longlong, _P, _P, ctypes.c_longlong, _P, _P]),
     "ln_set_tuning": (_I, [ctypes.c_char_p, _I]),
     "ln_get_tuning": (_I, [ctypes.c_char_p, _P]),
     "ln_gemm_workspace_size": (_I, [_I, _I, _I, _I, _I, _P]),
@@ -197,6 +198,23 @@ def get_tuning(key: str) -> int:
     v = ctypes.c_int(0)
     _check(lib().ln_get_tuning(key.encode(), ctypes.byref(v)), "ln_get_tuning")
     return int(v.value)
+
+
+PEAK_KINDS = {"mma_bf16": 0, "mma_tf32": 1, "ffma": 2, "copy": 3}
+
+
+def peak_probe(kind, iters=1, src=None, dst=None, stream=None) -> float:
+    """Launch one peak probe ("mma_bf16", "mma_tf32", "ffma" or "copy"; see
+    ln_peak_probe in loopnest.h) on the stream and return its algorithmic work
+    (flops, or bytes read plus written). `dst` is the probe's error word or
+    sink (MMA, FFMA) or the copy's destination; `src` the copy's source."""
+    work = ctypes.c_double(0.0)
+    nbytes = 0 if dst is None else dst.numel() * dst.element_size()
+    if src is not None and src.numel() * src.element_size() < nbytes:
+        raise ValueError("the copy probe's source is smaller than its destination")
+    _check(lib().ln_peak_probe(_enum(PEAK_KINDS, kind, "probe"), int(iters), _ptr(src), _ptr(dst), nbytes,
+                               ctypes.byref(work), _stream(stream)), "ln_peak_probe")
+    return float(work.value)
 
 
 def stream_check(stream=None):

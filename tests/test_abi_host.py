@@ -227,4 +227,17 @@ def test_gramschmidt_validation(L):
     # launch timing modes: 0 off, 1 every launch, 2 spans
     assert L.ln_timing_enable(3) == 1 and L.ln_timing_enable(-1) == 1
     assert L.ln_timing_enable(2) == 0 and L.ln_timing_enable(0) == 0
+    # peak probes: bad arguments are refused before anything is launched
+    w = ctypes.c_double(1.0)
+    probe = L.ln_peak_probe
+    probe.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
+                      ctypes.c_void_p, ctypes.c_void_p]
+    assert probe(9, 1, None, None, 0, ctypes.byref(w), None) == 1 and w.value == 0.0
+    assert probe(0, 0, None, ctypes.c_void_p(256), 4, ctypes.byref(w), None) == 1  # iters < 1
+    assert probe(1, 1 << 21, None, ctypes.c_void_p(256), 4, ctypes.byref(w), None) == 1  # iters > 2^20
+    assert probe(0, 8, None, None, 4, ctypes.byref(w), None) == 1  # no error word
+    assert probe(2, 8, None, ctypes.c_void_p(258), 4, ctypes.byref(w), None) == 1  # unaligned sink
+    assert probe(3, 0, ctypes.c_void_p(256), ctypes.c_void_p(512), 24, ctypes.byref(w), None) == 1  # not x16
+    assert probe(3, 0, ctypes.c_void_p(256), ctypes.c_void_p(272), 64, ctypes.byref(w), None) == 2  # overlap
+    assert probe(3, 0, None, None, 0, None, None) == 1  # NULL work
     assert L.ln_set_tuning(b"simt_tile", 32) == 1 and L.ln_set_tuning(b"simt_tile", 1) == 1
