@@ -5,7 +5,10 @@
  * GEMM, a chain of two GEMMs (polybench 2mm), three chained products
  * (polybench 3mm), covariance, correlation, SYRK and SYR2K (single and
  * batched), modified Gram-Schmidt QR, plus the vector-Jacobian products of the
- * chain, 3mm, covariance and correlation.
+ * chain, 3mm, covariance and correlation. Around them: tuning knobs
+ * (ln_set_tuning), launch counting and CUDA-event timing (ln_timing_*), and
+ * peak probes that measure this device's tensor-core, FFMA and copy rates
+ * (ln_peak_probe).
  *
  * Every operation exists in two forms:
  *   LN_FORM_PLAIN        one thread per output element, reading global memory
