@@ -1,4 +1,4 @@
-"""Seeded random shapes at tile boundaries, every operation and form.
+"""Seeded random shapes at tile boundaries, every operation, adjoint and form.
 
 Each size is a multiple of 32, 64, 128 or 256 (one to three of them), or one
 more or one less: the edges where the tcgen05 engine's 128-row and 64-k tiles,
@@ -138,4 +138,50 @@ def test_cov_corr_sweep(api, i):
         check(cov, cov_ref, prec, f"covariance {n}x{m} {form}")
         check(corr, corr_ref, prec, f"correlation {n}x{m} {form}")
         assert np.array_equal(cov, cov.T) and np.array_equal(corr, corr.T)
+    api.stream_check()
+
+
+# adjoints: the forms and precisions that keep the gate
+EXACT = [m for m in MODES if m[1] not in ("bf16", "tf32")]
+
+
+@pytest.mark.parametrize("i", range(CASES))
+def test_chain_bwd_sweep(api, i):
+    (ni, nj, nk, nl), seed = draw("chain_bwd", i, 4)
+    d = inputs.chain_inputs(ni, nj, nk, nl, seed=seed)
+    G = inputs.gemm_inputs(ni, nl, 1, seed=seed + 1)["C"]
+    refs = oracle.gemm_chain_vjp(d["A"], d["B"], d["C"], G)
+    t = [dev(x) for x in (d["A"], d["B"], d["C"], G)]
+    for form, prec in EXACT:
+        got = api.gemm_chain_bwd(*t, form=form, prec=prec)
+        for name, g, r in zip(("dA", "dB", "dC"), got, refs):
+            check(host(g), r, prec, f"chain {name} {ni},{nj},{nk},{nl} {form}")
+    api.stream_check()
+
+
+@pytest.mark.parametrize("i", range(CASES))
+def test_3mm_bwd_sweep(api, i):
+    (ni, nj, nk, nl, nm), seed = draw("3mm_bwd", i, 5)
+    rng = np.random.default_rng(seed)
+    mats = [rng.uniform(-1, 1, size=s).astype(np.float32)
+            for s in ((ni, nk), (nk, nj), (nj, nm), (nm, nl), (ni, nl))]
+    refs = oracle.three_mm_vjp(*mats)
+    t = [dev(x) for x in mats]
+    for form, prec in EXACT:
+        got = api.three_mm_bwd(*t, form=form, prec=prec)
+        for name, g, r in zip(("dA", "dB", "dC", "dD"), got, refs):
+            check(host(g), r, prec, f"3mm {name} {ni},{nj},{nk},{nl},{nm} {form}")
+    api.stream_check()
+
+
+@pytest.mark.parametrize("i", range(CASES))
+def test_cov_corr_bwd_sweep(api, i):
+    (n, m), seed = draw("cov_bwd", i, 2)
+    X = inputs.cov_inputs(n, m, seed=seed)["X"]
+    W = np.random.default_rng(seed).uniform(-1, 1, size=(m, m)).astype(np.float32)
+    rc, rr = oracle.covariance_vjp(X, W), oracle.correlation_vjp(X, W)
+    Xd, Wd = dev(X), dev(W)
+    for form, prec in EXACT:
+        check(host(api.covariance_bwd(Xd, Wd, form=form, prec=prec)), rc, prec, f"covariance dX {n}x{m} {form}")
+        check(host(api.correlation_bwd(Xd, Wd, form=form, prec=prec)), rr, prec, f"correlation dX {n}x{m} {form}")
     api.stream_check()
