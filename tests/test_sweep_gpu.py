@@ -185,3 +185,46 @@ def test_cov_corr_bwd_sweep(api, i):
         check(host(api.covariance_bwd(Xd, Wd, form=form, prec=prec)), rc, prec, f"covariance dX {n}x{m} {form}")
         check(host(api.correlation_bwd(Xd, Wd, form=form, prec=prec)), rr, prec, f"correlation dX {n}x{m} {form}")
     api.stream_check()
+
+
+@pytest.mark.parametrize("i", range(CASES))
+@pytest.mark.parametrize("two", [False, True])
+def test_batched_sweep(api, i, two):
+    """One batch of 24 instances whose n and k are drawn at tile edges, in one
+    fill, through the persistent batched kernel (SymBatch)."""
+    sizes, seed = draw("batched", i, 48)
+    fill = ("full", "lower", "upper")[seed % 3]
+    fl = {"full": 0, "lower": 1, "upper": 2}[fill]
+    inst = [inputs.sym_inputs(n, k, seed=seed + j) for j, (n, k) in enumerate(zip(sizes[0::2], sizes[1::2]))]
+    alpha, beta = inst[0]["alpha"], inst[0]["beta"]
+    refs = [oracle.syr2k(x["A"], x["B"], x["C"], alpha, beta, fl) if two else
+            oracle.syrk(x["A"], x["C"], alpha, beta, fl) for x in inst]
+    As = [dev(x["A"]) for x in inst]
+    Bs = [dev(x["B"]) for x in inst] if two else None
+    for form, prec in MODES:
+        Cs = [dev(x["C"]) for x in inst]
+        api.SymBatch(As, Cs, Bs, alpha, beta, fill=fill, form=form, prec=prec).run()
+        api.stream_check()
+        for x, C, r in zip(inst, Cs, refs):
+            check(host(C), r, prec, f"batched {'syr2k' if two else 'syrk'} n={x['A'].shape[0]} "
+                                    f"k={x['A'].shape[1]} {fill} {form}")
+
+
+@pytest.mark.parametrize("i", range(CASES))
+def test_gramschmidt_sweep(api, i):
+    """Modified Gram-Schmidt QR of an m x n matrix (m >= n) drawn at tile
+    edges: R within the gate, Q within the gate or the conditioning bound, QR
+    reproducing A, R upper triangular with a non-negative diagonal."""
+    sizes, seed = draw("gramschmidt", i, 2)
+    m, n = max(sizes), min(sizes)
+    A = inputs.gramschmidt_inputs(m, n, seed=seed)["A"]
+    Qo, Ro = oracle.gramschmidt(A)
+    kappa = np.linalg.cond(A.astype(np.float64))
+    for form in ("plain", "internalized"):
+        Q, R = api.gramschmidt(dev(A), form=form)
+        api.stream_check()
+        Q, R = host(Q), host(R)
+        assert np.array_equal(np.tril(R, -1), np.zeros_like(R)) and np.all(np.diag(R) >= 0), (m, n, form)
+        assert inputs.rel_fro(R, Ro) <= GATE, (m, n, form)
+        assert inputs.rel_fro(Q, Qo) <= max(GATE, kappa * 2.0 ** -24), (m, n, form)
+        assert inputs.rel_fro(Q @ R, A.astype(np.float64)) <= GATE, (m, n, form)
