@@ -85,7 +85,7 @@ def parse():
     return ap.parse_args()
 
 
-UMMA_SOURCES = ["ln_umma_kernel.cuh", "ln_umma_general.cu", "ln_umma_sym.cu", "ln_umma_pair.cu", "ln_umma_tf32.cu", "ln_split.cuh",
+UMMA_SOURCES = ["ln_umma_kernel.cuh", "ln_umma_general.cu", "ln_umma_sym.cu", "ln_umma_pair.cu", "ln_umma_tf32.cu", "ln_umma_tf32_pair.cu", "ln_split.cuh",
                 "ln_epilogue.cuh", "ln_async.cuh", "ln_pack_stream.cuh", "ln_internal.h"]
 
 

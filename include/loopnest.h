@@ -191,8 +191,11 @@ ln_status ln_peak_probe(int kind, long long iters, const void *src, void *dst, l
  *              CTAs compute vertically adjacent output tiles with
  *              tcgen05.mma.cta_group::2, each holding its own rows of A and
  *              half of the shared column tile of B; 1 pairs 256-wide general
- *              tiles, 2 every tile width and symmetric outputs (measured
- *              slower on 128-wide tiles), 0 none; results are bit-identical;
+ *              tiles of the split precisions (3XBF16, 3XTF32), 2 also
+ *              single-pass BF16 and TF32 (measured slower paired) and, with
+ *              BF16 operands, every other tile width and symmetric outputs
+ *              (measured slower on 128-wide tiles), 0 none; results are
+ *              bit-identical;
  *   "simt_exact" 0 or 1 (default 1): the FP32 tiled form launches its EXACT
  *              instance (no bounds predicates, 16-byte epilogue accesses) when
  *              M, N are multiples of its tile width, K of 8, and every operand

@@ -329,6 +329,10 @@ ln_status umma_contract_sym_tf32(const UmmaProblem &p, int terms, int bn, int to
 ln_status umma_contract_batched_tf32(const UmmaProblem *d_probs, const int *d_tile_prefix, const int *d_tile_owner,
                                      int total_tiles, int *d_queue, int terms, cudaStream_t st);
 ln_status umma_read_error_tf32(int *value);
+// ln_umma_tf32_pair.cu: TF32 launches on CTA pairs, 256-wide general tiles
+// (`total` counts pair tiles)
+ln_status umma_contract_tf32_pair(int ek, const UmmaProblem &p, int terms, int total, cudaStream_t st);
+ln_status umma_read_error_tf32_pair(int *value);
 ln_status umma_read_error(int *value);
 // batched planning on the device
 // ln_pack.cu: batched layout. The plan kernel orders instances by decreasing

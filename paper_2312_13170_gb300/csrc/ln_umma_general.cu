@@ -111,11 +111,16 @@ ln_status umma_contract(const UmmaProblem &p0, int terms, cudaStream_t st, const
         LN_CUDA_TRY(cudaMemsetAsync(p.kcnt, 0, umma_split_cnt_bytes(tiles / p.ksplit, 0), st));
     }
     if (tiles > 0x7fffffffLL) return fail(LN_ERR_INVALID_VALUE, "too many work items");
-    // CTA pairs over vertically adjacent tiles ("pair" knob 1: 256-wide tiles, where
-    // they measured faster; 2: every width): `total` counts pair tiles
+    // CTA pairs over vertically adjacent tiles ("pair" knob 1: 256-wide tiles of
+    // split operands, where they measured faster; with one term a stage holds
+    // one product's MMAs, too few to cover the pair's per-stage hand-off;
+    // 2: every width and term count, TF32 operands still 256-wide only):
+    // `total` counts pair tiles
     const int bn_pair = p.bn > 0 ? p.bn : umma_tile_n(terms, 0, p.epi.M, p.epi.N);
-    if (!p.tf32 && (tune_pair() == 2 || (tune_pair() == 1 && bn_pair == 256)) && p.ksplit <= 1 && !p.streamk &&
-        p.mt >= 2) {
+    const bool pair_auto = tune_pair() == 1 && bn_pair == 256 && terms >= 2;
+    const bool pair_width = p.tf32 ? bn_pair == 256 && (tune_pair() == 2 || pair_auto)
+                                   : tune_pair() == 2 || pair_auto;
+    if (pair_width && p.ksplit <= 1 && !p.streamk && p.mt >= 2) {
         p.pair = 1;
         tiles = ceil_div(p.mt, 2) * p.nt;
     }
@@ -124,7 +129,8 @@ ln_status umma_contract(const UmmaProblem &p0, int terms, cudaStream_t st, const
     if (bn != 128 && bn != 256) return fail(LN_ERR_INVALID_VALUE, "tile width %d", bn);
     if (terms > 2 && bn != 128) return fail(LN_ERR_INVALID_VALUE, "three split terms need 128-wide tiles");
     const bool wide = bn == 256;
-    if (p.tf32) return umma_contract_tf32(ek, p, terms, bn, total, st);
+    if (p.tf32)
+        return p.pair ? umma_contract_tf32_pair(ek, p, terms, total, st) : umma_contract_tf32(ek, p, terms, bn, total, st);
     if (p.pair) return umma_contract_pair(ek, p, terms, bn, total, st, side, side_done);
     switch (terms) {
         case 1:
@@ -147,7 +153,7 @@ ln_status umma_read_error_general(int *value) {
 }
 
 ln_status umma_read_error(int *value) {
-    int a = 0, b = 0, c = 0, d = 0;
+    int a = 0, b = 0, c = 0, d = 0, e = 0;
     ln_status s = umma_read_error_general(&a);
     if (s != LN_SUCCESS) return s;
     s = umma_read_error_sym(&b);
@@ -156,7 +162,9 @@ ln_status umma_read_error(int *value) {
     if (s != LN_SUCCESS) return s;
     s = umma_read_error_tf32(&d);
     if (s != LN_SUCCESS) return s;
-    *value = a | b | c | d;
+    s = umma_read_error_tf32_pair(&e);
+    if (s != LN_SUCCESS) return s;
+    *value = a | b | c | d | e;
     return LN_SUCCESS;
 }
 

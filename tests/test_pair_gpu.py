@@ -1,6 +1,7 @@
 """CTA pairs of the tensor-core contractions (the "pair" knob: 1, the default,
-pairs 256-wide general tiles; 2, used here, pairs every width, symmetric
-outputs included).
+pairs 256-wide general tiles of the split precisions, BF16 and TF32 operands;
+2, used here, also single-pass BF16 and TF32, and every width with BF16
+operands, symmetric outputs included).
 
 Two CTAs of a cluster compute vertically adjacent output tiles and each copies
 half of the shared column operand into both CTAs' shared memory. Every tile is
@@ -57,7 +58,7 @@ def paired_and_not(api, fn):
     return out
 
 
-@pytest.mark.parametrize("prec", ["bf16", "3xbf16", "6xbf16"])
+@pytest.mark.parametrize("prec", ["bf16", "3xbf16", "6xbf16", "tf32", "3xtf32"])
 @pytest.mark.parametrize("M,N,K", [(300, 517, 389), (256, 256, 256), (1000, 1100, 700), (129, 77, 1000)])
 def test_gemm_pairs(api, prec, M, N, K):
     g = inputs.gemm_inputs(M, N, K, seed=M + N)
@@ -69,7 +70,7 @@ def test_gemm_pairs(api, prec, M, N, K):
 
     on, off = paired_and_not(api, run)
     assert np.array_equal(on, off)
-    if prec != "bf16":
+    if prec not in ("bf16", "tf32"):
         assert inputs.rel_fro(on, oracle.gemm(g["A"], g["B"], g["C"], g["alpha"], g["beta"])) <= GATE
 
 
@@ -81,13 +82,14 @@ def test_gemm_pairs_integer_bitexact(api):
     assert np.array_equal(host(Cd).astype(np.float64), oracle.gemm(A, B, C, 2.0, -1.0))
 
 
-@pytest.mark.parametrize("shape", [(2048, 2048, 2048, 2048), (333, 257, 500, 129)])
-def test_chain_pairs(api, shape):
+@pytest.mark.parametrize("prec", ["3xbf16", "3xtf32"])
+@pytest.mark.parametrize("shape", [(2048, 2048, 2048, 2048), (333, 257, 500, 129), (1500, 700, 900, 1300)])
+def test_chain_pairs(api, shape, prec):
     d = inputs.chain_inputs(*shape, seed=41)
     t = {k: dev(d[k]) for k in "ABCD"}
 
     def run():
-        E, F = api.gemm_chain(t["A"], t["B"], t["C"], t["D"], d["alpha"], d["beta"], prec="3xbf16")
+        E, F = api.gemm_chain(t["A"], t["B"], t["C"], t["D"], d["alpha"], d["beta"], prec=prec)
         return host(E), host(F)
 
     (E1, F1), (E0, F0) = paired_and_not(api, run)
@@ -97,12 +99,13 @@ def test_chain_pairs(api, shape):
     assert inputs.rel_fro(E1[rows], E_ref) <= GATE and inputs.rel_fro(F1[rows], F_ref) <= GATE
 
 
-def test_3mm_pairs(api):
+@pytest.mark.parametrize("prec", ["3xbf16", "3xtf32"])
+def test_3mm_pairs(api, prec):
     rng = np.random.default_rng(42)
     A, B, C, D = (rng.uniform(-1, 1, size=s).astype(np.float32) for s in ((700, 500), (500, 900), (900, 300),
                                                                           (300, 650)))
     T = [dev(x) for x in (A, B, C, D)]
-    on, off = paired_and_not(api, lambda: host(api.three_mm(*T, prec="3xbf16")))
+    on, off = paired_and_not(api, lambda: host(api.three_mm(*T, prec=prec)))
     assert np.array_equal(on, off)
     assert inputs.rel_fro(on, oracle.three_mm(A, B, C, D)) <= GATE
 
