@@ -23,3 +23,17 @@ def test_reference_arm_json_line():
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"]
+
+
+def test_traffic_capture_matches_the_kernel_sources():
+    """roofline.traffic comes from an ncu capture stored with a hash of the
+    tcgen05 kernel's sources; it must list the same sources as bench.py and
+    match their committed contents, so that an edited kernel without a fresh
+    capture shows up here rather than as a null traffic figure."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    with open(os.path.join(ROOT, "profiles", "k_umma_traffic.json")) as f:
+        d = json.load(f)
+    assert d["sources"] == bench.UMMA_SOURCES
+    assert bench.umma_traffic() == d["dram_bytes_per_launch_mean"] > 0
